@@ -1,0 +1,353 @@
+"""Benchmark of the fused phase-field LB step on GB300.
+
+Workload: FP32 sessile droplet on a curved wall -- a 128^3 periodic box with a
+voxelised solid sphere of radius 30 centred on the bottom plane, solid planes
+at z = 0 and z = 127, a droplet of radius 20 (tanh profile, W = 4) tangent to
+the sphere's top, input contact angle 60 deg, density ratio 1000,
+sigma = 0.005, tau = 0.8, M = 0.02, optimised model (tanh F, free-slip band,
+blend 0.95).  Synthetic geometry.
+
+One bench step = one time step of the whole path in one fused kernel launch:
+phi recompute, wall ghosts, stencils, macros, h and g collisions and
+streaming, and the diagnostics reduction (mass, pressure jump, contact-line
+band, max |u|).  The state (3 x 19 FP32 population arrays, ~480 MB) is
+larger than L2, so no L2 flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank advances its own replica (independent lattices,
+no data-path exchange: weak scaling).  --impl reference times the FP64 CPU
+oracle on this workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "fused AC+NS LB step MLUPS"
+# Algorithmic bytes per fluid-cell update at FP32 storage: 2 population sets
+# x 19 x (read + write) x 4 B, plus the 1-byte cell flag.
+ALGO_BYTES_FP32 = 2 * 19 * 2 * 4 + 1
+THETA = 60.0
+N_BOX = 128
+KERNEL_SOURCES = ("pflb_kernels.cuh", "pflb_model.cuh", "pflb_launch.cuh", "pflb_f32.cu")
+ORACLE_KEYS = ("sigma", "W", "M", "rho_H", "rho_L", "nu_H", "nu_L", "theta_deg", "Fex", "blend",
+               "F_mode", "mobility_corr", "free_slip")
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2512_01032_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def hbm_peak():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of the fused kernel from the committed ncu
+    summary, if it was taken on the current kernel sources."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "k_fused_sessile128_traffic.json")))
+    except Exception:
+        return None
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        try:
+            for ln in open(self.path).read().strip().splitlines()[1:]:
+                f = [x.strip() for x in ln.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1].split()[0]))
+                    smax.append(float(f[2].split()[0]))
+                except ValueError:
+                    continue
+                for k, nm in enumerate(self.NAMES):
+                    if f[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+        except Exception:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload():
+    return synth.sessile_sphere(N_BOX, THETA)
+
+
+def config_of(g, fluid):
+    return {"workload": f"FP32 sessile droplet on a curved wall, {g.nx}x{g.ny}x{g.nz} D3Q19, "
+                        f"solid sphere R=30, drop R=20, theta={THETA:g} deg, density ratio 1000",
+            "lattice": [g.nx, g.ny, g.nz], "fluid_cells": int(fluid), "storage": "fp32",
+            "kernel": "fused z-marching (one launch per step, diagnostics on)",
+            "l2": "inputs larger than L2 (no flush)"}
+
+
+def oracle_lattice(g, p, drop, nthreads):
+    import oracle as O
+    op = {k: v for k, v in p.items() if k in ORACLE_KEYS}
+    L = O.OracleLattice(g.nx, g.ny, g.nz, solid=g.solid, wall_normal=g.normals(),
+                        theta_cells=g.theta(), nthreads=nthreads, **op)
+    phi0 = O.tanh_phi(0, (g.nx, g.ny, g.nz), drop["center"], drop["R"], p["W"]) * (1 - g.solid)
+    L.init_phi(phi0)
+    return L
+
+
+def slab(g, z0, nz_s):
+    """The z-planes [z0, z0 + nz_s) of a geometry as a periodic lattice."""
+    s = synth.Geometry(g.nx, g.ny, nz_s)
+    s.solid3 = g.solid3[z0:z0 + nz_s].copy()
+    s.theta3 = g.theta3[z0:z0 + nz_s].copy()
+    nrm = g.normals().reshape(g.nz, g.ny, g.nx, 3)[z0:z0 + nz_s].copy()
+    s.normals = lambda: nrm.reshape(-1)
+    return s
+
+
+def cpu_baseline(g, p, drop, budget_s=15.0):
+    """The oracle as it stands, all host cores, on the same lattice for a
+    bounded number of steps (about budget_s of CPU time)."""
+    nthreads = os.cpu_count() or 1
+    L = oracle_lattice(g, p, drop, nthreads)
+    t0 = time.perf_counter()
+    L.step(1)
+    per = max(time.perf_counter() - t0, 1e-6)
+    k = max(1, min(200, int(budget_s / per)))
+    t0 = time.perf_counter()
+    L.step(k)
+    dt = time.perf_counter() - t0
+    fluid = int(g.N - g.solid.sum())
+    return {"value": fluid * k / dt / 1e6, "unit": "MLUPS", "cores": nthreads, "kind": "oracle",
+            "sample": f"{k} FP64 oracle steps of the full {g.nx}x{g.ny}x{g.nz} lattice "
+                      f"({dt:.1f} s on {nthreads} threads)"}
+
+
+def main_reference(args):
+    """Reference arm: the FP64 oracle timed on the host cores.  Each bench
+    step is one oracle step of a z-slab of the workload lattice (around the
+    droplet), the slab height chosen so the whole run takes about two
+    minutes."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    g, p, drop = workload()
+    nthreads = os.cpu_count() or 1
+    cal = oracle_lattice(slab(g, 40, 8), p, dict(drop, center=(drop["center"][0],
+                                                                drop["center"][1], 10.0)),
+                         nthreads)
+    t0 = time.perf_counter()
+    cal.step(2)
+    rate = 2 * g.nx * g.ny * 8 / max(time.perf_counter() - t0, 1e-6)
+    per_step_cells = rate * 110.0 / max(1, args.steps + args.warmup)
+    nz_s = int(max(4, min(g.nz, per_step_cells // (g.nx * g.ny))))
+    z0 = max(0, min(g.nz - nz_s, 50 - nz_s // 2))
+    sg = slab(g, z0, nz_s)
+    sd = dict(drop, center=(drop["center"][0], drop["center"][1], drop["center"][2] - z0))
+    L = oracle_lattice(sg, p, sd, nthreads)
+    for _ in range(args.warmup):
+        L.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        L.step(1)
+    dt = time.perf_counter() - t0
+    fluid = int(sg.N - sg.solid.sum())
+    v = fluid * args.steps / dt / 1e6
+    sample = (f"each step: one FP64 oracle step of planes z={z0}..{z0 + nz_s - 1} "
+              f"({sg.nx}x{sg.ny}x{nz_s}, {fluid} fluid cells) of the workload lattice")
+    line = {"metric": METRIC, "value": v, "unit": "MLUPS", "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(g, int(g.N - g.solid.sum())),
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": nthreads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--tile", type=str, default="", help="bx,by,lz of the fused kernel")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return main_reference(args)
+    args.warmup = max(args.warmup, 3)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2512_01032_gb300 import pflb
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+
+    g, p, drop = workload()
+    fluid = int(g.N - g.solid.sum())
+    L = pflb.Lattice(g.nx, g.ny, g.nz, solid=g.solid, wall_normal=g.normals(),
+                     theta_cells=g.theta(), stream=stream, storage="fp32", **p)
+    if args.tile:
+        bx, by, lz = (int(v) for v in args.tile.split(","))
+        L.set_kernel(0, bx, by, lz)
+    L.init_tanh(0, drop["center"], drop["R"])
+    L.set_diag_every(1)
+
+    # ---------------------------------------------- device-resident timing
+    L.step(args.warmup)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    start.record(stream)
+    L.step(args.steps)
+    end.record(stream)
+    end.synchronize()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clocks = clk.stop()
+    ms = start.elapsed_time(end)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    d = L.last_diag()
+    ms_step = ms / args.steps
+    value = world * fluid * args.steps / (ms * 1e-3) / 1e6
+
+    peak, peak_kind = hbm_peak()
+    achieved = fluid * ALGO_BYTES_FP32 / (ms_step * 1e-3) / 1e9
+    traffic = recorded_traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS hbm_gbs)",
+                "algorithmic_bytes_per_cell": ALGO_BYTES_FP32, "kernel": "k_fused"}
+
+    # ---------------------------------------------- end to end (host buffers)
+    e2e = None
+    if not args.no_e2e:
+        phi0 = torch.empty(g.N, dtype=torch.float64, pin_memory=True).numpy()
+        L2 = pflb.Lattice(g.nx, g.ny, g.nz, solid=g.solid, wall_normal=g.normals(),
+                          theta_cells=g.theta(), stream=stream, storage="fp32", **p)
+        L2.init_tanh(0, drop["center"], drop["R"])
+        phi0[:] = L2.read("phi")
+        L2.set_diag_every(1)
+        force = np.zeros(3)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        L2.init_phi(phi0)
+        for _ in range(args.steps):
+            L2.set_force(force)
+            L2.step(1)
+            L2.last_diag()
+        phi_out = L2.read("phi")
+        t1 = time.perf_counter()
+        te = t1 - t0
+        if world > 1:
+            t = torch.tensor([te], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": world * fluid * args.steps / te / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": (8 * g.N + 24 * args.steps) / args.steps,
+               "d2h_bytes_per_step": (256 * args.steps + 8 * g.N) / args.steps,
+               "path": "pflb_init_phi(host phi) + per step pflb_set_force + pflb_step + "
+                       "pflb_last_diag (host) + final pflb_read(phi)",
+               "final_mass": float(phi_out.sum())}
+        L2.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(g, p, drop)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic", "config": config_of(g, fluid),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": args.steps, "clocks": clocks,
+                "diag_last": {"mass": d["mass"], "dp": d["dp"], "u_max": d["u_max"],
+                              "nonfinite": d["nonfinite"]}}
+        print(json.dumps(line), flush=True)
+    L.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,221 @@
+/*
+ * pflb.h -- C ABI of the GB300 phase-field lattice Boltzmann library.
+ *
+ * One time step advances the two D3Q19 population sets of the conservative
+ * Allen-Cahn phase-field lattice Boltzmann method of "Capillary flow
+ * simulation with the phase-field-based lattice Boltzmann solver"
+ * (arXiv 2512.01032):
+ *   h_i : phase-field populations, Eqs. 1-4 (with the local mobility
+ *         correction of Eq. 4);
+ *   g_i : hydrodynamic populations (the paper's g-bar), Eqs. 5-11 (filtered
+ *         collision, force K_i with the chemical potential of Eq. 7);
+ * with the central-difference gradient and Laplacian of Eq. 13, the
+ * wettability ghosts of Eqs. 12-15 and the optimised friction model of
+ * Sec. III A (tanh F(phi), free-slip band, hysteresis blend) at solid voxels.
+ *
+ * Conventions shared by every call:
+ *   - Lattice units (the paper's Sec. I convention), T = 1/3.
+ *   - Cells are indexed x fastest: cell = x + nx*(y + ny*z).  The box is
+ *     periodic in x, y and z; walls are solid voxels.
+ *   - The library owns all device memory of a lattice; the caller owns every
+ *     host buffer.  Input arrays are copied before the call returns.
+ *   - Every call returns a pflb_status; no exception crosses the ABI.  After
+ *     a CUDA error the lattice is poisoned: later calls return
+ *     PFLB_ERR_STATE.  pflb_last_error() gives a thread-local message.
+ *   - Work is ordered on the CUDA stream given at creation (NULL = the
+ *     legacy default stream).  pflb_step is asynchronous; pflb_read,
+ *     pflb_diag and pflb_save synchronise that stream.
+ */
+#ifndef PFLB_H
+#define PFLB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pflb_lattice pflb_lattice;
+
+typedef enum {
+  PFLB_OK = 0,
+  PFLB_ERR_ARG = 1,     /* invalid argument or parameter */
+  PFLB_ERR_OOM = 2,     /* device or host allocation failed */
+  PFLB_ERR_CUDA = 3,    /* a CUDA call failed (lattice is poisoned) */
+  PFLB_ERR_NAN = 4,     /* a diagnostic found non-finite fields */
+  PFLB_ERR_TIMEOUT = 5, /* a bounded wait ran out */
+  PFLB_ERR_BUDGET = 6,  /* request exceeds the memory budget */
+  PFLB_ERR_STATE = 7    /* lattice poisoned by an earlier error */
+} pflb_status;
+
+/* Population storage (the collision always computes in FP32 for FP32
+ * storage and in FP64 for FP64 storage). */
+enum { PFLB_STORAGE_FP64 = 0, PFLB_STORAGE_FP32 = 1 };
+
+/* Fields for pflb_read. */
+enum { PFLB_FIELD_PHI = 0, PFLB_FIELD_RHO = 1, PFLB_FIELD_P = 2,
+       PFLB_FIELD_UX = 3, PFLB_FIELD_UY = 4, PFLB_FIELD_UZ = 5 };
+
+/* Step kernels: one fused pass per step (default), or a phi pass followed
+ * by a per-cell pass. */
+enum { PFLB_KERNEL_FUSED = 0, PFLB_KERNEL_TWOPASS = 1 };
+
+/* Geometry, read during pflb_create only.
+ *   solid       : host, nx*ny*nz bytes, nonzero = solid voxel.
+ *   wall_normal : host, 3 doubles per cell (x,y,z), unit normal pointing into
+ *                 the fluid, read at wall nodes (fluid cells with a solid
+ *                 D3Q19 neighbour); NULL = estimate from the mask as the
+ *                 normalised -sum_i w_i c_i [x + c_i solid].
+ *   theta_deg   : host, one input contact angle per cell (degrees, measured
+ *                 inside the phi = 1 phase), read at wall nodes; NULL = use
+ *                 params.theta_deg everywhere. */
+typedef struct {
+  int nx, ny, nz;
+  const uint8_t *solid;
+  const double *wall_normal;
+  const double *theta_deg;
+} pflb_geometry;
+
+/* Model parameters (lattice units).
+ *   sigma, W, M       : surface tension, interface width, mobility (Eqs. 1-7)
+ *   rho_H, rho_L      : densities of the phi = 1 (heavy) and phi = 0 phases;
+ *                       rho = rho_L + phi (rho_H - rho_L)
+ *   nu_H, nu_L        : kinematic viscosities; tau = nu/T + 1/2 (Eq. 8)
+ *   theta_deg         : default input contact angle (Sec. II B)
+ *   Fex               : external body force (Eq. 6)
+ *   gamma, phi_M, phi_m, D, eps : mobility correction constants (Eq. 4)
+ *   blend             : hysteresis blend b: ghost = b old + (1-b) new
+ *   band_lo, band_hi  : free-slip band on phi (Sec. III A)
+ *   F_tilde, F_width  : optimised F(phi) = (tanh((phi-F_tilde)/F_width)+1)/2
+ *   F_mode            : 0 = F(phi) = phi, 1 = optimised tanh F
+ *   mobility_corr     : 1 = add delta-theta of Eq. 4
+ *   free_slip         : 1 = specular reflection of edge links at flat
+ *                       axis-aligned walls when phi at both wall nodes of
+ *                       the link pair lies in the band
+ *   storage           : PFLB_STORAGE_* */
+typedef struct {
+  double sigma, W, M, rho_H, rho_L, nu_H, nu_L, theta_deg;
+  double Fex[3];
+  double gamma, phi_M, phi_m, D, eps, blend, band_lo, band_hi, F_tilde, F_width;
+  int F_mode, mobility_corr, free_slip, storage;
+} pflb_params;
+
+/* Diagnostics of the current state, accumulated in FP64 on the device.
+ *   mass        : sum of phi over fluid cells
+ *   n_heavy     : number of fluid cells with phi >= 0.5
+ *   p_heavy/p_light : mean P over fluid cells with phi > 0.95 / phi < 0.05
+ *   dp          : p_heavy - p_light (pressure jump)
+ *   u_max       : max |u| over fluid cells
+ *   region_mass : sum of phi over the box set by pflb_set_region
+ *   cl_count, cl_mean[3], cl_m2[3] : wall nodes with 0.25 <= phi <= 0.75
+ *                 (contact-line band): count, mean and mean square position
+ *   kinetic     : sum of rho |u|^2 / 2
+ *   nonfinite   : number of fluid cells with a non-finite phi, P or u */
+typedef struct {
+  int64_t step;
+  double mass, n_heavy, p_heavy, p_light, n_p_heavy, n_p_light, dp, u_max;
+  double region_mass;
+  double cl_count, cl_mean[3], cl_m2[3];
+  double kinetic;
+  double nonfinite;
+} pflb_diag_t;
+
+/* Fill p with the paper's defaults: gamma = -22.5, phi_M = 0.8,
+ * phi_m = 0.2, D = 1e-4, eps = 1e-10 (Eq. 4); blend = 0.95, band
+ * [0.5, 0.95], F_tilde = 0.1, F_width = 0.001 (Sec. III A); the remaining
+ * physical values are those of the static-droplet case (sigma = 0.01,
+ * W = 4, M = 0.02, rho ratio 1000, nu = 0.1), FP32 storage. */
+void pflb_default_params(pflb_params *p);
+
+/* Create a lattice from geometry and parameters.  Validates parameters
+ * (dimensions >= 1, W > 0, M > 0, nu > 0 so that tau > 1/2, rho_L > 0,
+ * rho_H > 0, 0 <= blend <= 1, storage known) and returns PFLB_ERR_ARG
+ * otherwise.  cuda_stream: a cudaStream_t or NULL.  On success *out owns
+ * all device memory (about 228 B/cell at FP32 storage); the state is
+ * zero until an init call. */
+pflb_status pflb_create(const pflb_geometry *geom, const pflb_params *params, void *cuda_stream,
+                        pflb_lattice **out);
+
+/* Initialise phi from the steady tanh profile of Eq. 12 and set the
+ * equilibrium state (u = 0, P = P0, h = h_eq, g = g_eq with K_i from the
+ * initial gradient, wetting ghosts = phi of the wall node); resets the
+ * step counter.
+ *   shape 0 (sphere): phi = (1 + tanh(2 (R - r)/W))/2, r = minimum-image
+ *           distance from center (cell centres at integer coordinates);
+ *   shape 1 (half space): phi = (1 + tanh(2 d/W))/2, d = (center - x).normal;
+ *   shape 2 (slab): phi = (1 + tanh(2 (R - |d|)/W))/2.
+ * normal may be NULL for shape 0.  phi is zero on solid cells. */
+pflb_status pflb_init_tanh(pflb_lattice *L, int shape, const double center[3], double R,
+                           const double normal[3], double P0);
+
+/* Same from a host phi array (nx*ny*nz doubles; solid cells ignored). */
+pflb_status pflb_init_phi(pflb_lattice *L, const double *phi_host, double P0);
+
+/* Set the external body force F_ex of Eq. 6 for the following steps. */
+pflb_status pflb_set_force(pflb_lattice *L, const double Fex[3]);
+
+/* Box [lo, hi) (x0,x1,y0,y1,z0,z1) over which region_mass is summed. */
+pflb_status pflb_set_region(pflb_lattice *L, const int box[6]);
+
+/* Choose the step kernel and its launch shape: tile bx * by threads
+ * (bx * by <= 256, 2 (bx+2) + 2 by <= bx * by) marching lz planes in z.
+ * Zeros keep the current values. */
+pflb_status pflb_set_kernel(pflb_lattice *L, int kind, int bx, int by, int lz);
+
+/* Advance nsteps time steps (asynchronous on the lattice stream). */
+pflb_status pflb_step(pflb_lattice *L, int64_t nsteps);
+
+/* Make pflb_step accumulate the diagnostics (pflb_diag_t) inside the step
+ * kernel on every k-th step (step index divisible by k), at the cost of a
+ * block reduction and a few FP64 atomics per block; 0 (the default) turns
+ * this off.  The values describe the state each such step consumed. */
+pflb_status pflb_set_diag_every(pflb_lattice *L, int k);
+
+/* Diagnostics accumulated by the most recent step that computed them;
+ * out->step is that step's index.  Synchronises.  PFLB_ERR_STATE if no step
+ * has computed diagnostics since the last init; PFLB_ERR_NAN (with *out
+ * filled) when a non-finite value was found. */
+pflb_status pflb_last_diag(pflb_lattice *L, pflb_diag_t *out);
+
+/* Advance nsteps >= 1 steps, the last of them accumulating diagnostics, and
+ * return those (as pflb_last_diag; synchronises). */
+pflb_status pflb_step_diag(pflb_lattice *L, int64_t nsteps, pflb_diag_t *out);
+
+/* Copy one macroscopic field of the current state (as the next step would
+ * see it: phi = sum h, ghosts updated, P and u recovered) into host_out
+ * (nx*ny*nz doubles; zero on solid cells).  Synchronises. */
+pflb_status pflb_read(pflb_lattice *L, int field, double *host_out);
+
+/* Diagnostics of the current state (synchronises).  Returns PFLB_ERR_NAN
+ * (with *out filled) when a non-finite value was found. */
+pflb_status pflb_diag(pflb_lattice *L, pflb_diag_t *out);
+
+/* Number of steps taken since the last init. */
+int64_t pflb_get_step(const pflb_lattice *L);
+
+/* Bytes of device memory the lattice holds. */
+int64_t pflb_device_bytes(const pflb_lattice *L);
+
+/* Device memory a lattice of this geometry and storage would need (bytes),
+ * counted from the mask without allocating (the lazily allocated field
+ * output of pflb_read and the init scratch are not included); -1 on a bad
+ * argument. */
+int64_t pflb_estimate_bytes(const pflb_geometry *geom, int storage);
+
+/* Checkpoint the full state (populations, wall buffers, ghosts, step) to a
+ * file, and restore it into a lattice of identical geometry and storage.
+ * A restored run continues bit for bit. */
+pflb_status pflb_save(pflb_lattice *L, const char *path);
+pflb_status pflb_load(pflb_lattice *L, const char *path);
+
+/* Free the lattice (synchronises its stream first).  NULL is ignored. */
+void pflb_destroy(pflb_lattice *L);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *pflb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PFLB_H */

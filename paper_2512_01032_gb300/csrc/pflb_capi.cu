@@ -1,0 +1,590 @@
+// pflb_capi.cu -- C ABI of the phase-field lattice Boltzmann library
+// (declarations and contracts in include/pflb.h).
+//
+// Host side of lattice creation: the voxel mask becomes per-cell flags
+// (solid, wall node), a wall-node list in cell order with each node's
+// solid-link bits, wall normal and contact angle (Sec. II B), then
+// everything is uploaded once.  Stepping only enqueues kernels.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pflb_internal.h"
+#include "pflb_model.cuh"
+
+using pflb::Lattice;
+
+struct pflb_lattice : public Lattice {};
+
+namespace {
+
+thread_local std::string g_err;
+
+pflb_status fail(pflb_status s, const std::string &msg) {
+  g_err = msg;
+  return s;
+}
+
+pflb_status cuda_fail(Lattice *L, cudaError_t e, const char *what) {
+  if (L) L->poisoned = true;
+  return fail(PFLB_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(L, call)                                      \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(L, e_, #call); \
+  } while (0)
+
+bool is_fp64(const Lattice *L) { return L->p.storage == PFLB_STORAGE_FP64; }
+
+cudaError_t do_init(Lattice *L, const double *d_phi0, double P0) {
+  return is_fp64(L) ? pflb::launch_init<double, double>(*L, d_phi0, P0)
+                    : pflb::launch_init<float, float>(*L, d_phi0, P0);
+}
+cudaError_t do_step(Lattice *L, bool diag) {
+  return is_fp64(L) ? pflb::launch_step<double, double>(*L, diag)
+                    : pflb::launch_step<float, float>(*L, diag);
+}
+cudaError_t do_macro(Lattice *L, bool fields) {
+  return is_fp64(L) ? pflb::launch_macro<double, double>(*L, fields)
+                    : pflb::launch_macro<float, float>(*L, fields);
+}
+
+pflb_status check_lattice(const pflb_lattice *L) {
+  if (!L) return fail(PFLB_ERR_ARG, "null lattice");
+  if (L->poisoned) return fail(PFLB_ERR_STATE, "lattice poisoned by an earlier CUDA error");
+  return PFLB_OK;
+}
+
+pflb_status check_params(const pflb_params *p) {
+  if (!p) return fail(PFLB_ERR_ARG, "null params");
+  if (!(p->W > 0) || !(p->M > 0) || !(p->sigma >= 0))
+    return fail(PFLB_ERR_ARG, "need W > 0, M > 0, sigma >= 0");
+  if (!(p->nu_H > 0) || !(p->nu_L > 0))
+    return fail(PFLB_ERR_ARG, "need nu > 0 (tau = nu/T + 1/2 > 1/2)");
+  if (!(p->rho_H > 0) || !(p->rho_L > 0)) return fail(PFLB_ERR_ARG, "need rho_H, rho_L > 0");
+  if (!(p->blend >= 0 && p->blend <= 1)) return fail(PFLB_ERR_ARG, "need 0 <= blend <= 1");
+  if (!(p->D > 0) || !(p->F_width > 0)) return fail(PFLB_ERR_ARG, "need D > 0, F_width > 0");
+  if (p->storage != PFLB_STORAGE_FP64 && p->storage != PFLB_STORAGE_FP32)
+    return fail(PFLB_ERR_ARG, "unknown storage");
+  if (p->F_mode != 0 && p->F_mode != 1) return fail(PFLB_ERR_ARG, "F_mode must be 0 or 1");
+  return PFLB_OK;
+}
+
+inline long long wrap(long long a, long long n) {
+  a %= n;
+  return a < 0 ? a + n : a;
+}
+
+struct HostGeom {
+  std::vector<uint8_t> flags;
+  std::vector<int> widx;
+  std::vector<uint32_t> wmask;
+  std::vector<double> wgeo;  // [5][nw]
+};
+
+// Flags, wall list (cell order), solid-link masks, normals and angles.
+void build_geometry(const pflb_geometry *g, const pflb_params *p, HostGeom &hg) {
+  const int nx = g->nx, ny = g->ny, nz = g->nz;
+  const long long N = (long long)nx * ny * nz;
+  hg.flags.assign(N, 0);
+  hg.widx.assign(N, -1);
+  std::vector<uint32_t> masks;
+  std::vector<long long> cells;
+  for (long long c = 0; c < N; ++c) {
+    if (g->solid[c]) {
+      hg.flags[c] = pflb::F_SOLID;
+      continue;
+    }
+    const long long x = c % nx, y = (c / nx) % ny, z = c / ((long long)nx * ny);
+    uint32_t m = 0;
+    for (int i = 1; i < pflb::Q; ++i) {
+      long long xx = wrap(x + pflb::cx_of(i), nx), yy = wrap(y + pflb::cy_of(i), ny),
+                zz = wrap(z + pflb::cz_of(i), nz);
+      if (g->solid[xx + nx * (yy + (long long)ny * zz)]) m |= 1u << i;
+    }
+    if (m) {
+      hg.flags[c] = pflb::F_WALL;
+      hg.widx[c] = (int)cells.size();
+      cells.push_back(c);
+      masks.push_back(m);
+    }
+  }
+  const size_t nw = cells.size();
+  hg.wmask = masks;
+  hg.wgeo.assign(5 * nw, 0.0);
+  for (size_t k = 0; k < nw; ++k) {
+    const long long c = cells[k];
+    double n[3] = {0, 0, 0};
+    if (g->wall_normal) {
+      for (int a = 0; a < 3; ++a) n[a] = g->wall_normal[3 * c + a];
+    } else {
+      for (int i = 1; i < pflb::Q; ++i)
+        if ((masks[k] >> i) & 1u) {
+          n[0] -= pflb::w_of(i) * pflb::cx_of(i);
+          n[1] -= pflb::w_of(i) * pflb::cy_of(i);
+          n[2] -= pflb::w_of(i) * pflb::cz_of(i);
+        }
+      const double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+      if (nn > 0)
+        for (int a = 0; a < 3; ++a) n[a] /= nn;
+    }
+    const double th = (g->theta_deg ? g->theta_deg[c] : p->theta_deg) * (3.14159265358979323846 / 180.0);
+    hg.wgeo[0 * nw + k] = n[0];
+    hg.wgeo[1 * nw + k] = n[1];
+    hg.wgeo[2 * nw + k] = n[2];
+    hg.wgeo[3 * nw + k] = std::cos(th);
+    hg.wgeo[4 * nw + k] = std::sin(th);
+  }
+}
+
+template <class T>
+cudaError_t dev_alloc(Lattice *L, T **ptr, size_t count) {
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void **)ptr, count * sizeof(T));
+  if (e == cudaSuccess) L->dev_bytes += (int64_t)(count * sizeof(T));
+  return e;
+}
+
+void free_all(Lattice *L) {
+  void *ptrs[] = {L->h[0], L->h[1], L->g, L->wp[0], L->wp[1], L->flags, L->widx, L->wmask,
+                  L->wgeo, L->ghost, L->phi, L->diag, L->out, L->phi0};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+}
+
+int64_t bytes_for(long long N, long long nw, int storage) {
+  const int64_t e = storage == PFLB_STORAGE_FP64 ? 8 : 4;
+  const int64_t r = e;
+  return 3 * 19 * N * e + 2 * 18 * nw * e + N * (1 + 4) + nw * 4 + 5 * nw * r + 18 * nw * r +
+         N * r + 96 * 8;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pflb_default_params(pflb_params *p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof *p);
+  p->sigma = 0.01;
+  p->W = 4.0;
+  p->M = 0.02;
+  p->rho_H = 1.0;
+  p->rho_L = 1e-3;
+  p->nu_H = 0.1;
+  p->nu_L = 0.1;
+  p->theta_deg = 90.0;
+  p->gamma = -22.5;
+  p->phi_M = 0.8;
+  p->phi_m = 0.2;
+  p->D = 1e-4;
+  p->eps = 1e-10;
+  p->blend = 0.95;
+  p->band_lo = 0.5;
+  p->band_hi = 0.95;
+  p->F_tilde = 0.1;
+  p->F_width = 0.001;
+  p->F_mode = 0;
+  p->mobility_corr = 1;
+  p->free_slip = 0;
+  p->storage = PFLB_STORAGE_FP32;
+}
+
+pflb_status pflb_create(const pflb_geometry *geom, const pflb_params *params, void *cuda_stream,
+                        pflb_lattice **out) {
+  if (!out) return fail(PFLB_ERR_ARG, "null out");
+  *out = nullptr;
+  if (!geom || !geom->solid) return fail(PFLB_ERR_ARG, "null geometry or mask");
+  if (geom->nx < 1 || geom->ny < 1 || geom->nz < 1)
+    return fail(PFLB_ERR_ARG, "dimensions must be >= 1");
+  if ((long long)geom->nx * geom->ny * geom->nz > (1LL << 40))
+    return fail(PFLB_ERR_ARG, "lattice too large");
+  pflb_status s = check_params(params);
+  if (s != PFLB_OK) return s;
+
+  pflb_lattice *L = new (std::nothrow) pflb_lattice();
+  if (!L) return fail(PFLB_ERR_OOM, "host allocation failed");
+  L->nx = geom->nx; L->ny = geom->ny; L->nz = geom->nz;
+  L->N = (long long)L->nx * L->ny * L->nz;
+  L->p = *params;
+  L->stream = (cudaStream_t)cuda_stream;
+  L->elem = is_fp64(L) ? 8 : 4;
+  L->reg[1] = L->nx; L->reg[3] = L->ny; L->reg[5] = L->nz;
+  L->lz = L->nz < 16 ? L->nz : 16;
+
+  HostGeom hg;
+  try {
+    build_geometry(geom, params, hg);
+  } catch (...) {
+    delete L;
+    return fail(PFLB_ERR_OOM, "host allocation failed while building geometry");
+  }
+  L->nw = (int)hg.wmask.size();
+  const size_t N = (size_t)L->N, nw = (size_t)L->nw;
+  const size_t E = L->elem, Rb = L->elem;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void **p, size_t bytes) {
+    if (e != cudaSuccess) return;
+    e = cudaMalloc(p, bytes ? bytes : 1);
+    if (e == cudaSuccess) L->dev_bytes += (int64_t)bytes;
+  };
+  A(&L->h[0], 19 * N * E);
+  A(&L->h[1], 19 * N * E);
+  A(&L->g, 19 * N * E);
+  A(&L->wp[0], 18 * nw * E);
+  A(&L->wp[1], 18 * nw * E);
+  A((void **)&L->flags, N);
+  A((void **)&L->widx, N * sizeof(int));
+  A((void **)&L->wmask, nw * sizeof(uint32_t));
+  A(&L->wgeo, 5 * nw * Rb);
+  A(&L->ghost, 18 * nw * Rb);
+  A(&L->phi, N * Rb);
+  A((void **)&L->diag, 96 * sizeof(double));
+  if (e != cudaSuccess) {
+    free_all(L);
+    delete L;
+    cudaGetLastError();
+    return fail(PFLB_ERR_OOM, std::string("device allocation failed: ") + cudaGetErrorString(e));
+  }
+  // Upload geometry.
+  std::vector<float> wgeo_f;
+  const void *wgeo_src = hg.wgeo.data();
+  if (!is_fp64(L)) {
+    wgeo_f.assign(hg.wgeo.begin(), hg.wgeo.end());
+    wgeo_src = wgeo_f.data();
+  }
+  cudaStream_t st = L->stream;
+  e = cudaMemcpyAsync(L->flags, hg.flags.data(), N, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(L->widx, hg.widx.data(), N * sizeof(int), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && nw)
+    e = cudaMemcpyAsync(L->wmask, hg.wmask.data(), nw * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && nw)
+    e = cudaMemcpyAsync(L->wgeo, wgeo_src, 5 * nw * Rb, cudaMemcpyHostToDevice, st);
+  void *zero_bufs[] = {L->h[0], L->h[1], L->g, L->wp[0], L->wp[1], L->ghost, L->phi};
+  size_t zero_len[] = {19 * N * E, 19 * N * E, 19 * N * E, 18 * nw * E, 18 * nw * E,
+                       18 * nw * Rb, N * Rb};
+  for (int k = 0; k < 7 && e == cudaSuccess; ++k)
+    if (zero_len[k]) e = cudaMemsetAsync(zero_bufs[k], 0, zero_len[k], st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    free_all(L);
+    delete L;
+    return fail(PFLB_ERR_CUDA, std::string("upload failed: ") + cudaGetErrorString(e));
+  }
+  *out = L;
+  return PFLB_OK;
+}
+
+static pflb_status init_from_device_phi(pflb_lattice *L, double P0) {
+  CK(L, do_init(L, L->phi0, P0));
+  CK(L, cudaStreamSynchronize(L->stream));
+  return PFLB_OK;
+}
+
+pflb_status pflb_init_phi(pflb_lattice *L, const double *phi_host, double P0) {
+  pflb_status s = check_lattice(L);
+  if (s != PFLB_OK) return s;
+  if (!phi_host) return fail(PFLB_ERR_ARG, "null phi");
+  if (!L->phi0) {
+    cudaError_t e = cudaMalloc((void **)&L->phi0, (size_t)L->N * sizeof(double));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      L->phi0 = nullptr;
+      return fail(PFLB_ERR_OOM, "device allocation failed (init scratch)");
+    }
+    L->dev_bytes += L->N * 8;
+  }
+  CK(L, cudaMemcpyAsync(L->phi0, phi_host, (size_t)L->N * sizeof(double), cudaMemcpyHostToDevice,
+                        L->stream));
+  return init_from_device_phi(L, P0);
+}
+
+pflb_status pflb_init_tanh(pflb_lattice *L, int shape, const double center[3], double R,
+                           const double normal[3], double P0) {
+  pflb_status s = check_lattice(L);
+  if (s != PFLB_OK) return s;
+  if (!center || shape < 0 || shape > 2) return fail(PFLB_ERR_ARG, "bad shape or center");
+  double nv[3] = {1, 0, 0};
+  if (shape != 0) {
+    if (!normal) return fail(PFLB_ERR_ARG, "shape needs a normal");
+    const double nn = std::sqrt(normal[0] * normal[0] + normal[1] * normal[1] + normal[2] * normal[2]);
+    if (!(nn > 0)) return fail(PFLB_ERR_ARG, "zero normal");
+    for (int a = 0; a < 3; ++a) nv[a] = normal[a] / nn;
+  }
+  std::vector<double> phi;
+  try {
+    phi.resize((size_t)L->N);
+  } catch (...) {
+    return fail(PFLB_ERR_OOM, "host allocation failed");
+  }
+  const double W = L->p.W;
+  const int dims[3] = {L->nx, L->ny, L->nz};
+  for (long long c = 0; c < L->N; ++c) {
+    const long long pos[3] = {c % L->nx, (c / L->nx) % L->ny, c / ((long long)L->nx * L->ny)};
+    double d[3];
+    for (int a = 0; a < 3; ++a) {
+      double dd = (double)pos[a] - center[a];
+      dd -= dims[a] * std::nearbyint(dd / dims[a]);  // minimum image
+      d[a] = dd;
+    }
+    double arg;
+    if (shape == 0) {
+      arg = R - std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    } else {
+      const double sd = d[0] * nv[0] + d[1] * nv[1] + d[2] * nv[2];
+      arg = shape == 1 ? -sd : R - std::fabs(sd);
+    }
+    phi[c] = 0.5 * (1.0 + std::tanh(2.0 * arg / W));  // Eq. 12
+  }
+  return pflb_init_phi(L, phi.data(), P0);
+}
+
+pflb_status pflb_set_force(pflb_lattice *L, const double Fex[3]) {
+  pflb_status s = check_lattice(L);
+  if (s != PFLB_OK) return s;
+  if (!Fex) return fail(PFLB_ERR_ARG, "null force");
+  for (int a = 0; a < 3; ++a) L->p.Fex[a] = Fex[a];
+  return PFLB_OK;
+}
+
+pflb_status pflb_set_region(pflb_lattice *L, const int box[6]) {
+  pflb_status s = check_lattice(L);
+  if (s != PFLB_OK) return s;
+  if (!box) return fail(PFLB_ERR_ARG, "null box");
+  for (int k = 0; k < 6; ++k) L->reg[k] = box[k];
+  return PFLB_OK;
+}
+
+pflb_status pflb_set_kernel(pflb_lattice *L, int kind, int bx, int by, int lz) {
+  pflb_status s = check_lattice(L);
+  if (s != PFLB_OK) return s;
+  if (kind != PFLB_KERNEL_FUSED && kind != PFLB_KERNEL_TWOPASS)
+    return fail(PFLB_ERR_ARG, "unknown kernel");
+  const int nbx = bx > 0 ? bx : L->bx, nby = by > 0 ? by : L->by, nlz = lz > 0 ? lz : L->lz;
+  if (nbx * nby > 256 || nbx < 1 || nby < 1)
+    return fail(PFLB_ERR_ARG, "bx*by must be in [1, 256]");
+  if (2 * (nbx + 2) + 2 * nby > nbx * nby)
+    return fail(PFLB_ERR_ARG, "tile too thin: halo ring larger than the block");
+  L->kernel = kind;
+  L->bx = nbx;
+  L->by = nby;
+  L->lz = nlz;
+  return PFLB_OK;
+}
+
+pflb_status pflb_step(pflb_lattice *L, int64_t nsteps) {
+  pflb_status s = check_lattice(L);
+  if (s != PFLB_OK) return s;
+  if (nsteps < 0) return fail(PFLB_ERR_ARG, "negative step count");
+  for (int64_t k = 0; k < nsteps; ++k) {
+    const bool d = L->diag_every > 0 && (L->step % L->diag_every) == 0;
+    CK(L, do_step(L, d));
+  }
+  return PFLB_OK;
+}
+
+pflb_status pflb_set_diag_every(pflb_lattice *L, int every) {
+  pflb_status s = check_lattice(L);
+  if (s != PFLB_OK) return s;
+  if (every < 0) return fail(PFLB_ERR_ARG, "negative diagnostic interval");
+  L->diag_every = every;
+  return PFLB_OK;
+}
+
+static pflb_status fetch_diag(pflb_lattice *L, const double *dev, pflb_diag_t *out) {
+  double d[32];
+  CK(L, cudaMemcpyAsync(d, dev, sizeof d, cudaMemcpyDeviceToHost, L->stream));
+  CK(L, cudaStreamSynchronize(L->stream));
+  std::memset(out, 0, sizeof *out);
+  out->step = L->step;
+  out->mass = d[pflb::D_MASS];
+  out->n_heavy = d[pflb::D_NHEAVY];
+  out->n_p_heavy = d[pflb::D_NPH];
+  out->n_p_light = d[pflb::D_NPL];
+  out->p_heavy = d[pflb::D_NPH] > 0 ? d[pflb::D_PH] / d[pflb::D_NPH] : 0.0;
+  out->p_light = d[pflb::D_NPL] > 0 ? d[pflb::D_PL] / d[pflb::D_NPL] : 0.0;
+  out->dp = out->p_heavy - out->p_light;
+  out->u_max = d[pflb::D_UMAX];
+  out->region_mass = d[pflb::D_REGION];
+  out->cl_count = d[pflb::D_CLN];
+  if (out->cl_count > 0) {
+    out->cl_mean[0] = d[pflb::D_CLX] / out->cl_count;
+    out->cl_mean[1] = d[pflb::D_CLY] / out->cl_count;
+    out->cl_mean[2] = d[pflb::D_CLZ] / out->cl_count;
+    out->cl_m2[0] = d[pflb::D_CLXX] / out->cl_count;
+    out->cl_m2[1] = d[pflb::D_CLYY] / out->cl_count;
+    out->cl_m2[2] = d[pflb::D_CLZZ] / out->cl_count;
+  }
+  out->kinetic = d[pflb::D_KIN];
+  out->nonfinite = d[pflb::D_NONFINITE];
+  if (out->nonfinite > 0 || !std::isfinite(out->mass))
+    return fail(PFLB_ERR_NAN, "non-finite values in the fields");
+  return PFLB_OK;
+}
+
+pflb_status pflb_step_diag(pflb_lattice *L, int64_t nsteps, pflb_diag_t *out) {
+  pflb_status s = check_lattice(L);
+  if (s != PFLB_OK) return s;
+  if (nsteps < 1 || !out) return fail(PFLB_ERR_ARG, "need nsteps >= 1 and an output");
+  for (int64_t k = 0; k < nsteps; ++k) CK(L, do_step(L, k == nsteps - 1));
+  return pflb_last_diag(L, out);
+}
+
+pflb_status pflb_last_diag(pflb_lattice *L, pflb_diag_t *out) {
+  pflb_status s = check_lattice(L);
+  if (s != PFLB_OK) return s;
+  if (!out) return fail(PFLB_ERR_ARG, "null output");
+  if (L->ndiag == 0) return fail(PFLB_ERR_STATE, "no step has computed diagnostics yet");
+  pflb_status r = fetch_diag(L, L->diag + 32 * ((L->ndiag - 1) & 1), out);
+  out->step = L->last_diag_step;
+  return r;
+}
+
+pflb_status pflb_diag(pflb_lattice *L, pflb_diag_t *out) {
+  pflb_status s = check_lattice(L);
+  if (s != PFLB_OK) return s;
+  if (!out) return fail(PFLB_ERR_ARG, "null output");
+  CK(L, do_macro(L, false));
+  return fetch_diag(L, L->diag + 64, out);
+}
+
+pflb_status pflb_read(pflb_lattice *L, int field, double *host_out) {
+  pflb_status s = check_lattice(L);
+  if (s != PFLB_OK) return s;
+  if (!host_out || field < 0 || field > 5) return fail(PFLB_ERR_ARG, "bad field or output");
+  if (!L->out) {
+    cudaError_t e = cudaMalloc((void **)&L->out, 6 * (size_t)L->N * sizeof(double));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      L->out = nullptr;
+      return fail(PFLB_ERR_OOM, "device allocation failed (field output)");
+    }
+    L->dev_bytes += 6 * L->N * 8;
+  }
+  CK(L, do_macro(L, true));
+  CK(L, cudaMemcpyAsync(host_out, L->out + (size_t)field * L->N, (size_t)L->N * sizeof(double),
+                        cudaMemcpyDeviceToHost, L->stream));
+  CK(L, cudaStreamSynchronize(L->stream));
+  return PFLB_OK;
+}
+
+int64_t pflb_get_step(const pflb_lattice *L) { return L ? L->step : -1; }
+
+int64_t pflb_device_bytes(const pflb_lattice *L) { return L ? L->dev_bytes : 0; }
+
+int64_t pflb_estimate_bytes(const pflb_geometry *geom, int storage) {
+  if (!geom || !geom->solid || geom->nx < 1 || geom->ny < 1 || geom->nz < 1) return -1;
+  const long long N = (long long)geom->nx * geom->ny * geom->nz;
+  long long nw = 0;
+  for (long long c = 0; c < N; ++c) {
+    if (geom->solid[c]) continue;
+    const long long x = c % geom->nx, y = (c / geom->nx) % geom->ny,
+                    z = c / ((long long)geom->nx * geom->ny);
+    for (int i = 1; i < pflb::Q; ++i) {
+      long long xx = wrap(x + pflb::cx_of(i), geom->nx), yy = wrap(y + pflb::cy_of(i), geom->ny),
+                zz = wrap(z + pflb::cz_of(i), geom->nz);
+      if (geom->solid[xx + geom->nx * (yy + (long long)geom->ny * zz)]) { ++nw; break; }
+    }
+  }
+  return bytes_for(N, nw, storage);
+}
+
+static const char kMagic[8] = {'P', 'F', 'L', 'B', 'C', 'K', 'P', '1'};
+
+pflb_status pflb_save(pflb_lattice *L, const char *path) {
+  pflb_status s = check_lattice(L);
+  if (s != PFLB_OK) return s;
+  if (!path) return fail(PFLB_ERR_ARG, "null path");
+  const int rd = (int)(L->step & 1);
+  const size_t N = (size_t)L->N, nw = (size_t)L->nw, E = L->elem;
+  std::vector<char> buf;
+  const size_t sizes[4] = {19 * N * E, 19 * N * E, 18 * nw * E, 18 * nw * E};
+  const void *src[4] = {L->h[rd], L->g, L->wp[rd], L->ghost};
+  FILE *f = std::fopen(path, "wb");
+  if (!f) return fail(PFLB_ERR_ARG, std::string("cannot open ") + path);
+  int64_t hdr[6] = {L->nx, L->ny, L->nz, L->nw, L->p.storage, L->step};
+  bool ok = std::fwrite(kMagic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof hdr, 1, f) == 1;
+  for (int k = 0; k < 4 && ok; ++k) {
+    try {
+      buf.resize(sizes[k] ? sizes[k] : 1);
+    } catch (...) {
+      std::fclose(f);
+      return fail(PFLB_ERR_OOM, "host allocation failed");
+    }
+    cudaError_t e = cudaMemcpyAsync(buf.data(), src[k], sizes[k], cudaMemcpyDeviceToHost, L->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(L->stream);
+    if (e != cudaSuccess) {
+      std::fclose(f);
+      return cuda_fail(L, e, "checkpoint copy");
+    }
+    ok = std::fwrite(buf.data(), 1, sizes[k], f) == sizes[k];
+  }
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? PFLB_OK : fail(PFLB_ERR_ARG, "write failed");
+}
+
+pflb_status pflb_load(pflb_lattice *L, const char *path) {
+  pflb_status s = check_lattice(L);
+  if (s != PFLB_OK) return s;
+  if (!path) return fail(PFLB_ERR_ARG, "null path");
+  FILE *f = std::fopen(path, "rb");
+  if (!f) return fail(PFLB_ERR_ARG, std::string("cannot open ") + path);
+  char magic[8];
+  int64_t hdr[6];
+  if (std::fread(magic, 1, 8, f) != 8 || std::memcmp(magic, kMagic, 8) != 0 ||
+      std::fread(hdr, sizeof hdr, 1, f) != 1) {
+    std::fclose(f);
+    return fail(PFLB_ERR_ARG, "not a checkpoint");
+  }
+  if (hdr[0] != L->nx || hdr[1] != L->ny || hdr[2] != L->nz || hdr[3] != L->nw ||
+      hdr[4] != L->p.storage) {
+    std::fclose(f);
+    return fail(PFLB_ERR_ARG, "checkpoint geometry or storage differs");
+  }
+  L->step = hdr[5];
+  const int rd = (int)(L->step & 1);
+  const size_t N = (size_t)L->N, nw = (size_t)L->nw, E = L->elem;
+  const size_t sizes[4] = {19 * N * E, 19 * N * E, 18 * nw * E, 18 * nw * E};
+  void *dst[4] = {L->h[rd], L->g, L->wp[rd], L->ghost};
+  std::vector<char> buf;
+  for (int k = 0; k < 4; ++k) {
+    try {
+      buf.resize(sizes[k] ? sizes[k] : 1);
+    } catch (...) {
+      std::fclose(f);
+      return fail(PFLB_ERR_OOM, "host allocation failed");
+    }
+    if (std::fread(buf.data(), 1, sizes[k], f) != sizes[k]) {
+      std::fclose(f);
+      return fail(PFLB_ERR_ARG, "truncated checkpoint");
+    }
+    cudaError_t e = cudaMemcpyAsync(dst[k], buf.data(), sizes[k], cudaMemcpyHostToDevice, L->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(L->stream);
+    if (e != cudaSuccess) {
+      std::fclose(f);
+      return cuda_fail(L, e, "checkpoint upload");
+    }
+  }
+  std::fclose(f);
+  return PFLB_OK;
+}
+
+void pflb_destroy(pflb_lattice *L) {
+  if (!L) return;
+  cudaStreamSynchronize(L->stream);
+  free_all(L);
+  delete L;
+}
+
+const char *pflb_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

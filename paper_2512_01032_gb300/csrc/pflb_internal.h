@@ -1,0 +1,51 @@
+// pflb_internal.h -- host-side lattice record shared by the C ABI and the
+// per-precision launchers.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+
+#include "../../include/pflb.h"
+
+namespace pflb {
+
+struct Lattice {
+  int nx = 0, ny = 0, nz = 0;
+  long long N = 0;
+  int nw = 0;                 // wall nodes
+  pflb_params p{};
+  cudaStream_t stream = nullptr;
+  size_t elem = 4;            // bytes per stored population
+  // device buffers
+  void *h[2] = {nullptr, nullptr};  // [19][N] each
+  void *g = nullptr;                // [19][N]
+  void *wp[2] = {nullptr, nullptr}; // [18][nw] each
+  uint8_t *flags = nullptr;         // [N]
+  int *widx = nullptr;              // [N]
+  uint32_t *wmask = nullptr;        // [nw]
+  void *wgeo = nullptr;             // [5][nw] compute type
+  void *ghost = nullptr;            // [18][nw] compute type
+  void *phi = nullptr;              // [N] compute type (two-pass path)
+  double *diag = nullptr;           // [32]
+  double *out = nullptr;            // [6][N] lazily allocated
+  double *phi0 = nullptr;           // [N] init scratch, lazily allocated
+  int64_t step = 0;
+  int64_t ndiag = 0;          // diagnostic launches since init (ping-pong index)
+  int64_t last_diag_step = -1;
+  int diag_every = 0;         // pflb_step accumulates diagnostics every k-th step
+  int kernel = PFLB_KERNEL_FUSED;
+  int bx = 32, by = 8, lz = 16;
+  int reg[6] = {0, 0, 0, 0, 0, 0};
+  bool poisoned = false;
+  int64_t dev_bytes = 0;
+};
+
+// Per-precision launchers (pflb_launch.cuh, instantiated per storage type).
+// All enqueue work on L.stream; none synchronises.
+template <class S, class R> cudaError_t launch_init(Lattice &L, const double *d_phi0, double P0);
+template <class S, class R> cudaError_t launch_step(Lattice &L, bool diag);
+template <class S, class R> cudaError_t launch_macro(Lattice &L, bool fields);
+template <class S, class R> cudaError_t set_model(Lattice &L);
+template <class S, class R> int max_block_threads();
+
+}  // namespace pflb

@@ -1,0 +1,158 @@
+// pflb_launch.cuh -- per-precision kernel launchers (included by one
+// translation unit per storage type).
+#pragma once
+#include "pflb_internal.h"
+#include "pflb_kernels.cuh"
+
+namespace pflb {
+
+template <class R>
+static Model<R> make_model(const pflb_params &p) {
+  const double T = 1.0 / 3.0;
+  Model<R> m;
+  m.sigma = (R)p.sigma;
+  m.W = (R)p.W;
+  m.M = (R)p.M;
+  m.rho_L = (R)p.rho_L;
+  m.rho_dif = (R)(p.rho_H - p.rho_L);
+  m.tau_H = (R)(p.nu_H / T + 0.5);
+  m.tau_L = (R)(p.nu_L / T + 0.5);
+  m.Fx = (R)p.Fex[0];
+  m.Fy = (R)p.Fex[1];
+  m.Fz = (R)p.Fex[2];
+  m.gamma = (R)p.gamma;
+  m.phi_M = (R)p.phi_M;
+  m.phi_m = (R)p.phi_m;
+  m.inv_D = (R)(1.0 / p.D);
+  m.eps = (R)p.eps;
+  m.blend = (R)p.blend;
+  m.band_lo = (R)p.band_lo;
+  m.band_hi = (R)p.band_hi;
+  m.F_tilde = (R)p.F_tilde;
+  m.inv_F_width = (R)(1.0 / p.F_width);
+  m.inv_tau_phi = (R)(1.0 / (p.M / T + 0.5));
+  m.theta_coef = (R)(p.M / (T * p.W));
+  m.mu_a = (R)(48.0 * p.sigma / p.W);
+  m.mu_b = (R)(1.5 * p.sigma * p.W);
+  m.two_over_W = (R)(2.0 / p.W);
+  m.F_mode = p.F_mode;
+  m.mobility_corr = p.mobility_corr;
+  m.free_slip = p.free_slip;
+  return m;
+}
+
+template <class S, class R>
+static Args<S, R> make_args(Lattice &L) {
+  Args<S, R> a;
+  a.nx = L.nx; a.ny = L.ny; a.nz = L.nz; a.lz = L.lz;
+  a.N = L.N;
+  a.nw = L.nw;
+  const int rd = (int)(L.step & 1);
+  a.hin = (const S *)L.h[rd];
+  a.hout = (S *)L.h[rd ^ 1];
+  a.g = (S *)L.g;
+  a.flags = L.flags;
+  a.widx = L.widx;
+  a.wmask = L.wmask;
+  a.wgeo = (const R *)L.wgeo;
+  a.ghost = (R *)L.ghost;
+  a.wp_rd = (const S *)L.wp[rd];
+  a.wp_wr = (S *)L.wp[rd ^ 1];
+  a.phi = (const R *)L.phi;
+  a.m = make_model<R>(L.p);
+  a.diag = nullptr;
+  a.diag_zero = nullptr;
+  for (int k = 0; k < 6; ++k) a.reg[k] = L.reg[k];
+  a.out = nullptr;
+  return a;
+}
+
+template <class S, class R>
+cudaError_t set_model(Lattice &) { return cudaSuccess; }
+
+template <class S, class R>
+int max_block_threads() { return 256; }
+
+template <class S, class R>
+cudaError_t launch_init(Lattice &L, const double *d_phi0, double P0) {
+  L.step = 0;
+  L.ndiag = 0;
+  L.last_diag_step = -1;
+  Args<S, R> a = make_args<S, R>(L);
+  cudaError_t e = cudaMemsetAsync(L.diag, 0, 96 * sizeof(double), L.stream);
+  if (e != cudaSuccess) return e;
+  const int T = 256;
+  const long long B = (L.N + T - 1) / T;
+  k_init<S, R><<<(unsigned)B, T, 0, L.stream>>>(a, d_phi0, P0, (S *)L.h[0], (S *)L.wp[0]);
+  return cudaGetLastError();
+}
+
+template <class S, class R, bool ODD, bool DIAG>
+static cudaError_t launch_fused_t(Lattice &L, Args<S, R> &a) {
+  const int bx = L.bx, by = L.by;
+  dim3 grid((L.nx + bx - 1) / bx, (L.ny + by - 1) / by, (L.nz + L.lz - 1) / L.lz);
+  const size_t smem = 3 * (size_t)(bx + 2) * (by + 2) * sizeof(R);
+  k_fused<S, R, ODD, DIAG><<<grid, bx * by, smem, L.stream>>>(a, bx, by);
+  return cudaGetLastError();
+}
+
+template <class S, class R, bool ODD, int MODE, bool DIAG>
+static cudaError_t launch_cell_t(Lattice &L, Args<S, R> &a) {
+  const int T = 256;
+  const long long B = (L.N + T - 1) / T;
+  k_phi<S, R><<<(unsigned)B, T, 0, L.stream>>>(a, (R *)L.phi);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_cell<S, R, ODD, MODE, DIAG><<<(unsigned)B, T, 0, L.stream>>>(a);
+  return cudaGetLastError();
+}
+
+template <class S, class R>
+cudaError_t launch_step(Lattice &L, bool diag) {
+  Args<S, R> a = make_args<S, R>(L);
+  const bool odd = (L.step & 1) != 0;
+  cudaError_t e;
+  if (diag) {
+    // Diagnostic launch d accumulates into buffer d&1 and zeroes the other.
+    a.diag = L.diag + 32 * (L.ndiag & 1);
+    a.diag_zero = L.diag + 32 * ((L.ndiag + 1) & 1);
+  }
+  if (L.kernel == PFLB_KERNEL_FUSED) {
+    if (odd) e = diag ? launch_fused_t<S, R, true, true>(L, a) : launch_fused_t<S, R, true, false>(L, a);
+    else e = diag ? launch_fused_t<S, R, false, true>(L, a) : launch_fused_t<S, R, false, false>(L, a);
+  } else {
+    if (odd) e = diag ? launch_cell_t<S, R, true, MODE_STEP, true>(L, a)
+                      : launch_cell_t<S, R, true, MODE_STEP, false>(L, a);
+    else e = diag ? launch_cell_t<S, R, false, MODE_STEP, true>(L, a)
+                  : launch_cell_t<S, R, false, MODE_STEP, false>(L, a);
+  }
+  if (e == cudaSuccess) {
+    if (diag) {
+      L.last_diag_step = L.step;
+      L.ndiag++;
+    }
+    L.step++;
+  }
+  return e;
+}
+
+template <class S, class R>
+cudaError_t launch_macro(Lattice &L, bool fields) {
+  Args<S, R> a = make_args<S, R>(L);
+  a.out = fields ? L.out : nullptr;
+  a.diag = L.diag + 64;
+  a.diag_zero = nullptr;
+  cudaError_t e = cudaMemsetAsync(a.diag, 0, 32 * sizeof(double), L.stream);
+  if (e != cudaSuccess) return e;
+  if (L.step & 1) return launch_cell_t<S, R, true, MODE_MACRO, true>(L, a);
+  return launch_cell_t<S, R, false, MODE_MACRO, true>(L, a);
+}
+
+#define PFLB_INSTANTIATE(S, R)                                                   \
+  template cudaError_t launch_init<S, R>(Lattice &, const double *, double);     \
+  template cudaError_t launch_step<S, R>(Lattice &, bool);                       \
+  template cudaError_t launch_macro<S, R>(Lattice &, bool);                      \
+  template cudaError_t set_model<S, R>(Lattice &);                               \
+  template int max_block_threads<S, R>();
+
+}  // namespace pflb

@@ -1,0 +1,291 @@
+// pflb_model.cuh -- per-cell arithmetic of the conservative Allen-Cahn
+// phase-field lattice Boltzmann step (D3Q19), device side.
+//
+// Sources (arXiv 2512.01032):
+//   Eq. 1     h_i relaxation with tau_phi = M/T + 1/2
+//   Eqs. 2-3  h equilibrium phi*Gamma_i + theta*w_i*(c_i . n), Gamma_i
+//   Eq. 4     local mobility correction delta-theta
+//   Eqs. 5-6  hydrodynamic equilibrium and force K_i
+//   Eq. 7     chemical potential
+//   Eq. 8     tau_mix; optimised F(phi) of Sec. III A
+//   Eqs. 9-11 filtered collision (Hermite second-order filter)
+//   text after Eq. 11: P and rho*u recovery
+//   Eq. 13    central-difference gradient and Laplacian
+//   Eqs. 12-15 wettability ghosts; Sec. III A blend and free-slip band
+//
+// Populations: h = phase field, g = hydrodynamic (the paper's g-bar).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pflb {
+
+constexpr int Q = 19;
+
+// D3Q19: rest, +-x, +-y, +-z, then twelve edge directions in opposite pairs.
+__host__ __device__ constexpr int cx_of(int i) {
+  constexpr int t[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+  return t[i];
+}
+__host__ __device__ constexpr int cy_of(int i) {
+  constexpr int t[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+  return t[i];
+}
+__host__ __device__ constexpr int cz_of(int i) {
+  constexpr int t[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+  return t[i];
+}
+__host__ __device__ constexpr int opp_of(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+__host__ __device__ constexpr double w_of(int i) {
+  return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+// Direction index of a velocity vector (-1 if not in the set).
+__host__ __device__ constexpr int dir_of(int x, int y, int z) {
+  for (int i = 0; i < Q; ++i)
+    if (cx_of(i) == x && cy_of(i) == y && cz_of(i) == z) return i;
+  return -1;
+}
+
+// Specular-reflection data of edge link i (two nonzero components on axes
+// a < b).  fa/fb: face directions along c_ia e_a and c_ib e_b.  If the face
+// neighbour fa is solid and fb fluid, the wall lies across axis a: the
+// tangential partner is x + e(fb) and the reflected direction is ra.
+// Symmetrically for fb solid / fa fluid with rb.
+struct EdgeInfo { int fa, fb, ra, rb; };
+__host__ __device__ constexpr EdgeInfo edge_info(int i) {
+  int c[3] = {cx_of(i), cy_of(i), cz_of(i)};
+  int a = -1, b = -1;
+  for (int k = 0; k < 3; ++k)
+    if (c[k] != 0) { if (a < 0) a = k; else b = k; }
+  if (b < 0) return EdgeInfo{-1, -1, -1, -1};
+  int ea[3] = {0, 0, 0}, eb[3] = {0, 0, 0};
+  ea[a] = c[a];
+  eb[b] = c[b];
+  int fa = dir_of(ea[0], ea[1], ea[2]);
+  int fb = dir_of(eb[0], eb[1], eb[2]);
+  int r1[3] = {c[0], c[1], c[2]};
+  r1[a] = -r1[a];
+  int r2[3] = {c[0], c[1], c[2]};
+  r2[b] = -r2[b];
+  return EdgeInfo{fa, fb, dir_of(r1[0], r1[1], r1[2]), dir_of(r2[0], r2[1], r2[2])};
+}
+
+// Diagnostic accumulator slots (double, device).
+enum {
+  D_MASS = 0, D_NHEAVY, D_PH, D_NPH, D_PL, D_NPL, D_REGION, D_CLN, D_CLX, D_CLY, D_CLZ,
+  D_CLXX, D_CLYY, D_CLZZ, D_KIN, D_NONFINITE, D_UMAX, D_COUNT
+};
+
+// Cell flags.
+constexpr uint8_t F_SOLID = 1;
+constexpr uint8_t F_WALL = 2;
+
+// Model parameters in the compute precision R (derived constants included).
+template <class R>
+struct Model {
+  R sigma, W, M, rho_L, rho_dif;
+  R tau_H, tau_L;
+  R Fx, Fy, Fz;
+  R gamma, phi_M, phi_m, inv_D, eps, blend, band_lo, band_hi, F_tilde, inv_F_width;
+  R inv_tau_phi;       // 1 / (M/T + 1/2)
+  R theta_coef;        // M / (T W)
+  R mu_a, mu_b;        // 48 sigma / W, 3 sigma W / 2
+  R two_over_W;        // 2 / W
+  int F_mode, mobility_corr, free_slip;
+};
+
+// ------------------------------------------------------------ storage
+// Population storage types: the collision always runs in R.
+template <class S> struct Store;
+template <> struct Store<double> {
+  static __device__ __forceinline__ double ld(const double *p) { return *p; }
+  static __device__ __forceinline__ void st(double *p, double v) { *p = v; }
+};
+template <> struct Store<float> {
+  static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
+  static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
+};
+
+template <class R> __device__ __forceinline__ R rsqrt_(R x);
+template <> __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+template <> __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+template <class R> __device__ __forceinline__ R sqrt_(R x);
+template <> __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+template <> __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+template <class R> __device__ __forceinline__ R tanh_(R x);
+template <> __device__ __forceinline__ double tanh_(double x) { return tanh(x); }
+template <> __device__ __forceinline__ float tanh_(float x) { return tanhf(x); }
+template <class R> __device__ __forceinline__ R abs_(R x);
+template <> __device__ __forceinline__ double abs_(double x) { return fabs(x); }
+template <> __device__ __forceinline__ float abs_(float x) { return fabsf(x); }
+template <class R> __device__ __forceinline__ R clamp01_(R x) {
+  return x < R(0) ? R(0) : (x > R(1) ? R(1) : x);
+}
+template <class R> __device__ __forceinline__ R fminf_(R a, R b) { return a < b ? a : b; }
+
+// ------------------------------------------------------------ stencil
+// Eq. 13 written with both halves of each opposite pair merged:
+// grad = (1/T) sum_i w_i c_i v_i,  lap = (2/T) sum_i w_i (v_i - v_0).
+template <class R>
+__device__ __forceinline__ void cd_stencil(const R v[Q], R &gx, R &gy, R &gz, R &lap) {
+  const R a = R(1.0 / 18.0) * R(3.0), b = R(1.0 / 36.0) * R(3.0);
+  gx = a * (v[1] - v[2]) + b * ((v[7] - v[8]) + (v[9] - v[10]) + (v[11] - v[12]) + (v[13] - v[14]));
+  gy = a * (v[3] - v[4]) + b * ((v[7] - v[8]) - (v[9] - v[10]) + (v[15] - v[16]) + (v[17] - v[18]));
+  gz = a * (v[5] - v[6]) + b * ((v[11] - v[12]) - (v[13] - v[14]) + (v[15] - v[16]) - (v[17] - v[18]));
+  R sf = (v[1] + v[2]) + (v[3] + v[4]) + (v[5] + v[6]);
+  R se = ((v[7] + v[8]) + (v[9] + v[10])) + ((v[11] + v[12]) + (v[13] + v[14])) +
+         ((v[15] + v[16]) + (v[17] + v[18]));
+  lap = R(6.0) * (R(1.0 / 18.0) * sf + R(1.0 / 36.0) * se - R(2.0 / 3.0) * v[0]);
+}
+
+// ------------------------------------------------------------ wetting
+// Ghost values of Eqs. 14-15 with the hysteresis blend of Sec. III A.
+// The tanh of a sum is evaluated through tanh(a + b) = (s + tb)/(1 + s tb)
+// with s = tanh(a) = 2 phi - 1 (clamped to [-1, 1]) and tb = tanh(2 d_i/W),
+// which is algebraically identical to the artanh form and needs no artanh.
+// In: old ghosts in val[i] for solid links, grad from those values.
+// Out: val[i] <- new ghost for each solid link (also returned in gnew).
+template <class R>
+__device__ __forceinline__ void wall_ghosts(const Model<R> &m, R phi, R gx, R gy, R gz, R nwx,
+                                            R nwy, R nwz, R cth, R sth, uint32_t links,
+                                            R val[Q]) {
+  R gn = gx * nwx + gy * nwy + gz * nwz;
+  R tx = gx - gn * nwx, ty = gy - gn * nwy, tz = gz - gn * nwz;
+  R tn2 = tx * tx + ty * ty + tz * tz;
+  R inv = tn2 >= R(1e-20) ? R(1) / sqrt_(tn2) : R(0);
+  tx *= inv; ty *= inv; tz *= inv;
+  R wx = -cth * nwx + sth * tx, wy = -cth * nwy + sth * ty, wz = -cth * nwz + sth * tz;
+  R s = R(2) * phi - R(1);
+  s = s > R(1) ? R(1) : (s < R(-1) ? R(-1) : s);
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    if (!((links >> i) & 1u)) continue;
+    R d = wx * R(cx_of(i)) + wy * R(cy_of(i)) + wz * R(cz_of(i));
+    R tb = tanh_(m.two_over_W * d);
+    R fresh = R(0.5) * (R(1) + (s + tb) / (R(1) + s * tb));
+    val[i] = m.blend * val[i] + (R(1) - m.blend) * fresh;
+  }
+}
+
+// ------------------------------------------------------------ macros
+template <class R>
+struct Macro {
+  R rho, P, ux, uy, uz, mu;
+};
+
+// Chemical potential (Eq. 7), rho, velocity and pressure recovery.
+template <class R>
+__device__ __forceinline__ Macro<R> macros(const Model<R> &m, const R g[Q], R phi, R gx, R gy,
+                                           R gz, R lap) {
+  Macro<R> r;
+  r.rho = m.rho_L + phi * m.rho_dif;
+  r.mu = m.mu_a * phi * (phi - R(1)) * (phi - R(0.5)) - m.mu_b * lap;
+  R s = R(0), jx, jy, jz;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) s += g[i];
+  jx = (g[1] - g[2]) + ((g[7] - g[8]) + (g[9] - g[10])) + ((g[11] - g[12]) + (g[13] - g[14]));
+  jy = (g[3] - g[4]) + ((g[7] - g[8]) - (g[9] - g[10])) + ((g[15] - g[16]) + (g[17] - g[18]));
+  jz = (g[5] - g[6]) + ((g[11] - g[12]) - (g[13] - g[14])) + ((g[15] - g[16]) - (g[17] - g[18]));
+  R irho = R(1) / r.rho;
+  r.ux = (jx + R(0.5) * (r.mu * gx + m.Fx)) * irho;
+  r.uy = (jy + R(0.5) * (r.mu * gy + m.Fy)) * irho;
+  r.uz = (jz + R(0.5) * (r.mu * gz + m.Fz)) * irho;
+  R ug = r.ux * gx + r.uy * gy + r.uz * gz;
+  r.P = R(1.0 / 3.0) * s + R(0.5 / 3.0) * m.rho_dif * ug;
+  return r;
+}
+
+template <class R>
+__device__ __forceinline__ R tau_mix(const Model<R> &m, R phi) {
+  R F = phi;
+  if (m.F_mode == 1) F = R(0.5) * (tanh_((phi - m.F_tilde) * m.inv_F_width) + R(1));
+  return (R(1) - F) * m.tau_L + F * m.tau_H;
+}
+
+// Local mobility correction (Eq. 4).
+template <class R>
+__device__ __forceinline__ R delta_theta(const Model<R> &m, R phi, R gnorm, R lap) {
+  R Y1 = fminf_(clamp01_((phi - m.phi_M) * m.inv_D), clamp01_((R(1) - phi) * m.inv_D));
+  R Y2 = fminf_(clamp01_(phi * m.inv_D), clamp01_((m.phi_m - phi) * m.inv_D));
+  R s = lap / abs_(lap + m.eps);
+  return m.gamma * m.theta_coef * gnorm * ((R(1) + s) * Y1 + (R(1) - s) * Y2);
+}
+
+// h collision (Eqs. 1-4): in place on h[].
+template <class R>
+__device__ __forceinline__ void collide_h(const Model<R> &m, R h[Q], R phi, R gx, R gy, R gz,
+                                          R lap, R ux, R uy, R uz) {
+  R gn2 = gx * gx + gy * gy + gz * gz;
+  R gnorm = sqrt_(gn2);
+  R inv = R(1) / (gnorm + m.eps);
+  R nx = gx * inv, ny = gy * inv, nz = gz * inv;
+  R th = m.theta_coef * (R(1) - R(4) * (phi - R(0.5)) * (phi - R(0.5)));
+  if (m.mobility_corr) th += delta_theta(m, phi, gnorm, lap);
+  const R uu15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
+  const R om = m.inv_tau_phi;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const R cu = R(cx_of(i)) * ux + R(cy_of(i)) * uy + R(cz_of(i)) * uz;
+    const R cn = R(cx_of(i)) * nx + R(cy_of(i)) * ny + R(cz_of(i)) * nz;
+    const R wi = R(w_of(i));
+    const R G = wi * (R(1) + R(3) * cu + R(4.5) * cu * cu - uu15);
+    const R heq = phi * G + th * wi * cn;
+    h[i] = h[i] - om * (h[i] - heq);
+  }
+}
+
+// Filtered hydrodynamic collision (Eqs. 5-11, reading: G_eq = E + K/2,
+// Pi = sum c c (g - g_eq)), in place on g[].
+template <class R>
+__device__ __forceinline__ void collide_g(const Model<R> &m, R g[Q], const Macro<R> &mc, R phi,
+                                          R gx, R gy, R gz) {
+  const R ux = mc.ux, uy = mc.uy, uz = mc.uz;
+  const R uu15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
+  const R ug = ux * gx + uy * gy + uz * gz;
+  const R uF = ux * m.Fx + uy * m.Fy + uz * m.Fz;
+  const R muT = R(3) * mc.mu;  // mu / T
+  const R P3 = R(3) * mc.P;    // P / T
+  R pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
+  // First pass: E_i + K_i/2 into g_out, and the non-equilibrium moments.
+  R base[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const R c0 = R(cx_of(i)), c1 = R(cy_of(i)), c2 = R(cz_of(i));
+    const R wi = R(w_of(i));
+    const R cu = c0 * ux + c1 * uy + c2 * uz;
+    const R G = wi * (R(1) + R(3) * cu + R(4.5) * cu * cu - uu15);
+    const R cg = c0 * gx + c1 * gy + c2 * gz - ug;         // (c - u) . grad phi
+    const R cF = c0 * m.Fx + c1 * m.Fy + c2 * m.Fz - uF;   // (c - u) . F
+    const R K = ((G - wi) * m.rho_dif + G * muT) * cg + R(3) * G * cF;
+    const R E = mc.rho * G + wi * (P3 - mc.rho);
+    const R neq = g[i] - E + R(0.5) * K;
+    base[i] = E + R(0.5) * K;
+    if (cx_of(i)) pxx += neq;
+    if (cy_of(i)) pyy += neq;
+    if (cz_of(i)) pzz += neq;
+    if (cx_of(i) * cy_of(i) > 0) pxy += neq;
+    if (cx_of(i) * cy_of(i) < 0) pxy -= neq;
+    if (cx_of(i) * cz_of(i) > 0) pxz += neq;
+    if (cx_of(i) * cz_of(i) < 0) pxz -= neq;
+    if (cy_of(i) * cz_of(i) > 0) pyz += neq;
+    if (cy_of(i) * cz_of(i) < 0) pyz -= neq;
+  }
+  // Phi_i : Pi = w_i / (2 T^2) (c_i c_i : Pi - T tr Pi)
+  const R tau = tau_mix(m, phi);
+  const R f = (R(1) - R(1) / tau) * R(4.5);
+  const R tr3 = (pxx + pyy + pzz) * R(1.0 / 3.0);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int c0 = cx_of(i), c1 = cy_of(i), c2 = cz_of(i);
+    R cc = R(0);
+    if (c0) cc += pxx;
+    if (c1) cc += pyy;
+    if (c2) cc += pzz;
+    if (c0 * c1) cc += R(2 * c0 * c1) * pxy;
+    if (c0 * c2) cc += R(2 * c0 * c2) * pxz;
+    if (c1 * c2) cc += R(2 * c1 * c2) * pyz;
+    g[i] = base[i] + f * R(w_of(i)) * (cc - tr3);
+  }
+}
+
+}  // namespace pflb

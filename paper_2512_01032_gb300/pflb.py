@@ -1,0 +1,293 @@
+"""Thin ctypes binding of the C ABI in ``include/pflb.h``.
+
+Argument marshalling only: every step of the path runs in the CUDA library.
+The names follow the C functions (``pflb_create`` -> ``create`` and so on).
+``Lattice`` is a small owner object around the opaque handle.  Streams may
+be given as a ``torch.cuda.Stream`` or a raw ``cudaStream_t`` integer.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_P = C.POINTER
+_d = _P(C.c_double)
+
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NAN, ERR_TIMEOUT, ERR_BUDGET, ERR_STATE = range(8)
+STORAGE_FP64, STORAGE_FP32 = 0, 1
+FIELD_PHI, FIELD_RHO, FIELD_P, FIELD_UX, FIELD_UY, FIELD_UZ = range(6)
+FIELDS = {"phi": 0, "rho": 1, "P": 2, "ux": 3, "uy": 4, "uz": 5}
+KERNEL_FUSED, KERNEL_TWOPASS = 0, 1
+
+STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NAN",
+                5: "ERR_TIMEOUT", 6: "ERR_BUDGET", 7: "ERR_STATE"}
+
+
+class PflbError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Geometry(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("solid", _P(C.c_uint8)), ("wall_normal", _d), ("theta_deg", _d)]
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("sigma", C.c_double), ("W", C.c_double), ("M", C.c_double), ("rho_H", C.c_double),
+        ("rho_L", C.c_double), ("nu_H", C.c_double), ("nu_L", C.c_double),
+        ("theta_deg", C.c_double), ("Fex", C.c_double * 3),
+        ("gamma", C.c_double), ("phi_M", C.c_double), ("phi_m", C.c_double), ("D", C.c_double),
+        ("eps", C.c_double), ("blend", C.c_double), ("band_lo", C.c_double),
+        ("band_hi", C.c_double), ("F_tilde", C.c_double), ("F_width", C.c_double),
+        ("F_mode", C.c_int), ("mobility_corr", C.c_int), ("free_slip", C.c_int),
+        ("storage", C.c_int),
+    ]
+
+
+class Diag(C.Structure):
+    _fields_ = [
+        ("step", C.c_int64), ("mass", C.c_double), ("n_heavy", C.c_double),
+        ("p_heavy", C.c_double), ("p_light", C.c_double), ("n_p_heavy", C.c_double),
+        ("n_p_light", C.c_double), ("dp", C.c_double), ("u_max", C.c_double),
+        ("region_mass", C.c_double), ("cl_count", C.c_double), ("cl_mean", C.c_double * 3),
+        ("cl_m2", C.c_double * 3), ("kinetic", C.c_double), ("nonfinite", C.c_double),
+    ]
+
+    def as_dict(self):
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if isinstance(v, C.Array) else v
+        return out
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load ``libpflb.so`` (building it when missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path}")
+    lib = C.CDLL(path)
+    st = C.c_int
+    lib.pflb_default_params.argtypes = [_P(Params)]
+    lib.pflb_default_params.restype = None
+    lib.pflb_create.argtypes = [_P(Geometry), _P(Params), C.c_void_p, _P(C.c_void_p)]
+    lib.pflb_create.restype = st
+    lib.pflb_init_tanh.argtypes = [C.c_void_p, C.c_int, _d, C.c_double, _d, C.c_double]
+    lib.pflb_init_tanh.restype = st
+    lib.pflb_init_phi.argtypes = [C.c_void_p, _d, C.c_double]
+    lib.pflb_init_phi.restype = st
+    lib.pflb_set_force.argtypes = [C.c_void_p, _d]
+    lib.pflb_set_force.restype = st
+    lib.pflb_set_region.argtypes = [C.c_void_p, _P(C.c_int)]
+    lib.pflb_set_region.restype = st
+    lib.pflb_set_kernel.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]
+    lib.pflb_set_kernel.restype = st
+    lib.pflb_step.argtypes = [C.c_void_p, C.c_int64]
+    lib.pflb_step.restype = st
+    lib.pflb_step_diag.argtypes = [C.c_void_p, C.c_int64, _P(Diag)]
+    lib.pflb_step_diag.restype = st
+    lib.pflb_set_diag_every.argtypes = [C.c_void_p, C.c_int]
+    lib.pflb_set_diag_every.restype = st
+    lib.pflb_last_diag.argtypes = [C.c_void_p, _P(Diag)]
+    lib.pflb_last_diag.restype = st
+    lib.pflb_read.argtypes = [C.c_void_p, C.c_int, _d]
+    lib.pflb_read.restype = st
+    lib.pflb_diag.argtypes = [C.c_void_p, _P(Diag)]
+    lib.pflb_diag.restype = st
+    lib.pflb_get_step.argtypes = [C.c_void_p]
+    lib.pflb_get_step.restype = C.c_int64
+    lib.pflb_device_bytes.argtypes = [C.c_void_p]
+    lib.pflb_device_bytes.restype = C.c_int64
+    lib.pflb_estimate_bytes.argtypes = [_P(Geometry), C.c_int]
+    lib.pflb_estimate_bytes.restype = C.c_int64
+    lib.pflb_save.argtypes = [C.c_void_p, C.c_char_p]
+    lib.pflb_save.restype = st
+    lib.pflb_load.argtypes = [C.c_void_p, C.c_char_p]
+    lib.pflb_load.restype = st
+    lib.pflb_destroy.argtypes = [C.c_void_p]
+    lib.pflb_destroy.restype = None
+    lib.pflb_last_error.argtypes = []
+    lib.pflb_last_error.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != OK:
+        msg = load().pflb_last_error().decode(errors="replace")
+        raise PflbError(status, msg)
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    load().pflb_default_params(C.byref(p))
+    for k, v in kw.items():
+        if k == "Fex":
+            for a in range(3):
+                p.Fex[a] = float(v[a])
+        elif k == "storage" and isinstance(v, str):
+            p.storage = {"fp64": STORAGE_FP64, "fp32": STORAGE_FP32}[v]
+        elif hasattr(p, k):
+            setattr(p, k, v)
+        else:
+            raise KeyError(f"unknown parameter {k}")
+    return p
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def make_geometry(nx, ny, nz, solid=None, wall_normal=None, theta_cells=None):
+    """Build a ``Geometry`` struct plus the numpy arrays it points into."""
+    N = int(nx) * int(ny) * int(nz)
+    s = np.zeros(N, np.uint8) if solid is None else np.ascontiguousarray(
+        np.asarray(solid, np.uint8).reshape(-1))
+    if s.size != N:
+        raise ValueError("solid mask has the wrong size")
+    nw = None if wall_normal is None else _f64(wall_normal).reshape(-1)
+    th = None if theta_cells is None else _f64(theta_cells).reshape(-1)
+    if nw is not None and nw.size != 3 * N:
+        raise ValueError("wall_normal must hold 3 values per cell")
+    if th is not None and th.size != N:
+        raise ValueError("theta_cells must hold one value per cell")
+    g = Geometry(int(nx), int(ny), int(nz), s.ctypes.data_as(_P(C.c_uint8)),
+                 nw.ctypes.data_as(_d) if nw is not None else None,
+                 th.ctypes.data_as(_d) if th is not None else None)
+    return g, (s, nw, th)
+
+
+def estimate_bytes(nx, ny, nz, solid=None, storage=STORAGE_FP32) -> int:
+    g, keep = make_geometry(nx, ny, nz, solid)
+    return int(load().pflb_estimate_bytes(C.byref(g), int(storage)))
+
+
+class Lattice:
+    """Owner of one ``pflb_lattice`` handle."""
+
+    def __init__(self, nx, ny, nz, solid=None, wall_normal=None, theta_cells=None, stream=None,
+                 params: Params | None = None, **kw):
+        lib = load()
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.N = self.nx * self.ny * self.nz
+        self.params = params if params is not None else default_params(**kw)
+        geom, keep = make_geometry(nx, ny, nz, solid, wall_normal, theta_cells)
+        self._stream = stream
+        h = C.c_void_p()
+        _check(lib.pflb_create(C.byref(geom), C.byref(self.params),
+                               C.c_void_p(_stream_handle(stream)), C.byref(h)))
+        self._h = h
+        self._lib = lib
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.pflb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- calls
+    def init_tanh(self, shape=0, center=(0, 0, 0), R=0.0, normal=None, P0=0.0):
+        c = _f64(center)
+        n = _f64(normal) if normal is not None else None
+        _check(self._lib.pflb_init_tanh(self._h, int(shape), c.ctypes.data_as(_d), float(R),
+                                        n.ctypes.data_as(_d) if n is not None else None,
+                                        float(P0)))
+
+    def init_phi(self, phi, P0=0.0):
+        a = _f64(phi).reshape(-1)
+        if a.size != self.N:
+            raise ValueError("phi has the wrong size")
+        _check(self._lib.pflb_init_phi(self._h, a.ctypes.data_as(_d), float(P0)))
+
+    def set_force(self, F):
+        f = _f64(F)
+        _check(self._lib.pflb_set_force(self._h, f.ctypes.data_as(_d)))
+
+    def set_region(self, box):
+        b = (C.c_int * 6)(*[int(v) for v in box])
+        _check(self._lib.pflb_set_region(self._h, b))
+
+    def set_kernel(self, kind=KERNEL_FUSED, bx=0, by=0, lz=0):
+        _check(self._lib.pflb_set_kernel(self._h, int(kind), int(bx), int(by), int(lz)))
+
+    def step(self, n=1):
+        _check(self._lib.pflb_step(self._h, int(n)))
+
+    def step_diag(self, n=1) -> dict:
+        d = Diag()
+        _check(self._lib.pflb_step_diag(self._h, int(n), C.byref(d)))
+        return d.as_dict()
+
+    def set_diag_every(self, k: int):
+        _check(self._lib.pflb_set_diag_every(self._h, int(k)))
+
+    def last_diag(self, allow_nan=False) -> dict:
+        d = Diag()
+        s = self._lib.pflb_last_diag(self._h, C.byref(d))
+        if s != OK and not (allow_nan and s == ERR_NAN):
+            _check(s)
+        return d.as_dict()
+
+    def read(self, field) -> np.ndarray:
+        f = FIELDS[field] if isinstance(field, str) else int(field)
+        out = np.empty(self.N, np.float64)
+        _check(self._lib.pflb_read(self._h, f, out.ctypes.data_as(_d)))
+        return out
+
+    def read_all(self) -> dict:
+        return {k: self.read(k) for k in FIELDS}
+
+    def diag(self, allow_nan=False) -> dict:
+        d = Diag()
+        s = self._lib.pflb_diag(self._h, C.byref(d))
+        if s != OK and not (allow_nan and s == ERR_NAN):
+            _check(s)
+        return d.as_dict()
+
+    @property
+    def t(self) -> int:
+        return int(self._lib.pflb_get_step(self._h))
+
+    def device_bytes(self) -> int:
+        return int(self._lib.pflb_device_bytes(self._h))
+
+    def save(self, path):
+        _check(self._lib.pflb_save(self._h, os.fsencode(path)))
+
+    def load(self, path):
+        _check(self._lib.pflb_load(self._h, os.fsencode(path)))

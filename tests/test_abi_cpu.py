@@ -1,0 +1,115 @@
+"""C ABI checks that need no GPU: the library builds and exports every
+function declared in include/pflb.h, the ctypes structs match the C layout,
+and argument validation rejects bad input before any device work."""
+import json
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pflb.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(pflb_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2512_01032_gb300 import pflb
+    pflb.load()
+    out = subprocess.run(["nm", "-D", "--defined-only", pflb.lib_path()], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (pflb_\w+)", out))
+    missing = [s for s in _declared() if s not in exported]
+    assert not missing, missing
+    assert len(_declared()) >= 18
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """sizeof/offsetof of the C structs equal the ctypes mirrors."""
+    import ctypes as C
+    from paper_2512_01032_gb300 import pflb
+    src = tmp_path / "layout.c"
+    src.write_text(r'''
+#include <stddef.h>
+#include <stdio.h>
+#include "pflb.h"
+int main(void) {
+  printf("{\"params\": %zu, \"geom\": %zu, \"diag\": %zu, "
+         "\"storage\": %zu, \"Fex\": %zu, \"nonfinite\": %zu, \"cl_m2\": %zu}\n",
+         sizeof(pflb_params), sizeof(pflb_geometry), sizeof(pflb_diag_t),
+         offsetof(pflb_params, storage), offsetof(pflb_params, Fex),
+         offsetof(pflb_diag_t, nonfinite), offsetof(pflb_diag_t, cl_m2));
+  return 0;
+}
+''')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = json.loads(subprocess.run([str(exe)], capture_output=True, text=True,
+                                    check=True).stdout)
+    assert got["params"] == C.sizeof(pflb.Params)
+    assert got["geom"] == C.sizeof(pflb.Geometry)
+    assert got["diag"] == C.sizeof(pflb.Diag)
+    assert got["storage"] == pflb.Params.storage.offset
+    assert got["Fex"] == pflb.Params.Fex.offset
+    assert got["nonfinite"] == pflb.Diag.nonfinite.offset
+    assert got["cl_m2"] == pflb.Diag.cl_m2.offset
+
+
+def test_default_params_are_the_papers():
+    from paper_2512_01032_gb300 import pflb
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_constants.json")))
+    p = pflb.default_params()
+    for k, attr in (("gamma", "gamma"), ("phi_M", "phi_M"), ("phi_m", "phi_m"), ("D", "D"),
+                    ("eps_dtheta", "eps"), ("blend", "blend"), ("band_lo", "band_lo"),
+                    ("band_hi", "band_hi"), ("F_tilde", "F_tilde"), ("F_width", "F_width")):
+        assert getattr(p, attr) == gold[k]["value"], k
+
+
+@pytest.mark.parametrize("bad", [dict(nu_H=0.0), dict(nu_L=-0.1), dict(W=0.0), dict(M=0.0),
+                                 dict(rho_L=0.0), dict(blend=1.5), dict(storage=7),
+                                 dict(F_mode=3), dict(D=0.0)])
+def test_create_rejects_bad_parameters(bad):
+    """tau = nu/T + 1/2 must exceed 1/2 and the other parameters be valid:
+    PFLB_ERR_ARG before any device call."""
+    from paper_2512_01032_gb300 import pflb
+    with pytest.raises(pflb.PflbError) as ei:
+        pflb.Lattice(4, 4, 4, **bad)
+    assert ei.value.status == pflb.ERR_ARG
+
+
+def test_create_rejects_bad_geometry():
+    import ctypes as C
+    from paper_2512_01032_gb300 import pflb
+    lib = pflb.load()
+    p = pflb.default_params()
+    h = C.c_void_p()
+    g, keep = pflb.make_geometry(2, 2, 2)
+    g.nx = 0
+    assert lib.pflb_create(C.byref(g), C.byref(p), None, C.byref(h)) == pflb.ERR_ARG
+    assert lib.pflb_create(None, C.byref(p), None, C.byref(h)) == pflb.ERR_ARG
+    assert b"null" in lib.pflb_last_error()
+    # null handles are rejected, not dereferenced
+    assert lib.pflb_step(None, 1) == pflb.ERR_ARG
+    assert lib.pflb_get_step(None) == -1
+    lib.pflb_destroy(None)
+
+
+def test_estimate_bytes_counts_wall_nodes():
+    """Host-side footprint estimate (used for admission by memory budget)."""
+    from paper_2512_01032_gb300 import pflb
+    n = 16
+    empty = pflb.estimate_bytes(n, n, n)
+    solid = np.zeros((n, n, n), np.uint8)
+    solid[0] = 1
+    walled = pflb.estimate_bytes(n, n, n, solid)
+    N = n ** 3
+    assert empty == 3 * 19 * N * 4 + N * 5 + N * 4 + 96 * 8
+    nw = 2 * n * n  # planes z = 1 and z = n-1 (periodic) touch the solid layer
+    assert walled - empty == nw * (2 * 18 * 4 + 4 + 5 * 4 + 18 * 4)

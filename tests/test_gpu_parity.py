@@ -1,0 +1,152 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (relative infinity norm, P normalised by max(|P|, 2 sigma/R)):
+FP64 storage <= 1e-11, FP32 storage <= 1e-5 on phi and P, as fixed for
+this method's step; u is checked with a looser bound because it is tiny
+(spurious currents) and normalised by its own maximum.
+"""
+import numpy as np
+import pytest
+
+from tests import _cases as CS
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-11, "fp32": 1e-5}
+TOL_U = {"fp64": 1e-9, "fp32": 1e-3}
+
+
+def _compare(G, Orc, steps_list, storage, p_scale, label=""):
+    t = 0
+    for s in steps_list:
+        G.step(s - t)
+        Orc.step(s - t)
+        t = s
+        ref = Orc.macros()
+        got = CS.gpu_fields(G)
+        e = CS.rel_errors(got, ref, p_scale)
+        assert e["phi"] <= TOL[storage], (label, s, e)
+        assert e["P"] <= TOL[storage], (label, s, e)
+        assert e["u"] <= TOL_U[storage], (label, s, e)
+        assert G.t == Orc.t == s
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_static_droplet_400_steps(storage, kernel):
+    """Periodic 32^3 droplet (R=8, W=4, ratio 1000, sigma=0.01, tau=0.8,
+    M=0.02): phi, P, u after 0, 1, 2, 7 and 400 steps."""
+    g, p, init = CS.droplet_case()
+    G, Orc = CS.make_pair(g, p, init, storage=storage, kernel=kernel)
+    _compare(G, Orc, [0, 1, 2, 7, 400], storage, 2 * p["sigma"] / init["R"], "droplet")
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_sessile_sphere_walls_wetting_free_slip(storage, kernel):
+    """Droplet on a voxelised sphere between two planes (32^3 scaling of the
+    128^3 workload), theta=60, optimised model: tanh F, free-slip band,
+    blend 0.95.  Exercises wall ghosts, bounce-back and specular links."""
+    g, p, init = CS.sessile_case(32, 60.0)
+    G, Orc = CS.make_pair(g, p, init, storage=storage, kernel=kernel)
+    _compare(G, Orc, [1, 2, 25, 120], storage, 2 * p["sigma"] / init["R"], "sessile")
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_slit_with_force_and_viscosity_ratio(storage):
+    """Capillary slit (scaled): walls with theta=45 only in the channel,
+    viscosity ratio 50, body force, optimised model."""
+    g, p, init = CS.slit_case()
+    G, Orc = CS.make_pair(g, p, init, storage=storage)
+    _compare(G, Orc, [3, 60], storage, 2 * p["sigma"] / 16.0, "slit")
+
+
+def test_square_channel_fp64_both_kernels_agree_bitwise():
+    """Square duct with a drop and a body force: FP64 parity, and the fused
+    and two-pass kernels give bit-identical fields (same per-cell
+    arithmetic)."""
+    g, p, init = CS.channel_case()
+    G0, Orc = CS.make_pair(g, p, init, storage="fp64", kernel=0)
+    G1, _ = CS.make_pair(g, p, init, storage="fp64", kernel=1)
+    _compare(G0, Orc, [5, 80], "fp64", 2 * p["sigma"] / init["R"], "channel")
+    G1.step(80)
+    for k in ("phi", "P", "ux"):
+        assert np.array_equal(G0.read(k), G1.read(k)), k
+
+
+@pytest.mark.parametrize("dims", [(37, 23, 11), (5, 3, 2), (1, 6, 5), (33, 9, 17)])
+def test_ragged_and_tiny_lattices(dims):
+    """Sizes that are not multiples of the tile, down to one cell wide; walls
+    included (a solid block and a floor)."""
+    import synth
+    nx, ny, nz = dims
+    shapes = [synth.Plane((0, 0, 0.5), (0, 0, 1))] if nz > 3 else []
+    if nx > 8:
+        shapes.append(synth.Box((nx // 2, 0, 0), (nx // 2 + 2, max(1, ny // 3), nz)))
+    g = synth.Geometry(nx, ny, nz, shapes, theta_deg=70.0)
+    p = dict(synth.sessile_sphere_params(70.0), Fex=(1e-6, -2e-6, 0.0))
+    init = dict(shape=0, center=(nx / 2.0, ny / 2.0, nz / 2.0), R=max(1.5, min(dims) / 3.0))
+    for storage in ("fp64", "fp32"):
+        G, Orc = CS.make_pair(g, p, init, storage=storage, kernel=0)
+        _compare(G, Orc, [1, 9], storage, 2 * p["sigma"] / init["R"], f"ragged{dims}")
+
+
+@pytest.mark.parametrize("tile", [(32, 8, 16), (64, 4, 7), (16, 16, 3), (32, 4, 32), (8, 8, 5)])
+def test_tile_shapes_bitwise_identical(tile):
+    """Every launch shape of the fused kernel gives the same bits as the
+    default one (FP32 storage)."""
+    g, p, init = CS.sessile_case(32, 120.0)
+    from paper_2512_01032_gb300 import pflb
+    ref = pflb.Lattice(g.nx, g.ny, g.nz, solid=g.solid, wall_normal=g.normals(),
+                       theta_cells=g.theta(), storage="fp32", **p)
+    ref.init_tanh(0, init["center"], init["R"])
+    ref.step(11)
+    L = pflb.Lattice(g.nx, g.ny, g.nz, solid=g.solid, wall_normal=g.normals(),
+                     theta_cells=g.theta(), storage="fp32", **p)
+    L.set_kernel(0, *tile)
+    L.init_tanh(0, init["center"], init["R"])
+    L.step(11)
+    for k in ("phi", "P", "uz"):
+        assert np.array_equal(ref.read(k), L.read(k)), (tile, k)
+
+
+def test_mask_normals_fallback_parity():
+    """Wall normals estimated from the mask (NULL normals) on both sides."""
+    g, p, init = CS.sessile_case(24, 120.0)
+    G, Orc = CS.make_pair(g, p, init, storage="fp64", use_normals=False)
+    _compare(G, Orc, [1, 30], "fp64", 2 * p["sigma"] / init["R"], "fallback-normals")
+
+
+@pytest.mark.slow
+def test_sessile_sphere_64_parity_fp32():
+    """The curved-wall workload at 64^3 (all lengths halved), FP32 storage,
+    the bench launch configuration, 100 steps."""
+    g, p, init = CS.sessile_case(64, 90.0)
+    G, Orc = CS.make_pair(g, p, init, storage="fp32", kernel=0)
+    _compare(G, Orc, [100], "fp32", 2 * p["sigma"] / init["R"], "sessile64")
+
+
+@pytest.mark.slow
+def test_full_size_128_first_steps_fp32():
+    """Full 128^3 curved-wall workload in the bench launch configuration:
+    every cell against the oracle after 2 steps."""
+    g, p, init = CS.sessile_case(128, 30.0)
+    G, Orc = CS.make_pair(g, p, init, storage="fp32", kernel=0)
+    _compare(G, Orc, [2], "fp32", 2 * p["sigma"] / init["R"], "sessile128")
+
+
+def test_full_size_128_conservation_fp32():
+    """Properties at full size over 2000 steps: total phi conserved to FP32
+    roundoff, no non-finite values, bounded spurious velocity."""
+    import synth
+    from paper_2512_01032_gb300 import pflb
+    g, p, init = synth.sessile_sphere(128, 150.0)
+    L = pflb.Lattice(g.nx, g.ny, g.nz, solid=g.solid, wall_normal=g.normals(),
+                     theta_cells=g.theta(), storage="fp32", **p)
+    L.init_tanh(0, init["center"], init["R"])
+    d0 = L.diag()
+    L.step(2000)
+    d1 = L.diag()
+    assert d1["nonfinite"] == 0
+    assert abs(d1["mass"] - d0["mass"]) / d0["mass"] < 2e-5
+    assert d1["u_max"] < 0.05
