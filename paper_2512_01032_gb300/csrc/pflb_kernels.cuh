@@ -245,7 +245,7 @@ __device__ __forceinline__ R cell_phi(const Args<S, R> &a, long long c) {
   if (a.flags[c] & F_SOLID) return R(0);
   R s = R(0);
 #pragma unroll
-  for (int i = 0; i < Q; ++i) s += (R)Store<S>::ld(a.hin + i * a.N + c);
+  for (int i = 0; i < Q; ++i) s += (R)ld_ro<S>(a.hin + i * a.N + c);
   return s;
 }
 
@@ -268,6 +268,11 @@ __global__ void __launch_bounds__(256) k_cell(Args<S, R> a) {
   acc.zero();
   if (c < a.N) {
     const uint8_t f = a.flags[c];
+    if (MODE == MODE_MACRO && (f & F_SOLID) && a.out) {
+      // fields are defined as zero on solid cells
+#pragma unroll
+      for (int k = 0; k < 6; ++k) a.out[k * a.N + c] = 0.0;
+    }
     if (!(f & F_SOLID)) {
       const int x = (int)(c % a.nx);
       const int y = (int)((c / a.nx) % a.ny);
@@ -278,7 +283,7 @@ __global__ void __launch_bounds__(256) k_cell(Args<S, R> a) {
       R phi = R(0);
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
-        h[i] = (R)Store<S>::ld(a.hin + i * a.N + c);
+        h[i] = (R)ld_ro<S>(a.hin + i * a.N + c);
         phi += h[i];
       }
 #pragma unroll
@@ -296,7 +301,7 @@ __global__ void __launch_bounds__(256) k_cell(Args<S, R> a) {
 // from the h populations (own cells and ring cells), so no phi field is
 // stored in HBM.
 template <class S, class R, bool ODD, bool DIAG>
-__global__ void __launch_bounds__(256) k_fused(Args<S, R> a, int BX, int BY) {
+__global__ void __launch_bounds__(256, 2) k_fused(Args<S, R> a, int BX, int BY) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R *sphi = reinterpret_cast<R *>(smem_raw);
   if (a.diag_zero && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x < 32)
@@ -343,7 +348,7 @@ __global__ void __launch_bounds__(256) k_fused(Args<S, R> a, int BX, int BY) {
       if (!(f & F_SOLID)) {
         R h[Q], val[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) h[i] = (R)Store<S>::ld(a.hin + i * a.N + c);
+        for (int i = 0; i < Q; ++i) h[i] = (R)ld_ro<S>(a.hin + i * a.N + c);
         const R *p0 = sphi + (((z % 3) + 3) % 3) * PS;
         const R *pm = sphi + ((((z - 1) % 3) + 3) % 3) * PS;
         const R *pp = sphi + ((((z + 1) % 3) + 3) % 3) * PS;

@@ -102,9 +102,13 @@ template <> struct Store<double> {
   static __device__ __forceinline__ void st(double *p, double v) { *p = v; }
 };
 template <> struct Store<float> {
-  static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
+  static __device__ __forceinline__ float ld(const float *p) { return *p; }
   static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
 };
+// Loads of data that no thread writes during the launch (the h buffer being
+// read): may go through the read-only data path.  In-place arrays (g) must
+// not, since the compiler may then move such loads past aliasing stores.
+template <class S> __device__ __forceinline__ S ld_ro(const S *p) { return __ldg(p); }
 
 template <class R> __device__ __forceinline__ R rsqrt_(R x);
 template <> __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
@@ -223,15 +227,21 @@ __device__ __forceinline__ void collide_h(const Model<R> &m, R h[Q], R phi, R gx
   if (m.mobility_corr) th += delta_theta(m, phi, gnorm, lap);
   const R uu15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
   const R om = m.inv_tau_phi;
+  // The relaxation conserves sum_i h_i = phi (sum_i h_eq_i = phi exactly).
+  // The rest population is closed from the others so that the stored sum
+  // carries one rounding instead of the bias of sum_i Gamma_i - 1.
+  R rest = phi;
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
+  for (int i = 1; i < Q; ++i) {
     const R cu = R(cx_of(i)) * ux + R(cy_of(i)) * uy + R(cz_of(i)) * uz;
     const R cn = R(cx_of(i)) * nx + R(cy_of(i)) * ny + R(cz_of(i)) * nz;
     const R wi = R(w_of(i));
     const R G = wi * (R(1) + R(3) * cu + R(4.5) * cu * cu - uu15);
     const R heq = phi * G + th * wi * cn;
     h[i] = h[i] - om * (h[i] - heq);
+    rest -= h[i];
   }
+  h[0] = rest;
 }
 
 // Filtered hydrodynamic collision (Eqs. 5-11, reading: G_eq = E + K/2,
@@ -253,11 +263,14 @@ __device__ __forceinline__ void collide_g(const Model<R> &m, R g[Q], const Macro
     const R c0 = R(cx_of(i)), c1 = R(cy_of(i)), c2 = R(cz_of(i));
     const R wi = R(w_of(i));
     const R cu = c0 * ux + c1 * uy + c2 * uz;
-    const R G = wi * (R(1) + R(3) * cu + R(4.5) * cu * cu - uu15);
+    // Gamma_i - w_i computed directly: rho*Gamma_i - w_i*rho would cancel
+    // in the heavy phase (rho = 1) and lose the small pressure part.
+    const R Gd = wi * (R(3) * cu + R(4.5) * cu * cu - uu15);
+    const R G = wi + Gd;
     const R cg = c0 * gx + c1 * gy + c2 * gz - ug;         // (c - u) . grad phi
     const R cF = c0 * m.Fx + c1 * m.Fy + c2 * m.Fz - uF;   // (c - u) . F
-    const R K = ((G - wi) * m.rho_dif + G * muT) * cg + R(3) * G * cF;
-    const R E = mc.rho * G + wi * (P3 - mc.rho);
+    const R K = (Gd * m.rho_dif + G * muT) * cg + R(3) * G * cF;
+    const R E = wi * P3 + mc.rho * Gd;
     const R neq = g[i] - E + R(0.5) * K;
     base[i] = E + R(0.5) * K;
     if (cx_of(i)) pxx += neq;

@@ -160,8 +160,12 @@ def static_droplet_params():
 
 
 def static_droplet(n=32, R=8.0):
+    """Droplet at the box centre ((n-1)/2 in cell coordinates 0..n-1, i.e.
+    between lattice sites, so that no cell sits on a mirror plane where
+    grad phi vanishes exactly)."""
     g = Geometry(n, n, n)
-    return g, static_droplet_params(), dict(shape=0, center=(n / 2, n / 2, n / 2), R=R)
+    c = (n - 1) / 2.0
+    return g, static_droplet_params(), dict(shape=0, center=(c, c, c), R=R)
 
 
 def sessile_sphere_params(theta_deg=90.0):
@@ -176,7 +180,7 @@ def sessile_sphere(n=128, theta_deg=90.0):
     solid planes at z=0 and z=n-1, droplet of radius 20*(n/128) tangent to the
     sphere's top (all lengths scale with n)."""
     s = n / 128.0
-    c = n / 2.0
+    c = (n - 1) / 2.0  # box centre, between lattice sites
     shapes = [Sphere((c, c, 0.0), 30.0 * s), Plane((0, 0, 0.5), (0, 0, 1)),
               Plane((0, 0, n - 1.5), (0, 0, -1))]
     g = Geometry(n, n, n, shapes, theta_deg=theta_deg)
@@ -188,8 +192,9 @@ def sessile_sphere(n=128, theta_deg=90.0):
 
 def slit_params():
     """Capillary filling: theta=45, density ratio 1000, viscosity ratio 50
-    (nu_H = 1/60, nu_L = 1/3), sigma=0.01, M=0.1666, W=2.5."""
-    return dict(sigma=0.01, W=2.5, M=0.1666, rho_H=1.0, rho_L=1e-3, nu_H=1.0 / 60.0,
+    (nu_H = 1/60, nu_L = 1/3), sigma=0.01, M=0.1666, W=4 (W=2.5 with these
+    relaxation times is unstable at the free interface)."""
+    return dict(sigma=0.01, W=4.0, M=0.1666, rho_H=1.0, rho_L=1e-3, nu_H=1.0 / 60.0,
                 nu_L=1.0 / 3.0, theta_deg=45.0, F_mode=1, mobility_corr=1, free_slip=1,
                 blend=0.95)
 

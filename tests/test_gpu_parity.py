@@ -2,8 +2,9 @@
 
 Tolerances (relative infinity norm, P normalised by max(|P|, 2 sigma/R)):
 FP64 storage <= 1e-11, FP32 storage <= 1e-5 on phi and P, as fixed for
-this method's step; u is checked with a looser bound because it is tiny
-(spurious currents) and normalised by its own maximum.
+this method's step.  u is near zero in these static cases (spurious
+currents ~1e-4), so it is checked with an absolute bound: 1e-12 (FP64) and
+2e-5 (FP32; u = j/rho divides FP32 rounding of j by rho_L = 1e-3).
 """
 import numpy as np
 import pytest
@@ -13,7 +14,7 @@ from tests import _cases as CS
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-11, "fp32": 1e-5}
-TOL_U = {"fp64": 1e-9, "fp32": 1e-3}
+TOL_U = {"fp64": 1e-12, "fp32": 2e-5}
 
 
 def _compare(G, Orc, steps_list, storage, p_scale, label=""):
@@ -27,7 +28,7 @@ def _compare(G, Orc, steps_list, storage, p_scale, label=""):
         e = CS.rel_errors(got, ref, p_scale)
         assert e["phi"] <= TOL[storage], (label, s, e)
         assert e["P"] <= TOL[storage], (label, s, e)
-        assert e["u"] <= TOL_U[storage], (label, s, e)
+        assert e["u_abs"] <= TOL_U[storage], (label, s, e)
         assert G.t == Orc.t == s
 
 
@@ -84,8 +85,9 @@ def test_ragged_and_tiny_lattices(dims):
     if nx > 8:
         shapes.append(synth.Box((nx // 2, 0, 0), (nx // 2 + 2, max(1, ny // 3), nz)))
     g = synth.Geometry(nx, ny, nz, shapes, theta_deg=70.0)
-    p = dict(synth.sessile_sphere_params(70.0), Fex=(1e-6, -2e-6, 0.0))
-    init = dict(shape=0, center=(nx / 2.0, ny / 2.0, nz / 2.0), R=max(1.5, min(dims) / 3.0))
+    p = dict(synth.sessile_sphere_params(70.0), Fex=(1e-8, -2e-8, 0.0))
+    init = dict(shape=0, center=(nx / 2.0 + 0.37, ny / 2.0 - 0.21, nz / 2.0 + 0.13),
+                R=max(1.5, min(dims) / 3.0))
     for storage in ("fp64", "fp32"):
         G, Orc = CS.make_pair(g, p, init, storage=storage, kernel=0)
         _compare(G, Orc, [1, 9], storage, 2 * p["sigma"] / init["R"], f"ragged{dims}")

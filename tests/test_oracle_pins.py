@@ -316,7 +316,7 @@ def test_mass_conserved_with_walls_wetting_and_free_slip():
     solid[0] = 1; solid[-1] = 1; solid[:, 0] = 1
     L = O.OracleLattice(nx, ny, nz, solid=solid.reshape(-1), nthreads=4, sigma=0.01, W=4.0,
                         M=0.05, rho_H=1.0, rho_L=1e-3, nu_H=0.05, nu_L=0.2, theta_deg=60.0,
-                        F_mode=1, free_slip=1, blend=0.95, Fex=(2e-6, 0, 0))
+                        F_mode=1, free_slip=1, blend=0.95, Fex=(2e-7, 0, 0))
     phi0 = O.tanh_phi(0, (nx, ny, nz), (10, 6, 3), 5.0, 4.0) * (1 - solid.reshape(-1))
     L.init_phi(phi0)
     m0 = L.macros()["phi"].sum()
