@@ -128,7 +128,8 @@ typedef struct {
 void pflb_default_params(pflb_params *p);
 
 /* Create a lattice from geometry and parameters.  Validates parameters
- * (dimensions >= 1, W > 0, M > 0, nu > 0 so that tau > 1/2, rho_L > 0,
+ * (dimensions >= 1 with nx*ny*nz < 2^31, W > 0, M > 0, nu > 0 so that
+ * tau > 1/2, rho_L > 0,
  * rho_H > 0, 0 <= blend <= 1, storage known) and returns PFLB_ERR_ARG
  * otherwise.  cuda_stream: a cudaStream_t or NULL.  On success *out owns
  * all device memory (about 228 B/cell at FP32 storage); the state is

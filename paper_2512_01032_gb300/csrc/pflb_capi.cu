@@ -205,8 +205,8 @@ pflb_status pflb_create(const pflb_geometry *geom, const pflb_params *params, vo
   if (!geom || !geom->solid) return fail(PFLB_ERR_ARG, "null geometry or mask");
   if (geom->nx < 1 || geom->ny < 1 || geom->nz < 1)
     return fail(PFLB_ERR_ARG, "dimensions must be >= 1");
-  if ((long long)geom->nx * geom->ny * geom->nz > (1LL << 40))
-    return fail(PFLB_ERR_ARG, "lattice too large");
+  if ((long long)geom->nx * geom->ny * geom->nz >= (1LL << 31))
+    return fail(PFLB_ERR_ARG, "lattice too large (nx*ny*nz must be below 2^31)");
   pflb_status s = check_params(params);
   if (s != PFLB_OK) return s;
 

@@ -2,7 +2,7 @@
 // method (arXiv 2512.01032, Sec. II and Sec. III A) on a periodic D3Q19
 // lattice with voxel walls.
 //
-// Memory layout (SoA, x fastest, cell = x + nx*(y + ny*z)):
+// Memory layout (SoA, x fastest, cell = x + nx*(y + ny*z), N < 2^31):
 //   h  : two buffers [19][N]; push streaming from h[t&1] into h[(t+1)&1].
 //        Two buffers because the fused kernel recomputes phi = sum_i h_i in
 //        a one-cell halo around its tile; in place, a neighbouring block
@@ -16,6 +16,8 @@
 //        tangential neighbour without two threads touching one A-A slot.
 //   ghost : per wall node, wetting ghosts phi_{s,i} [18][nwall] (compute type).
 //   flags : uint8 per cell (bit0 solid, bit1 wall node); widx: wall index.
+// The 19 per-direction base pointers of each population array travel in the
+// kernel parameters (constant bank), so an access costs one multiply-add.
 #pragma once
 #include "pflb_model.cuh"
 
@@ -23,28 +25,27 @@ namespace pflb {
 
 enum { MODE_STEP = 0, MODE_MACRO = 1 };
 
-
 template <class S, class R>
 struct Args {
   int nx, ny, nz, lz;
-  long long N;
+  int N;
   int nw;
-  const S *hin;
-  S *hout;
-  S *g;
+  const S *hin[Q];   // direction bases of the h buffer being read
+  S *hout[Q];        // direction bases of the h buffer being written
+  S *g[Q];           // direction bases of the g buffer (in place)
   const uint8_t *flags;
   const int *widx;
   const uint32_t *wmask;
-  const R *wgeo;   // [5][nw]: n_w (x,y,z), cos theta, sin theta
-  R *ghost;        // [18][nw]
-  const S *wp_rd;  // [18][nw]
-  S *wp_wr;        // [18][nw]
-  const R *phi;    // [N] phi field (two-pass path only)
+  const R *wgeo;     // [5][nw]: n_w (x,y,z), cos theta, sin theta
+  R *ghost;          // [18][nw]
+  const S *wp_rd;    // [18][nw]
+  S *wp_wr;          // [18][nw]
+  const R *phi;      // [N] phi field (two-pass path and field reads)
   Model<R> m;
-  double *diag;    // [D_COUNT] accumulator of this launch, or null
-  double *diag_zero;  // [32] accumulator of the next step, zeroed here
-  int reg[6];      // diagnostic box [x0,x1) x [y0,y1) x [z0,z1)
-  double *out;     // macro outputs [6][N] (phi, rho, P, ux, uy, uz) or null
+  double *diag;      // [D_COUNT] accumulator of this launch, or null
+  double *diag_zero; // [32] accumulator of the next diagnostic launch, zeroed here
+  int reg[6];        // diagnostic box [x0,x1) x [y0,y1) x [z0,z1)
+  double *out;       // macro outputs [6][N] (phi, rho, P, ux, uy, uz) or null
 };
 
 template <class R>
@@ -58,55 +59,63 @@ struct DiagAcc {
   }
 };
 
-// Neighbour index with periodic wrap, from per-axis tables.
+// Periodic neighbour offsets of one cell from six per-axis deltas.
 struct Nbr {
-  long long X[3], Y[3], Z[3];
+  int xm, xp, ym, yp, zm, zp;
   __device__ __forceinline__ void init(int x, int y, int z, int nx, int ny, int nz) {
-    int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-    int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-    int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
-    long long sy = nx, sz = (long long)nx * ny;
-    X[0] = xm; X[1] = x; X[2] = xp;
-    Y[0] = ym * sy; Y[1] = y * sy; Y[2] = yp * sy;
-    Z[0] = zm * sz; Z[1] = z * sz; Z[2] = zp * sz;
+    const int sy = nx, sz = nx * ny;
+    xm = x == 0 ? nx - 1 : -1;
+    xp = x == nx - 1 ? 1 - nx : 1;
+    ym = (y == 0 ? ny - 1 : -1) * sy;
+    yp = (y == ny - 1 ? 1 - ny : 1) * sy;
+    zm = (z == 0 ? nz - 1 : -1) * sz;
+    zp = (z == nz - 1 ? 1 - nz : 1) * sz;
   }
-  __device__ __forceinline__ long long at(int i) const {
-    return X[cx_of(i) + 1] + Y[cy_of(i) + 1] + Z[cz_of(i) + 1];
+  // offset of x + c_i relative to x
+  __device__ __forceinline__ int off(int i) const {
+    int o = 0;
+    if (cx_of(i) > 0) o += xp;
+    if (cx_of(i) < 0) o += xm;
+    if (cy_of(i) > 0) o += yp;
+    if (cy_of(i) < 0) o += ym;
+    if (cz_of(i) > 0) o += zp;
+    if (cz_of(i) < 0) o += zm;
+    return o;
   }
 };
 
 template <class R>
 __device__ __forceinline__ bool finite_(R v) { return isfinite(v); }
 
-// Full update (or macro evaluation) of one fluid cell.  h[] holds the cell's
-// streamed h populations, phi their sum, val[1..18] the phi of the 18
-// neighbours (anything for solid ones).
+// Full update (or macro evaluation) of one fluid cell c at (x, y, z).
+// h[] holds the cell's streamed h populations, phi their sum, val[1..18]
+// the phi of the 18 neighbours (anything for solid ones).
 template <class S, class R, bool ODD, int MODE, bool DIAG>
-__device__ __forceinline__ void update_cell(const Args<S, R> &a, int x, int y, int z, long long c,
+__device__ __forceinline__ void update_cell(const Args<S, R> &a, int x, int y, int z, int c,
                                             uint8_t f, R h[Q], R phi, R val[Q],
                                             DiagAcc<R> &acc) {
   const Model<R> &m = a.m;
-  const long long N = a.N;
   Nbr nb;
   nb.init(x, y, z, a.nx, a.ny, a.nz);
   uint32_t lm = 0;
-  int rec = -1;
+  int rec = 0;
   val[0] = phi;
   R gx, gy, gz, lap;
-  if (f & F_WALL) {
+  const bool wall = (f & F_WALL) != 0;
+  if (wall) {
     rec = a.widx[c];
     lm = a.wmask[rec];
     const int nw = a.nw;
 #pragma unroll
     for (int i = 1; i < Q; ++i)
-      if ((lm >> i) & 1u) val[i] = a.ghost[(i - 1) * (long long)nw + rec];
+      if ((lm >> i) & 1u) val[i] = a.ghost[(i - 1) * nw + rec];
     cd_stencil(val, gx, gy, gz, lap);  // grad phi with the previous ghosts
     wall_ghosts(m, phi, gx, gy, gz, a.wgeo[rec], a.wgeo[nw + rec], a.wgeo[2 * nw + rec],
                 a.wgeo[3 * nw + rec], a.wgeo[4 * nw + rec], lm, val);
     if (MODE == MODE_STEP) {
 #pragma unroll
       for (int i = 1; i < Q; ++i)
-        if ((lm >> i) & 1u) a.ghost[(i - 1) * (long long)nw + rec] = val[i];
+        if ((lm >> i) & 1u) a.ghost[(i - 1) * nw + rec] = val[i];
     }
   }
   cd_stencil(val, gx, gy, gz, lap);
@@ -116,11 +125,11 @@ __device__ __forceinline__ void update_cell(const Args<S, R> &a, int x, int y, i
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
     if (k != 0 && ((lm >> opp_of(k)) & 1u)) {
-      g[k] = (R)a.wp_rd[(k - 1) * (long long)a.nw + rec];
+      g[k] = (R)a.wp_rd[(k - 1) * a.nw + rec];
     } else if (!ODD) {
-      g[k] = (R)Store<S>::ld(a.g + k * N + c);
+      g[k] = (R)Store<S>::ld(a.g[k] + c);
     } else {
-      g[k] = (R)Store<S>::ld(a.g + opp_of(k) * N + nb.at(opp_of(k)));
+      g[k] = (R)Store<S>::ld(a.g[opp_of(k)] + (c + nb.off(opp_of(k))));
     }
   }
   const Macro<R> mc = macros(m, g, phi, gx, gy, gz, lap);
@@ -133,19 +142,19 @@ __device__ __forceinline__ void update_cell(const Args<S, R> &a, int x, int y, i
     if (x >= a.reg[0] && x < a.reg[1] && y >= a.reg[2] && y < a.reg[3] && z >= a.reg[4] &&
         z < a.reg[5])
       acc.v[D_REGION] += phi;
-    if ((f & F_WALL) && phi >= R(0.25) && phi <= R(0.75)) {
+    if (wall && phi >= R(0.25) && phi <= R(0.75)) {
       acc.v[D_CLN] += R(1);
       acc.v[D_CLX] += R(x); acc.v[D_CLY] += R(y); acc.v[D_CLZ] += R(z);
       acc.v[D_CLXX] += R(x) * R(x); acc.v[D_CLYY] += R(y) * R(y); acc.v[D_CLZZ] += R(z) * R(z);
     }
-    R u2 = mc.ux * mc.ux + mc.uy * mc.uy + mc.uz * mc.uz;
+    const R u2 = mc.ux * mc.ux + mc.uy * mc.uy + mc.uz * mc.uz;
     acc.v[D_KIN] += R(0.5) * mc.rho * u2;
     if (!(finite_(phi) && finite_(mc.P) && finite_(u2))) acc.v[D_NONFINITE] += R(1);
-    R um = sqrt_(u2);
-    acc.umax = um > acc.umax ? um : acc.umax;
+    acc.umax = u2 > acc.umax ? u2 : acc.umax;  // squared; root taken at the flush
   }
   if (MODE == MODE_MACRO) {
     if (a.out) {
+      const long long N = a.N;
       a.out[c] = (double)phi;
       a.out[N + c] = (double)mc.rho;
       a.out[2 * N + c] = (double)mc.P;
@@ -156,16 +165,15 @@ __device__ __forceinline__ void update_cell(const Args<S, R> &a, int x, int y, i
     return;
   }
 
-  collide_h(m, h, phi, gx, gy, gz, lap, mc.ux, mc.uy, mc.uz);
-  collide_g(m, g, mc, phi, gx, gy, gz);
+  collide(m, h, g, mc, phi, gx, gy, gz, lap);
 
   // h: push into the other buffer, halfway bounce-back at solid links.
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     if (i != 0 && ((lm >> i) & 1u))
-      Store<S>::st(a.hout + opp_of(i) * N + c, (S)h[i]);
+      Store<S>::st(a.hout[opp_of(i)] + c, (S)h[i]);
     else
-      Store<S>::st(a.hout + i * N + nb.at(i), (S)h[i]);
+      Store<S>::st(a.hout[i] + (c + nb.off(i)), (S)h[i]);
   }
   // g: A-A write; solid links go to the wall population buffer, either to
   // this node (bounce-back) or to the tangential neighbour (specular
@@ -184,17 +192,17 @@ __device__ __forceinline__ void update_cell(const Args<S, R> &a, int x, int y, i
           if (wa || wb) {
             const R py = wa ? val[e.fb] : val[e.fa];
             if (py >= m.band_lo && py <= m.band_hi) {
-              drec = a.widx[wa ? nb.at(e.fb) : nb.at(e.fa)];
+              drec = a.widx[c + (wa ? nb.off(e.fb) : nb.off(e.fa))];
               ddir = wa ? e.ra : e.rb;
             }
           }
         }
       }
-      a.wp_wr[(ddir - 1) * (long long)a.nw + drec] = (S)g[i];
+      a.wp_wr[(ddir - 1) * a.nw + drec] = (S)g[i];
     } else if (!ODD) {
-      Store<S>::st(a.g + opp_of(i) * N + c, (S)g[i]);
+      Store<S>::st(a.g[opp_of(i)] + c, (S)g[i]);
     } else {
-      Store<S>::st(a.g + i * N + nb.at(i), (S)g[i]);
+      Store<S>::st(a.g[i] + (c + nb.off(i)), (S)g[i]);
     }
   }
 }
@@ -208,7 +216,7 @@ __device__ void flush_diag(double *diag, DiagAcc<R> &acc) {
   double v[D_COUNT];
 #pragma unroll
   for (int k = 0; k < D_UMAX; ++k) v[k] = (double)acc.v[k];
-  v[D_UMAX] = (double)acc.umax;
+  v[D_UMAX] = sqrt((double)acc.umax);
 #pragma unroll
   for (int k = 0; k < D_COUNT; ++k) {
     for (int o = 16; o > 0; o >>= 1) {
@@ -241,29 +249,34 @@ __device__ void flush_diag(double *diag, DiagAcc<R> &acc) {
 
 // phi of one cell from the h buffer being read (0 for solid cells).
 template <class S, class R>
-__device__ __forceinline__ R cell_phi(const Args<S, R> &a, long long c) {
+__device__ __forceinline__ R cell_phi(const Args<S, R> &a, int c) {
   if (a.flags[c] & F_SOLID) return R(0);
   R s = R(0);
 #pragma unroll
-  for (int i = 0; i < Q; ++i) s += (R)ld_ro<S>(a.hin + i * a.N + c);
+  for (int i = 0; i < Q; ++i) s += (R)ld_ro<S>(a.hin[i] + c);
   return s;
+}
+
+template <class S, class R>
+__device__ __forceinline__ void zero_next_diag(const Args<S, R> &a) {
+  if (a.diag_zero && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x < 32)
+    a.diag_zero[threadIdx.x] = 0.0;
 }
 
 // --------------------------------------------------------- two-pass path
 // Pass 1: phi field.
 template <class S, class R>
-__global__ void k_phi(Args<S, R> a, R *phi_out) {
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__global__ void k_phi(const __grid_constant__ Args<S, R> a, R *phi_out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= a.N) return;
   phi_out[c] = cell_phi(a, c);
 }
 
 // Pass 2: one thread per cell, neighbour phi from the field.
 template <class S, class R, bool ODD, int MODE, bool DIAG>
-__global__ void __launch_bounds__(256) k_cell(Args<S, R> a) {
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (a.diag_zero && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x < 32)
-    a.diag_zero[threadIdx.x] = 0.0;
+__global__ void __launch_bounds__(256) k_cell(const __grid_constant__ Args<S, R> a) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  zero_next_diag(a);
   DiagAcc<R> acc;
   acc.zero();
   if (c < a.N) {
@@ -271,23 +284,23 @@ __global__ void __launch_bounds__(256) k_cell(Args<S, R> a) {
     if (MODE == MODE_MACRO && (f & F_SOLID) && a.out) {
       // fields are defined as zero on solid cells
 #pragma unroll
-      for (int k = 0; k < 6; ++k) a.out[k * a.N + c] = 0.0;
+      for (int k = 0; k < 6; ++k) a.out[(long long)k * a.N + c] = 0.0;
     }
     if (!(f & F_SOLID)) {
-      const int x = (int)(c % a.nx);
-      const int y = (int)((c / a.nx) % a.ny);
-      const int z = (int)(c / ((long long)a.nx * a.ny));
+      const int x = c % a.nx;
+      const int y = (c / a.nx) % a.ny;
+      const int z = c / (a.nx * a.ny);
       Nbr nb;
       nb.init(x, y, z, a.nx, a.ny, a.nz);
       R h[Q], val[Q];
       R phi = R(0);
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
-        h[i] = (R)ld_ro<S>(a.hin + i * a.N + c);
+        h[i] = (R)ld_ro<S>(a.hin[i] + c);
         phi += h[i];
       }
 #pragma unroll
-      for (int i = 1; i < Q; ++i) val[i] = a.phi[nb.at(i)];
+      for (int i = 1; i < Q; ++i) val[i] = a.phi[c + nb.off(i)];
       update_cell<S, R, ODD, MODE, DIAG>(a, x, y, z, c, f, h, phi, val, acc);
     }
   }
@@ -301,22 +314,23 @@ __global__ void __launch_bounds__(256) k_cell(Args<S, R> a) {
 // from the h populations (own cells and ring cells), so no phi field is
 // stored in HBM.
 template <class S, class R, bool ODD, bool DIAG>
-__global__ void __launch_bounds__(256, 2) k_fused(Args<S, R> a, int BX, int BY) {
+__global__ void __launch_bounds__(256, 2)
+    k_fused(const __grid_constant__ Args<S, R> a, int BX, int BY) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R *sphi = reinterpret_cast<R *>(smem_raw);
-  if (a.diag_zero && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x < 32)
-    a.diag_zero[threadIdx.x] = 0.0;
+  zero_next_diag(a);
   const int PW = BX + 2, PS = (BX + 2) * (BY + 2);
   const int tid = threadIdx.x;
   const int tx = tid % BX, ty = tid / BX;
   const int nx = a.nx, ny = a.ny, nz = a.nz;
-  const long long sz = (long long)nx * ny;
+  const int sz = nx * ny;
   const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
   const int zb = blockIdx.z * a.lz;
   const int ze = min(zb + a.lz, nz);
   const bool active = ty < BY;
   const bool valid = active && (x0 + tx) < nx && (y0 + ty) < ny;
   const int gx = (x0 + tx) % nx, gy = (y0 + ty) % ny;
+  const int col = gx + nx * gy;
   // ring cell of this thread (smem coords), if any
   const int nring = 2 * PW + 2 * BY;
   int rx = -1, ry = -1;
@@ -325,14 +339,13 @@ __global__ void __launch_bounds__(256, 2) k_fused(Args<S, R> a, int BX, int BY) 
     else if (tid < 2 * PW) { rx = tid - PW; ry = BY + 1; }
     else { int k = tid - 2 * PW; rx = (k & 1) ? BX + 1 : 0; ry = 1 + (k >> 1); }
   }
-  const int rgx = ((x0 + rx - 1) % nx + nx) % nx;
-  const int rgy = ((y0 + ry - 1) % ny + ny) % ny;
+  const int rcol = ((x0 + rx - 1) % nx + nx) % nx + nx * (((y0 + ry - 1) % ny + ny) % ny);
 
   auto plane = [&](int zu) {  // fill phi of (unwrapped) plane zu into its ring slot
     const int zw = ((zu % nz) + nz) % nz;
     R *dst = sphi + (((zu % 3) + 3) % 3) * PS;
-    if (active) dst[(ty + 1) * PW + tx + 1] = cell_phi(a, gx + nx * (long long)gy + sz * zw);
-    if (rx >= 0) dst[ry * PW + rx] = cell_phi(a, rgx + nx * (long long)rgy + sz * zw);
+    if (active) dst[(ty + 1) * PW + tx + 1] = cell_phi(a, col + sz * zw);
+    if (rx >= 0) dst[ry * PW + rx] = cell_phi(a, rcol + sz * zw);
   };
 
   DiagAcc<R> acc;
@@ -343,12 +356,12 @@ __global__ void __launch_bounds__(256, 2) k_fused(Args<S, R> a, int BX, int BY) 
     plane(z + 1);
     __syncthreads();
     if (valid) {
-      const long long c = gx + nx * (long long)gy + sz * z;
+      const int c = col + sz * z;
       const uint8_t f = a.flags[c];
       if (!(f & F_SOLID)) {
         R h[Q], val[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) h[i] = (R)ld_ro<S>(a.hin + i * a.N + c);
+        for (int i = 0; i < Q; ++i) h[i] = (R)ld_ro<S>(a.hin[i] + c);
         const R *p0 = sphi + (((z % 3) + 3) % 3) * PS;
         const R *pm = sphi + ((((z - 1) % 3) + 3) % 3) * PS;
         const R *pp = sphi + ((((z + 1) % 3) + 3) % 3) * PS;
@@ -369,45 +382,41 @@ __global__ void __launch_bounds__(256, 2) k_fused(Args<S, R> a, int BX, int BY) 
 
 // ------------------------------------------------------------ init
 // Equilibrium initial state from phi0 (reading: u = 0, P = P0, K from the
-// initial gradient, ghosts = phi of the wall node).
+// initial gradient, ghosts = phi of the wall node).  Writes the h buffer
+// given in h0 (the one step 0 reads) and wall populations into wp0.
 template <class S, class R>
-__global__ void k_init(Args<S, R> a, const double *phi0, double P0, S *h0, S *wp0) {
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__global__ void k_init(const __grid_constant__ Args<S, R> a, const double *phi0, double P0,
+                       S *h0base, S *wp0) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= a.N) return;
   const long long N = a.N;
   const uint8_t f = a.flags[c];
   if (f & F_SOLID) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) { h0[i * N + c] = (S)0; a.g[i * N + c] = (S)0; }
+    for (int i = 0; i < Q; ++i) { h0base[i * N + c] = (S)0; a.g[i][c] = (S)0; }
     return;
   }
-  const int x = (int)(c % a.nx), y = (int)((c / a.nx) % a.ny);
-  const int z = (int)(c / ((long long)a.nx * a.ny));
+  const int x = c % a.nx, y = (c / a.nx) % a.ny, z = c / (a.nx * a.ny);
   Nbr nb;
   nb.init(x, y, z, a.nx, a.ny, a.nz);
   const R phi = (R)phi0[c];
   R val[Q];
   val[0] = phi;
   uint32_t lm = 0;
-  int rec = -1;
+  int rec = 0;
   if (f & F_WALL) { rec = a.widx[c]; lm = a.wmask[rec]; }
 #pragma unroll
-  for (int i = 1; i < Q; ++i) val[i] = ((lm >> i) & 1u) ? phi : (R)phi0[nb.at(i)];
+  for (int i = 1; i < Q; ++i) val[i] = ((lm >> i) & 1u) ? phi : (R)phi0[c + nb.off(i)];
   if (f & F_WALL) {
 #pragma unroll
     for (int i = 1; i < Q; ++i)
-      if ((lm >> i) & 1u) a.ghost[(i - 1) * (long long)a.nw + rec] = phi;
+      if ((lm >> i) & 1u) a.ghost[(i - 1) * a.nw + rec] = phi;
   }
   R gx, gy, gz, lap;
   cd_stencil(val, gx, gy, gz, lap);
   const Model<R> &m = a.m;
-  // h = h_eq(phi, u = 0): relaxing from a zero state with omega = 1 gives it.
   R h[Q];
-#pragma unroll
-  for (int i = 0; i < Q; ++i) h[i] = R(0);
-  Model<R> m1 = m;
-  m1.inv_tau_phi = R(1);
-  collide_h(m1, h, phi, gx, gy, gz, lap, R(0), R(0), R(0));
+  h_equilibrium(m, h, phi, gx, gy, gz, lap);
   // g = g_eq(P0, u = 0) = w_i P0/T - K_i/2 with K_i = w_i (mu c_i.grad + c_i.F)/T.
   const R mu = m.mu_a * phi * (phi - R(1)) * (phi - R(0.5)) - m.mu_b * lap;
 #pragma unroll
@@ -417,9 +426,9 @@ __global__ void k_init(Args<S, R> a, const double *phi0, double P0, S *h0, S *wp
     const R cF = R(cx_of(i)) * m.Fx + R(cy_of(i)) * m.Fy + R(cz_of(i)) * m.Fz;
     const R K = wi * R(3) * (mu * cg + cF);
     const R gi = wi * R(3) * (R)P0 - R(0.5) * K;
-    h0[i * N + c] = (S)h[i];
-    a.g[i * N + c] = (S)gi;
-    if (i != 0 && ((lm >> opp_of(i)) & 1u)) wp0[(i - 1) * (long long)a.nw + rec] = (S)gi;
+    h0base[i * N + c] = (S)h[i];
+    a.g[i][c] = (S)gi;
+    if (i != 0 && ((lm >> opp_of(i)) & 1u)) wp0[(i - 1) * a.nw + rec] = (S)gi;
   }
 }
 

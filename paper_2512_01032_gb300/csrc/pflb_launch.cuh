@@ -45,12 +45,14 @@ template <class S, class R>
 static Args<S, R> make_args(Lattice &L) {
   Args<S, R> a;
   a.nx = L.nx; a.ny = L.ny; a.nz = L.nz; a.lz = L.lz;
-  a.N = L.N;
+  a.N = (int)L.N;
   a.nw = L.nw;
   const int rd = (int)(L.step & 1);
-  a.hin = (const S *)L.h[rd];
-  a.hout = (S *)L.h[rd ^ 1];
-  a.g = (S *)L.g;
+  for (int i = 0; i < Q; ++i) {
+    a.hin[i] = (const S *)L.h[rd] + (size_t)i * L.N;
+    a.hout[i] = (S *)L.h[rd ^ 1] + (size_t)i * L.N;
+    a.g[i] = (S *)L.g + (size_t)i * L.N;
+  }
   a.flags = L.flags;
   a.widx = L.widx;
   a.wmask = L.wmask;

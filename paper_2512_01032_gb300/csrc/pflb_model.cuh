@@ -215,74 +215,68 @@ __device__ __forceinline__ R delta_theta(const Model<R> &m, R phi, R gnorm, R la
   return m.gamma * m.theta_coef * gnorm * ((R(1) + s) * Y1 + (R(1) - s) * Y2);
 }
 
-// h collision (Eqs. 1-4): in place on h[].
+// Both collisions of one cell, in place on h[] and g[] (Eqs. 1-11):
+//   h: theta + delta-theta, h_eq = phi Gamma_i + theta w_i (c_i . n), BGK
+//      with 1/tau_phi; the rest population is closed as phi - sum_{i>0} h*_i
+//      (Eq. 1 conserves sum_i h_i = phi exactly; the closure keeps the
+//      stored sum free of the rounding bias of sum_i Gamma_i - 1).
+//   g: K_i (Eq. 6), E_i = w_i P/T + rho (Gamma_i - w_i), reading R2 of the
+//      filtered collision: g* = E + K/2 + (1 - 1/tau) Phi_i : Pi with
+//      Pi = sum c c (g - E + K/2).  Gamma_i - w_i is evaluated directly so
+//      that the heavy phase (rho = 1) does not cancel the pressure part.
+// Gamma_i is shared by the two sets.
 template <class R>
-__device__ __forceinline__ void collide_h(const Model<R> &m, R h[Q], R phi, R gx, R gy, R gz,
-                                          R lap, R ux, R uy, R uz) {
-  R gn2 = gx * gx + gy * gy + gz * gz;
-  R gnorm = sqrt_(gn2);
-  R inv = R(1) / (gnorm + m.eps);
-  R nx = gx * inv, ny = gy * inv, nz = gz * inv;
+__device__ __forceinline__ void collide(const Model<R> &m, R h[Q], R g[Q], const Macro<R> &mc,
+                                        R phi, R gx, R gy, R gz, R lap) {
+  const R ux = mc.ux, uy = mc.uy, uz = mc.uz;
+  // interface normal and theta (Eqs. 2-4)
+  const R gn2 = gx * gx + gy * gy + gz * gz;
+  const R gnorm = sqrt_(gn2);
+  const R inv = R(1) / (gnorm + m.eps);
   R th = m.theta_coef * (R(1) - R(4) * (phi - R(0.5)) * (phi - R(0.5)));
   if (m.mobility_corr) th += delta_theta(m, phi, gnorm, lap);
-  const R uu15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
+  const R thn = th * inv;  // theta * n = thn * grad
   const R om = m.inv_tau_phi;
-  // The relaxation conserves sum_i h_i = phi (sum_i h_eq_i = phi exactly).
-  // The rest population is closed from the others so that the stored sum
-  // carries one rounding instead of the bias of sum_i Gamma_i - 1.
-  R rest = phi;
-#pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    const R cu = R(cx_of(i)) * ux + R(cy_of(i)) * uy + R(cz_of(i)) * uz;
-    const R cn = R(cx_of(i)) * nx + R(cy_of(i)) * ny + R(cz_of(i)) * nz;
-    const R wi = R(w_of(i));
-    const R G = wi * (R(1) + R(3) * cu + R(4.5) * cu * cu - uu15);
-    const R heq = phi * G + th * wi * cn;
-    h[i] = h[i] - om * (h[i] - heq);
-    rest -= h[i];
-  }
-  h[0] = rest;
-}
-
-// Filtered hydrodynamic collision (Eqs. 5-11, reading: G_eq = E + K/2,
-// Pi = sum c c (g - g_eq)), in place on g[].
-template <class R>
-__device__ __forceinline__ void collide_g(const Model<R> &m, R g[Q], const Macro<R> &mc, R phi,
-                                          R gx, R gy, R gz) {
-  const R ux = mc.ux, uy = mc.uy, uz = mc.uz;
   const R uu15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
   const R ug = ux * gx + uy * gy + uz * gz;
   const R uF = ux * m.Fx + uy * m.Fy + uz * m.Fz;
   const R muT = R(3) * mc.mu;  // mu / T
   const R P3 = R(3) * mc.P;    // P / T
   R pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
-  // First pass: E_i + K_i/2 into g_out, and the non-equilibrium moments.
-  R base[Q];
+  R rest = phi;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const R c0 = R(cx_of(i)), c1 = R(cy_of(i)), c2 = R(cz_of(i));
+    const int c0 = cx_of(i), c1 = cy_of(i), c2 = cz_of(i);
     const R wi = R(w_of(i));
-    const R cu = c0 * ux + c1 * uy + c2 * uz;
-    // Gamma_i - w_i computed directly: rho*Gamma_i - w_i*rho would cancel
-    // in the heavy phase (rho = 1) and lose the small pressure part.
-    const R Gd = wi * (R(3) * cu + R(4.5) * cu * cu - uu15);
+    const R cu = R(c0) * ux + R(c1) * uy + R(c2) * uz;
+    const R Gd = wi * (cu * (R(3) + R(4.5) * cu) - uu15);  // Gamma_i - w_i
     const R G = wi + Gd;
-    const R cg = c0 * gx + c1 * gy + c2 * gz - ug;         // (c - u) . grad phi
-    const R cF = c0 * m.Fx + c1 * m.Fy + c2 * m.Fz - uF;   // (c - u) . F
+    // h
+    if (i != 0) {
+      const R cgr = R(c0) * gx + R(c1) * gy + R(c2) * gz;  // c . grad phi
+      const R heq = phi * G + (thn * wi) * cgr;
+      h[i] = h[i] + om * (heq - h[i]);
+      rest -= h[i];
+    }
+    // g
+    const R cg = R(c0) * gx + R(c1) * gy + R(c2) * gz - ug;        // (c - u) . grad phi
+    const R cF = R(c0) * m.Fx + R(c1) * m.Fy + R(c2) * m.Fz - uF;  // (c - u) . F
     const R K = (Gd * m.rho_dif + G * muT) * cg + R(3) * G * cF;
     const R E = wi * P3 + mc.rho * Gd;
-    const R neq = g[i] - E + R(0.5) * K;
-    base[i] = E + R(0.5) * K;
-    if (cx_of(i)) pxx += neq;
-    if (cy_of(i)) pyy += neq;
-    if (cz_of(i)) pzz += neq;
-    if (cx_of(i) * cy_of(i) > 0) pxy += neq;
-    if (cx_of(i) * cy_of(i) < 0) pxy -= neq;
-    if (cx_of(i) * cz_of(i) > 0) pxz += neq;
-    if (cx_of(i) * cz_of(i) < 0) pxz -= neq;
-    if (cy_of(i) * cz_of(i) > 0) pyz += neq;
-    if (cy_of(i) * cz_of(i) < 0) pyz -= neq;
+    const R bse = E + R(0.5) * K;
+    const R neq = g[i] - bse + K;  // g - (E - K/2)
+    g[i] = bse;
+    if (c0) pxx += neq;
+    if (c1) pyy += neq;
+    if (c2) pzz += neq;
+    if (c0 * c1 > 0) pxy += neq;
+    if (c0 * c1 < 0) pxy -= neq;
+    if (c0 * c2 > 0) pxz += neq;
+    if (c0 * c2 < 0) pxz -= neq;
+    if (c1 * c2 > 0) pyz += neq;
+    if (c1 * c2 < 0) pyz -= neq;
   }
+  h[0] = rest;
   // Phi_i : Pi = w_i / (2 T^2) (c_i c_i : Pi - T tr Pi)
   const R tau = tau_mix(m, phi);
   const R f = (R(1) - R(1) / tau) * R(4.5);
@@ -290,15 +284,33 @@ __device__ __forceinline__ void collide_g(const Model<R> &m, R g[Q], const Macro
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int c0 = cx_of(i), c1 = cy_of(i), c2 = cz_of(i);
-    R cc = R(0);
+    R cc = -tr3;
     if (c0) cc += pxx;
     if (c1) cc += pyy;
     if (c2) cc += pzz;
     if (c0 * c1) cc += R(2 * c0 * c1) * pxy;
     if (c0 * c2) cc += R(2 * c0 * c2) * pxz;
     if (c1 * c2) cc += R(2 * c1 * c2) * pyz;
-    g[i] = base[i] + f * R(w_of(i)) * (cc - tr3);
+    g[i] = g[i] + (f * R(w_of(i))) * cc;
   }
+}
+
+// h_eq (Eqs. 2-4) for initialisation.
+template <class R>
+__device__ __forceinline__ void h_equilibrium(const Model<R> &m, R h[Q], R phi, R gx, R gy, R gz,
+                                              R lap) {
+  const R gnorm = sqrt_(gx * gx + gy * gy + gz * gz);
+  R th = m.theta_coef * (R(1) - R(4) * (phi - R(0.5)) * (phi - R(0.5)));
+  if (m.mobility_corr) th += delta_theta(m, phi, gnorm, lap);
+  const R thn = th / (gnorm + m.eps);
+  R rest = phi;
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const R cgr = R(cx_of(i)) * gx + R(cy_of(i)) * gy + R(cz_of(i)) * gz;
+    h[i] = phi * R(w_of(i)) + (thn * R(w_of(i))) * cgr;
+    rest -= h[i];
+  }
+  h[0] = rest;
 }
 
 }  // namespace pflb
