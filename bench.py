@@ -135,7 +135,7 @@ def config_of(g, fluid):
     return {"workload": f"FP32 sessile droplet on a curved wall, {g.nx}x{g.ny}x{g.nz} D3Q19, "
                         f"solid sphere R=30, drop R=20, theta={THETA:g} deg, density ratio 1000",
             "lattice": [g.nx, g.ny, g.nz], "fluid_cells": int(fluid), "storage": "fp32",
-            "kernel": "fused z-marching (one launch per step, diagnostics on)",
+            "kernel": "fused z-marching, 32x4 tiles, 16 planes per block (one launch per step, diagnostics on)",
             "l2": "inputs larger than L2 (no flush)"}
 
 

@@ -56,9 +56,11 @@ enum { PFLB_STORAGE_FP64 = 0, PFLB_STORAGE_FP32 = 1 };
 enum { PFLB_FIELD_PHI = 0, PFLB_FIELD_RHO = 1, PFLB_FIELD_P = 2,
        PFLB_FIELD_UX = 3, PFLB_FIELD_UY = 4, PFLB_FIELD_UZ = 5 };
 
-/* Step kernels: one fused pass per step (default), or a phi pass followed
- * by a per-cell pass. */
-enum { PFLB_KERNEL_FUSED = 0, PFLB_KERNEL_TWOPASS = 1 };
+/* Step kernels: one fused z-marching pass per step (default), a phi pass
+ * followed by a per-cell pass, or the fused pass with h staged through
+ * shared memory by TMA (FP32 storage, nx a multiple of 4 and nx >= 64;
+ * otherwise it falls back to the default). */
+enum { PFLB_KERNEL_FUSED = 0, PFLB_KERNEL_TWOPASS = 1, PFLB_KERNEL_FUSED_TMA = 2 };
 
 /* Geometry, read during pflb_create only.
  *   solid       : host, nx*ny*nz bytes, nonzero = solid voxel.
@@ -159,8 +161,9 @@ pflb_status pflb_set_force(pflb_lattice *L, const double Fex[3]);
 pflb_status pflb_set_region(pflb_lattice *L, const int box[6]);
 
 /* Choose the step kernel and its launch shape: tile bx * by threads
- * (bx * by <= 256, 2 (bx+2) + 2 by <= bx * by) marching lz planes in z.
- * Zeros keep the current values. */
+ * (bx * by <= 256, 2 (bx+2) + 2 by <= bx * by) marching lz planes in z
+ * (the TMA kernel always uses 32 x 8 and takes only lz).  Defaults:
+ * 32 x 4 x 16.  Zeros keep the current values. */
 pflb_status pflb_set_kernel(pflb_lattice *L, int kind, int bx, int by, int lz);
 
 /* Advance nsteps time steps (asynchronous on the lattice stream). */
@@ -188,7 +191,9 @@ pflb_status pflb_step_diag(pflb_lattice *L, int64_t nsteps, pflb_diag_t *out);
 pflb_status pflb_read(pflb_lattice *L, int field, double *host_out);
 
 /* Diagnostics of the current state (synchronises).  Returns PFLB_ERR_NAN
- * (with *out filled) when a non-finite value was found. */
+ * (with *out filled) when a non-finite value was found, and
+ * PFLB_ERR_TIMEOUT (lattice poisoned) when a bounded wait inside a step
+ * kernel ran out; pflb_read and pflb_last_diag check the same flag. */
 pflb_status pflb_diag(pflb_lattice *L, pflb_diag_t *out);
 
 /* Number of steps taken since the last init. */

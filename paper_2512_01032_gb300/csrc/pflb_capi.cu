@@ -155,7 +155,7 @@ cudaError_t dev_alloc(Lattice *L, T **ptr, size_t count) {
 
 void free_all(Lattice *L) {
   void *ptrs[] = {L->h[0], L->h[1], L->g, L->wp[0], L->wp[1], L->flags, L->widx, L->wmask,
-                  L->wgeo, L->ghost, L->phi, L->diag, L->out, L->phi0};
+                  L->wgeo, L->ghost, L->phi, L->diag, L->out, L->phi0, L->err};
   for (void *p : ptrs)
     if (p) cudaFree(p);
 }
@@ -165,6 +165,49 @@ int64_t bytes_for(long long N, long long nw, int storage) {
   const int64_t r = e;
   return 3 * 19 * N * e + 2 * 18 * nw * e + N * (1 + 4) + nw * 4 + 5 * nw * r + 18 * nw * r +
          N * r + 96 * 8;
+}
+
+// TMA descriptors of the two h buffers (4-D: x, y, z, direction; box
+// 40 x 10 x 1 x 19 floats) for the staged step kernel.  Needs FP32 storage,
+// nx a multiple of 4 (16-byte row strides) and nx >= 64.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)ptr;
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+void make_tmaps(Lattice *L) {
+  L->tma_ok = false;
+  if (L->p.storage != PFLB_STORAGE_FP32 || L->nx % 4 != 0 || L->nx < 64) return;
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return;
+  const cuuint64_t dims[4] = {(cuuint64_t)L->nx, (cuuint64_t)L->ny, (cuuint64_t)L->nz, 19};
+  const cuuint64_t strides[3] = {(cuuint64_t)L->nx * 4, (cuuint64_t)L->nx * L->ny * 4,
+                                 (cuuint64_t)L->N * 4};
+  const cuuint32_t box[4] = {40, 10, 1, 19};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  for (int b = 0; b < 2; ++b) {
+    CUresult r = fn(&L->tmap[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, L->h[b], dims, strides, box,
+                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return;
+  }
+  L->tma_ok = true;
 }
 
 }  // namespace
@@ -248,6 +291,7 @@ pflb_status pflb_create(const pflb_geometry *geom, const pflb_params *params, vo
   A(&L->ghost, 18 * nw * Rb);
   A(&L->phi, N * Rb);
   A((void **)&L->diag, 96 * sizeof(double));
+  A((void **)&L->err, sizeof(int));
   if (e != cudaSuccess) {
     free_all(L);
     delete L;
@@ -269,10 +313,10 @@ pflb_status pflb_create(const pflb_geometry *geom, const pflb_params *params, vo
     e = cudaMemcpyAsync(L->wmask, hg.wmask.data(), nw * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && nw)
     e = cudaMemcpyAsync(L->wgeo, wgeo_src, 5 * nw * Rb, cudaMemcpyHostToDevice, st);
-  void *zero_bufs[] = {L->h[0], L->h[1], L->g, L->wp[0], L->wp[1], L->ghost, L->phi};
+  void *zero_bufs[] = {L->h[0], L->h[1], L->g, L->wp[0], L->wp[1], L->ghost, L->phi, L->err};
   size_t zero_len[] = {19 * N * E, 19 * N * E, 19 * N * E, 18 * nw * E, 18 * nw * E,
-                       18 * nw * Rb, N * Rb};
-  for (int k = 0; k < 7 && e == cudaSuccess; ++k)
+                       18 * nw * Rb, N * Rb, sizeof(int)};
+  for (int k = 0; k < 8 && e == cudaSuccess; ++k)
     if (zero_len[k]) e = cudaMemsetAsync(zero_bufs[k], 0, zero_len[k], st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
@@ -280,6 +324,7 @@ pflb_status pflb_create(const pflb_geometry *geom, const pflb_params *params, vo
     delete L;
     return fail(PFLB_ERR_CUDA, std::string("upload failed: ") + cudaGetErrorString(e));
   }
+  make_tmaps(L);
   *out = L;
   return PFLB_OK;
 }
@@ -367,7 +412,7 @@ pflb_status pflb_set_region(pflb_lattice *L, const int box[6]) {
 pflb_status pflb_set_kernel(pflb_lattice *L, int kind, int bx, int by, int lz) {
   pflb_status s = check_lattice(L);
   if (s != PFLB_OK) return s;
-  if (kind != PFLB_KERNEL_FUSED && kind != PFLB_KERNEL_TWOPASS)
+  if (kind != PFLB_KERNEL_FUSED && kind != PFLB_KERNEL_TWOPASS && kind != PFLB_KERNEL_FUSED_TMA)
     return fail(PFLB_ERR_ARG, "unknown kernel");
   const int nbx = bx > 0 ? bx : L->bx, nby = by > 0 ? by : L->by, nlz = lz > 0 ? lz : L->lz;
   if (nbx * nby > 256 || nbx < 1 || nby < 1)
@@ -400,10 +445,24 @@ pflb_status pflb_set_diag_every(pflb_lattice *L, int every) {
   return PFLB_OK;
 }
 
+// Reads the device error flag (synchronises): a bounded wait inside a
+// kernel ran out.
+static pflb_status check_device_flag(pflb_lattice *L) {
+  int flag = 0;
+  CK(L, cudaMemcpyAsync(&flag, L->err, sizeof flag, cudaMemcpyDeviceToHost, L->stream));
+  CK(L, cudaStreamSynchronize(L->stream));
+  if (flag) {
+    L->poisoned = true;
+    return fail(PFLB_ERR_TIMEOUT, "a bounded wait in the step kernel ran out; state is invalid");
+  }
+  return PFLB_OK;
+}
+
 static pflb_status fetch_diag(pflb_lattice *L, const double *dev, pflb_diag_t *out) {
   double d[32];
   CK(L, cudaMemcpyAsync(d, dev, sizeof d, cudaMemcpyDeviceToHost, L->stream));
-  CK(L, cudaStreamSynchronize(L->stream));
+  pflb_status fs = check_device_flag(L);
+  if (fs != PFLB_OK) return fs;
   std::memset(out, 0, sizeof *out);
   out->step = L->step;
   out->mass = d[pflb::D_MASS];
@@ -473,8 +532,7 @@ pflb_status pflb_read(pflb_lattice *L, int field, double *host_out) {
   CK(L, do_macro(L, true));
   CK(L, cudaMemcpyAsync(host_out, L->out + (size_t)field * L->N, (size_t)L->N * sizeof(double),
                         cudaMemcpyDeviceToHost, L->stream));
-  CK(L, cudaStreamSynchronize(L->stream));
-  return PFLB_OK;
+  return check_device_flag(L);
 }
 
 int64_t pflb_get_step(const pflb_lattice *L) { return L ? L->step : -1; }

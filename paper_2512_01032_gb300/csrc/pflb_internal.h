@@ -1,6 +1,7 @@
 // pflb_internal.h -- host-side lattice record shared by the C ABI and the
 // per-precision launchers.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <string>
@@ -29,12 +30,15 @@ struct Lattice {
   double *diag = nullptr;           // [32]
   double *out = nullptr;            // [6][N] lazily allocated
   double *phi0 = nullptr;           // [N] init scratch, lazily allocated
+  int *err = nullptr;               // device error flag (bounded waits that ran out)
+  CUtensorMap tmap[2];              // TMA maps of the two h buffers (staged kernel)
+  bool tma_ok = false;
   int64_t step = 0;
   int64_t ndiag = 0;          // diagnostic launches since init (ping-pong index)
   int64_t last_diag_step = -1;
   int diag_every = 0;         // pflb_step accumulates diagnostics every k-th step
   int kernel = PFLB_KERNEL_FUSED;
-  int bx = 32, by = 8, lz = 16;
+  int bx = 32, by = 4, lz = 16;
   int reg[6] = {0, 0, 0, 0, 0, 0};
   bool poisoned = false;
   int64_t dev_bytes = 0;

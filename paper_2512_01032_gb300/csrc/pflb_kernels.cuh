@@ -25,6 +25,11 @@ namespace pflb {
 
 enum { MODE_STEP = 0, MODE_MACRO = 1 };
 
+// Blocks per SM the fused kernels are compiled for (sets the register cap).
+#ifndef PFLB_MIN_BLOCKS
+#define PFLB_MIN_BLOCKS 2
+#endif
+
 template <class S, class R>
 struct Args {
   int nx, ny, nz, lz;
@@ -87,24 +92,43 @@ struct Nbr {
 template <class R>
 __device__ __forceinline__ bool finite_(R v) { return isfinite(v); }
 
-// Full update (or macro evaluation) of one fluid cell c at (x, y, z).
-// h[] holds the cell's streamed h populations, phi their sum, val[1..18]
-// the phi of the 18 neighbours (anything for solid ones).
+// Gather the g populations arriving at cell c (A-A): solid sources come
+// from the wall population buffer.
+template <class S, class R, bool ODD>
+__device__ __forceinline__ void gather_g(const Args<S, R> &a, int c, uint32_t lm, int rec,
+                                         const Nbr &nb, R g[Q]) {
+  if (lm == 0) {  // bulk cell: no solid link
+#pragma unroll
+    for (int k = 0; k < Q; ++k)
+      g[k] = ODD ? (R)Store<S>::ld(a.g[opp_of(k)] + (c + nb.off(opp_of(k))))
+                 : (R)Store<S>::ld(a.g[k] + c);
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+    if (k != 0 && ((lm >> opp_of(k)) & 1u)) {
+      g[k] = (R)a.wp_rd[(k - 1) * a.nw + rec];
+    } else if (!ODD) {
+      g[k] = (R)Store<S>::ld(a.g[k] + c);
+    } else {
+      g[k] = (R)Store<S>::ld(a.g[opp_of(k)] + (c + nb.off(opp_of(k))));
+    }
+  }
+}
+
+// Rest of the update (or macro evaluation) of one fluid cell c at (x, y, z)
+// once its populations are gathered: h[] and g[] hold the streamed
+// populations, phi = sum h, val[1..18] the phi of the 18 neighbours
+// (anything for solid ones), lm/rec the wall data (0 for bulk cells).
 template <class S, class R, bool ODD, int MODE, bool DIAG>
-__device__ __forceinline__ void update_cell(const Args<S, R> &a, int x, int y, int z, int c,
-                                            uint8_t f, R h[Q], R phi, R val[Q],
-                                            DiagAcc<R> &acc) {
+__device__ __forceinline__ void finish_cell(const Args<S, R> &a, int x, int y, int z, int c,
+                                            uint8_t f, uint32_t lm, int rec, const Nbr &nb,
+                                            R h[Q], R g[Q], R phi, R val[Q], DiagAcc<R> &acc) {
   const Model<R> &m = a.m;
-  Nbr nb;
-  nb.init(x, y, z, a.nx, a.ny, a.nz);
-  uint32_t lm = 0;
-  int rec = 0;
   val[0] = phi;
   R gx, gy, gz, lap;
   const bool wall = (f & F_WALL) != 0;
   if (wall) {
-    rec = a.widx[c];
-    lm = a.wmask[rec];
     const int nw = a.nw;
 #pragma unroll
     for (int i = 1; i < Q; ++i)
@@ -119,19 +143,6 @@ __device__ __forceinline__ void update_cell(const Args<S, R> &a, int x, int y, i
     }
   }
   cd_stencil(val, gx, gy, gz, lap);
-
-  // Gather g (A-A): solid sources come from the wall population buffer.
-  R g[Q];
-#pragma unroll
-  for (int k = 0; k < Q; ++k) {
-    if (k != 0 && ((lm >> opp_of(k)) & 1u)) {
-      g[k] = (R)a.wp_rd[(k - 1) * a.nw + rec];
-    } else if (!ODD) {
-      g[k] = (R)Store<S>::ld(a.g[k] + c);
-    } else {
-      g[k] = (R)Store<S>::ld(a.g[opp_of(k)] + (c + nb.off(opp_of(k))));
-    }
-  }
   const Macro<R> mc = macros(m, g, phi, gx, gy, gz, lap);
 
   if (DIAG) {
@@ -139,8 +150,8 @@ __device__ __forceinline__ void update_cell(const Args<S, R> &a, int x, int y, i
     if (phi >= R(0.5)) acc.v[D_NHEAVY] += R(1);
     if (phi > R(0.95)) { acc.v[D_PH] += mc.P; acc.v[D_NPH] += R(1); }
     if (phi < R(0.05)) { acc.v[D_PL] += mc.P; acc.v[D_NPL] += R(1); }
-    if (x >= a.reg[0] && x < a.reg[1] && y >= a.reg[2] && y < a.reg[3] && z >= a.reg[4] &&
-        z < a.reg[5])
+    if (z >= a.reg[4] && z < a.reg[5] && x >= a.reg[0] && x < a.reg[1] && y >= a.reg[2] &&
+        y < a.reg[3])
       acc.v[D_REGION] += phi;
     if (wall && phi >= R(0.25) && phi <= R(0.75)) {
       acc.v[D_CLN] += R(1);
@@ -149,7 +160,7 @@ __device__ __forceinline__ void update_cell(const Args<S, R> &a, int x, int y, i
     }
     const R u2 = mc.ux * mc.ux + mc.uy * mc.uy + mc.uz * mc.uz;
     acc.v[D_KIN] += R(0.5) * mc.rho * u2;
-    if (!(finite_(phi) && finite_(mc.P) && finite_(u2))) acc.v[D_NONFINITE] += R(1);
+    if (!finite_(phi + mc.P + u2)) acc.v[D_NONFINITE] += R(1);  // NaN/Inf propagate
     acc.umax = u2 > acc.umax ? u2 : acc.umax;  // squared; root taken at the flush
   }
   if (MODE == MODE_MACRO) {
@@ -167,6 +178,18 @@ __device__ __forceinline__ void update_cell(const Args<S, R> &a, int x, int y, i
 
   collide(m, h, g, mc, phi, gx, gy, gz, lap);
 
+  if (lm == 0) {  // bulk cell: plain streaming of both sets
+#pragma unroll
+    for (int i = 0; i < Q; ++i) Store<S>::st(a.hout[i] + (c + nb.off(i)), (S)h[i]);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if (!ODD)
+        Store<S>::st(a.g[opp_of(i)] + c, (S)g[i]);
+      else
+        Store<S>::st(a.g[i] + (c + nb.off(i)), (S)g[i]);
+    }
+    return;
+  }
   // h: push into the other buffer, halfway bounce-back at solid links.
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
@@ -207,42 +230,86 @@ __device__ __forceinline__ void update_cell(const Args<S, R> &a, int x, int y, i
   }
 }
 
-// Block reduction of the diagnostic partials into the device accumulator.
+// Full update (or macro evaluation) of one fluid cell: wall data, g
+// gather, then finish_cell.
+template <class S, class R, bool ODD, int MODE, bool DIAG>
+__device__ __forceinline__ void update_cell(const Args<S, R> &a, int x, int y, int z, int c,
+                                            uint8_t f, R h[Q], R phi, R val[Q],
+                                            DiagAcc<R> &acc) {
+  Nbr nb;
+  nb.init(x, y, z, a.nx, a.ny, a.nz);
+  uint32_t lm = 0;
+  int rec = 0;
+  if (f & F_WALL) {
+    rec = a.widx[c];
+    lm = a.wmask[rec];
+  }
+  R g[Q];
+  gather_g<S, R, ODD>(a, c, lm, rec, nb, g);
+  finish_cell<S, R, ODD, MODE, DIAG>(a, x, y, z, c, f, lm, rec, nb, h, g, phi, val, acc);
+}
+
+// Diagnostics are reduced in three levels: each cell's contributions (a
+// DiagAcc zeroed per cell) are summed over the warp with shuffles once per
+// plane into per-warp slots in shared memory (compute precision: FP32 work
+// stays off the slow FP64 pipe); at the end of the block the slots are
+// summed in FP64 and added to the device accumulator with FP64 atomics.
+// Nothing is carried in registers across the z march.
+constexpr int DIAG_MAX_WARPS = 8;
+
 template <class R>
-__device__ void flush_diag(double *diag, DiagAcc<R> &acc) {
-  __shared__ double red[32][D_COUNT];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nwarps = (blockDim.x + 31) >> 5;
-  double v[D_COUNT];
+__device__ __forceinline__ R warp_sum(R v) {
 #pragma unroll
-  for (int k = 0; k < D_UMAX; ++k) v[k] = (double)acc.v[k];
-  v[D_UMAX] = sqrt((double)acc.umax);
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <class R>
+__device__ __forceinline__ void diag_warp_add(R *slot, const DiagAcc<R> &d) {
+  const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int k = 0; k < D_COUNT; ++k) {
-    for (int o = 16; o > 0; o >>= 1) {
-      double t = __shfl_down_sync(0xffffffffu, v[k], o);
-      v[k] = (k == D_UMAX) ? fmax(v[k], t) : v[k] + t;
+  for (int k = 0; k < D_CLN; ++k) {
+    const R t = warp_sum(d.v[k]);
+    if (lane == 0) slot[k] += t;
+  }
+  if (__any_sync(0xffffffffu, d.v[D_CLN] != R(0))) {  // contact-line band cells (rare)
+#pragma unroll
+    for (int k = D_CLN; k <= D_CLZZ; ++k) {
+      const R t = warp_sum(d.v[k]);
+      if (lane == 0) slot[k] += t;
     }
   }
-  if (lane == 0)
-    for (int k = 0; k < D_COUNT; ++k) red[warp][k] = v[k];
-  __syncthreads();
-  if (warp == 0) {
 #pragma unroll
-    for (int k = 0; k < D_COUNT; ++k) {
-      double t = lane < nwarps ? red[lane][k] : 0.0;
-      for (int o = 16; o > 0; o >>= 1) {
-        double s = __shfl_down_sync(0xffffffffu, t, o);
-        t = (k == D_UMAX) ? fmax(t, s) : t + s;
-      }
-      if (lane == 0) {
-        if (k == D_UMAX) {
-          // non-negative doubles order like their bit patterns
-          atomicMax((unsigned long long *)(diag + k), (unsigned long long)__double_as_longlong(t));
-        } else if (t != 0.0) {
-          atomicAdd(diag + k, t);
-        }
-      }
+  for (int k = D_KIN; k < D_UMAX; ++k) {
+    const R t = warp_sum(d.v[k]);
+    if (lane == 0) slot[k] += t;
+  }
+  R um = d.umax;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) um = fmax(um, __shfl_xor_sync(0xffffffffu, um, o));
+  if (lane == 0) slot[D_UMAX] = slot[D_UMAX] > um ? slot[D_UMAX] : um;
+}
+
+template <class R>
+__device__ __forceinline__ void diag_block_zero(R (*wacc)[32]) {
+  for (int k = threadIdx.x; k < DIAG_MAX_WARPS * 32; k += blockDim.x) (&wacc[0][0])[k] = R(0);
+}
+
+template <class R>
+__device__ __forceinline__ void diag_block_flush(double *diag, R (*wacc)[32]) {
+  __syncthreads();
+  const int nwarps = (blockDim.x + 31) >> 5;
+  const int k = threadIdx.x;
+  if (k < D_COUNT) {
+    double t = 0.0;
+    for (int w = 0; w < nwarps; ++w)
+      t = (k == D_UMAX) ? fmax(t, (double)wacc[w][k]) : t + (double)wacc[w][k];
+    if (k == D_UMAX) {
+      // squared speed; non-negative doubles order like their bit patterns
+      atomicMax((unsigned long long *)(diag + k),
+                (unsigned long long)__double_as_longlong(sqrt(t)));
+    } else if (t != 0.0) {
+      atomicAdd(diag + k, t);
     }
   }
 }
@@ -277,6 +344,11 @@ template <class S, class R, bool ODD, int MODE, bool DIAG>
 __global__ void __launch_bounds__(256) k_cell(const __grid_constant__ Args<S, R> a) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   zero_next_diag(a);
+  __shared__ R wacc[DIAG_MAX_WARPS][32];
+  if (DIAG) {
+    diag_block_zero(wacc);
+    __syncthreads();
+  }
   DiagAcc<R> acc;
   acc.zero();
   if (c < a.N) {
@@ -304,7 +376,10 @@ __global__ void __launch_bounds__(256) k_cell(const __grid_constant__ Args<S, R>
       update_cell<S, R, ODD, MODE, DIAG>(a, x, y, z, c, f, h, phi, val, acc);
     }
   }
-  if (DIAG) flush_diag(a.diag, acc);
+  if (DIAG) {
+    diag_warp_add(wacc[threadIdx.x >> 5], acc);
+    diag_block_flush(a.diag, wacc);
+  }
 }
 
 // ------------------------------------------------------------ fused path
@@ -314,7 +389,7 @@ __global__ void __launch_bounds__(256) k_cell(const __grid_constant__ Args<S, R>
 // from the h populations (own cells and ring cells), so no phi field is
 // stored in HBM.
 template <class S, class R, bool ODD, bool DIAG>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, PFLB_MIN_BLOCKS)
     k_fused(const __grid_constant__ Args<S, R> a, int BX, int BY) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R *sphi = reinterpret_cast<R *>(smem_raw);
@@ -348,13 +423,15 @@ __global__ void __launch_bounds__(256, 2)
     if (rx >= 0) dst[ry * PW + rx] = cell_phi(a, rcol + sz * zw);
   };
 
-  DiagAcc<R> acc;
-  acc.zero();
+  __shared__ R wacc[DIAG_MAX_WARPS][32];
+  if (DIAG) diag_block_zero(wacc);  // first use follows a barrier below
   plane(zb - 1);
   plane(zb);
   for (int z = zb; z < ze; ++z) {
     plane(z + 1);
     __syncthreads();
+    DiagAcc<R> acc;
+    acc.zero();
     if (valid) {
       const int c = col + sz * z;
       const uint8_t f = a.flags[c];
@@ -375,9 +452,10 @@ __global__ void __launch_bounds__(256, 2)
         update_cell<S, R, ODD, MODE_STEP, DIAG>(a, gx, gy, z, c, f, h, phi, val, acc);
       }
     }
+    if (DIAG && active) diag_warp_add(wacc[tid >> 5], acc);
     __syncthreads();
   }
-  if (DIAG) flush_diag(a.diag, acc);
+  if (DIAG) diag_block_flush(a.diag, wacc);
 }
 
 // ------------------------------------------------------------ init

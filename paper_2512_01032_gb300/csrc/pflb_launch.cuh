@@ -1,6 +1,9 @@
 // pflb_launch.cuh -- per-precision kernel launchers (included by one
 // translation unit per storage type).
 #pragma once
+#include <type_traits>
+
+#include "pflb_async.cuh"
 #include "pflb_internal.h"
 #include "pflb_kernels.cuh"
 
@@ -89,8 +92,33 @@ cudaError_t launch_init(Lattice &L, const double *d_phi0, double P0) {
   return cudaGetLastError();
 }
 
+// The staged kernel (FP32, x extent a multiple of 4 and at least 64).
+inline bool async_eligible(const Lattice &L) {
+  return L.kernel == PFLB_KERNEL_FUSED_TMA && L.p.storage == PFLB_STORAGE_FP32 && L.tma_ok;
+}
+
+template <bool ODD, bool DIAG>
+static cudaError_t launch_async_t(Lattice &L, Args<float, float> &a) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_fused_async<ODD, DIAG>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AB_SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_fused_async<ODD, DIAG>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  dim3 grid((L.nx + AB_X - 1) / AB_X, (L.ny + AB_Y - 1) / AB_Y, (L.nz + L.lz - 1) / L.lz);
+  k_fused_async<ODD, DIAG><<<grid, AB_X * AB_Y, AB_SMEM, L.stream>>>(a, L.tmap[L.step & 1], L.err);
+  return cudaGetLastError();
+}
+
 template <class S, class R, bool ODD, bool DIAG>
 static cudaError_t launch_fused_t(Lattice &L, Args<S, R> &a) {
+  if constexpr (std::is_same<S, float>::value && std::is_same<R, float>::value) {
+    if (async_eligible(L)) return launch_async_t<ODD, DIAG>(L, a);
+  }
   const int bx = L.bx, by = L.by;
   dim3 grid((L.nx + bx - 1) / bx, (L.ny + by - 1) / by, (L.nz + L.lz - 1) / L.lz);
   const size_t smem = 3 * (size_t)(bx + 2) * (by + 2) * sizeof(R);
@@ -119,7 +147,7 @@ cudaError_t launch_step(Lattice &L, bool diag) {
     a.diag = L.diag + 32 * (L.ndiag & 1);
     a.diag_zero = L.diag + 32 * ((L.ndiag + 1) & 1);
   }
-  if (L.kernel == PFLB_KERNEL_FUSED) {
+  if (L.kernel == PFLB_KERNEL_FUSED || L.kernel == PFLB_KERNEL_FUSED_TMA) {
     if (odd) e = diag ? launch_fused_t<S, R, true, true>(L, a) : launch_fused_t<S, R, true, false>(L, a);
     else e = diag ? launch_fused_t<S, R, false, true>(L, a) : launch_fused_t<S, R, false, false>(L, a);
   } else {

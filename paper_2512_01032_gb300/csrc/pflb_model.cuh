@@ -113,12 +113,24 @@ template <class S> __device__ __forceinline__ S ld_ro(const S *p) { return __ldg
 template <class R> __device__ __forceinline__ R rsqrt_(R x);
 template <> __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
 template <> __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+// Square root, reciprocal, quotient and tanh: IEEE versions in FP64 (the
+// parity path); in FP32, short hardware-approximation forms (a few ulp,
+// well inside the FP32 tolerance of the step) that cost a handful of
+// instructions instead of the correctly rounded sequences.
 template <class R> __device__ __forceinline__ R sqrt_(R x);
 template <> __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
-template <> __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+template <> __device__ __forceinline__ float sqrt_(float x) {
+  return x > 0.0f ? x * rsqrtf(x) : 0.0f;
+}
+template <class R> __device__ __forceinline__ R div_(R a, R b);
+template <> __device__ __forceinline__ double div_(double a, double b) { return a / b; }
+template <> __device__ __forceinline__ float div_(float a, float b) { return __fdividef(a, b); }
 template <class R> __device__ __forceinline__ R tanh_(R x);
 template <> __device__ __forceinline__ double tanh_(double x) { return tanh(x); }
-template <> __device__ __forceinline__ float tanh_(float x) { return tanhf(x); }
+template <> __device__ __forceinline__ float tanh_(float x) {
+  // tanh x = 1 - 2 / (e^{2x} + 1); saturates correctly at +-inf
+  return 1.0f - __fdividef(2.0f, __expf(2.0f * x) + 1.0f);
+}
 template <class R> __device__ __forceinline__ R abs_(R x);
 template <> __device__ __forceinline__ double abs_(double x) { return fabs(x); }
 template <> __device__ __forceinline__ float abs_(float x) { return fabsf(x); }
@@ -156,7 +168,7 @@ __device__ __forceinline__ void wall_ghosts(const Model<R> &m, R phi, R gx, R gy
   R gn = gx * nwx + gy * nwy + gz * nwz;
   R tx = gx - gn * nwx, ty = gy - gn * nwy, tz = gz - gn * nwz;
   R tn2 = tx * tx + ty * ty + tz * tz;
-  R inv = tn2 >= R(1e-20) ? R(1) / sqrt_(tn2) : R(0);
+  R inv = tn2 >= R(1e-20) ? div_(R(1), sqrt_(tn2)) : R(0);
   tx *= inv; ty *= inv; tz *= inv;
   R wx = -cth * nwx + sth * tx, wy = -cth * nwy + sth * ty, wz = -cth * nwz + sth * tz;
   R s = R(2) * phi - R(1);
@@ -166,7 +178,7 @@ __device__ __forceinline__ void wall_ghosts(const Model<R> &m, R phi, R gx, R gy
     if (!((links >> i) & 1u)) continue;
     R d = wx * R(cx_of(i)) + wy * R(cy_of(i)) + wz * R(cz_of(i));
     R tb = tanh_(m.two_over_W * d);
-    R fresh = R(0.5) * (R(1) + (s + tb) / (R(1) + s * tb));
+    R fresh = R(0.5) * (R(1) + div_(s + tb, R(1) + s * tb));
     val[i] = m.blend * val[i] + (R(1) - m.blend) * fresh;
   }
 }
@@ -190,7 +202,7 @@ __device__ __forceinline__ Macro<R> macros(const Model<R> &m, const R g[Q], R ph
   jx = (g[1] - g[2]) + ((g[7] - g[8]) + (g[9] - g[10])) + ((g[11] - g[12]) + (g[13] - g[14]));
   jy = (g[3] - g[4]) + ((g[7] - g[8]) - (g[9] - g[10])) + ((g[15] - g[16]) + (g[17] - g[18]));
   jz = (g[5] - g[6]) + ((g[11] - g[12]) - (g[13] - g[14])) + ((g[15] - g[16]) - (g[17] - g[18]));
-  R irho = R(1) / r.rho;
+  R irho = div_(R(1), r.rho);
   r.ux = (jx + R(0.5) * (r.mu * gx + m.Fx)) * irho;
   r.uy = (jy + R(0.5) * (r.mu * gy + m.Fy)) * irho;
   r.uz = (jz + R(0.5) * (r.mu * gz + m.Fz)) * irho;
@@ -211,7 +223,7 @@ template <class R>
 __device__ __forceinline__ R delta_theta(const Model<R> &m, R phi, R gnorm, R lap) {
   R Y1 = fminf_(clamp01_((phi - m.phi_M) * m.inv_D), clamp01_((R(1) - phi) * m.inv_D));
   R Y2 = fminf_(clamp01_(phi * m.inv_D), clamp01_((m.phi_m - phi) * m.inv_D));
-  R s = lap / abs_(lap + m.eps);
+  R s = div_(lap, abs_(lap + m.eps));
   return m.gamma * m.theta_coef * gnorm * ((R(1) + s) * Y1 + (R(1) - s) * Y2);
 }
 
@@ -232,7 +244,7 @@ __device__ __forceinline__ void collide(const Model<R> &m, R h[Q], R g[Q], const
   // interface normal and theta (Eqs. 2-4)
   const R gn2 = gx * gx + gy * gy + gz * gz;
   const R gnorm = sqrt_(gn2);
-  const R inv = R(1) / (gnorm + m.eps);
+  const R inv = div_(R(1), gnorm + m.eps);
   R th = m.theta_coef * (R(1) - R(4) * (phi - R(0.5)) * (phi - R(0.5)));
   if (m.mobility_corr) th += delta_theta(m, phi, gnorm, lap);
   const R thn = th * inv;  // theta * n = thn * grad
@@ -279,7 +291,7 @@ __device__ __forceinline__ void collide(const Model<R> &m, R h[Q], R g[Q], const
   h[0] = rest;
   // Phi_i : Pi = w_i / (2 T^2) (c_i c_i : Pi - T tr Pi)
   const R tau = tau_mix(m, phi);
-  const R f = (R(1) - R(1) / tau) * R(4.5);
+  const R f = (R(1) - div_(R(1), tau)) * R(4.5);
   const R tr3 = (pxx + pyy + pzz) * R(1.0 / 3.0);
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
@@ -302,7 +314,7 @@ __device__ __forceinline__ void h_equilibrium(const Model<R> &m, R h[Q], R phi, 
   const R gnorm = sqrt_(gx * gx + gy * gy + gz * gz);
   R th = m.theta_coef * (R(1) - R(4) * (phi - R(0.5)) * (phi - R(0.5)));
   if (m.mobility_corr) th += delta_theta(m, phi, gnorm, lap);
-  const R thn = th / (gnorm + m.eps);
+  const R thn = div_(th, gnorm + m.eps);
   R rest = phi;
 #pragma unroll
   for (int i = 1; i < Q; ++i) {

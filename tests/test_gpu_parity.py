@@ -114,7 +114,7 @@ def test_ragged_and_tiny_lattices(dims):
         _compare(G, Orc, [1, 9], storage, 2 * p["sigma"] / init["R"], f"ragged{dims}")
 
 
-@pytest.mark.parametrize("tile", [(32, 8, 16), (64, 4, 7), (16, 16, 3), (32, 4, 32), (8, 8, 5)])
+@pytest.mark.parametrize("tile", [(32, 8, 16), (64, 4, 7), (16, 16, 3), (32, 4, 32), (8, 8, 5), (16, 8, 4)])
 def test_tile_shapes_bitwise_identical(tile):
     """Every launch shape of the fused kernel gives the same bits as the
     default one (FP32 storage)."""
@@ -173,3 +173,87 @@ def test_full_size_128_conservation_fp32():
     assert d1["nonfinite"] == 0
     assert abs(d1["mass"] - d0["mass"]) / d0["mass"] < 2e-5
     assert d1["u_max"] < 0.05
+
+
+@pytest.mark.parametrize("dims", [(68, 13, 9), (64, 8, 5), (96, 40, 7), (128, 3, 4)])
+def test_staged_kernel_matches_plain_bitwise(dims):
+    """The fused kernel with TMA staging of h (FP32, nx a multiple of 4,
+    nx >= 64) gives the same bits as the fused kernel without staging,
+    including partial tiles, periodic wrap of the staged rows in x and y and
+    walls; and it matches the oracle within the FP32 tolerance."""
+    import synth
+    from paper_2512_01032_gb300 import pflb
+    nx, ny, nz = dims
+    shapes = [synth.Plane((0, 0, 0.5), (0, 0, 1))] if nz > 3 else []
+    shapes.append(synth.Box((nx // 2, 0, 0), (nx // 2 + 3, max(1, ny // 3), nz)))
+    g = synth.Geometry(nx, ny, nz, shapes, theta_deg=70.0)
+    p = dict(synth.sessile_sphere_params(70.0))
+    init = dict(shape=0, center=(nx / 2.0 - 5.37, ny / 2.0 - 0.21, nz / 2.0 + 0.13),
+                R=max(1.5, min(ny, nz) / 2.5))
+    out = []
+    for kind in (pflb.KERNEL_FUSED_TMA, pflb.KERNEL_FUSED):
+        L = pflb.Lattice(nx, ny, nz, solid=g.solid, wall_normal=g.normals(),
+                         theta_cells=g.theta(), storage="fp32", **p)
+        L.set_kernel(kind, 0, 0, 3)
+        L.init_tanh(0, init["center"], init["R"])
+        L.step(7)
+        out.append({k: L.read(k) for k in ("phi", "P", "ux")})
+    for k in out[0]:
+        assert np.array_equal(out[0][k], out[1][k]), (dims, k)
+    G, Orc = CS.make_pair(g, p, init, storage="fp32", kernel=pflb.KERNEL_FUSED_TMA, tile=(0, 0, 3))
+    _compare(G, Orc, [1, 7], "fp32", 2 * p["sigma"] / init["R"], f"staged{dims}")
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
+def test_diagnostics_match_oracle_fields(storage, kernel):
+    """The FP64 diagnostics reduced inside the step kernel (and by the
+    macro pass) equal the same sums taken over the oracle's fields: mass,
+    phase volume, mean pressure of each bulk phase, max |u|, kinetic
+    energy, the contact-line band statistics and a region mass."""
+    import synth
+    from paper_2512_01032_gb300 import pflb
+    g, p, init = synth.sessile_sphere(64, 60.0)
+    G, Orc = CS.make_pair(g, p, init, storage=storage, kernel=kernel)
+    box = (10, 40, 5, 60, 20, 50)
+    G.set_region(box)
+    G.set_diag_every(1)
+    G.step(6)
+    Orc.step(5)
+    d_step = G.last_diag()          # state consumed by step 5
+    assert d_step["step"] == 5
+    ref = Orc.macros()
+    d_read = None
+    Orc.step(1)
+    ref6 = Orc.macros()
+    d_read = G.diag()               # state after 6 steps (macro pass)
+    tol = 1e-12 if storage == "fp64" else 2e-6
+
+    def expect(m):
+        phi, P = m["phi"], m["P"]
+        fluid = g.solid == 0
+        u2 = m["ux"] ** 2 + m["uy"] ** 2 + m["uz"] ** 2
+        wall = g.wall_nodes3().reshape(-1)
+        cl = wall & (phi >= 0.25) & (phi <= 0.75)
+        Z, Y, X = np.meshgrid(np.arange(g.nz), np.arange(g.ny), np.arange(g.nx), indexing="ij")
+        X, Y, Z = X.reshape(-1), Y.reshape(-1), Z.reshape(-1)
+        reg = (X >= box[0]) & (X < box[1]) & (Y >= box[2]) & (Y < box[3]) & (Z >= box[4]) & (Z < box[5])
+        return dict(mass=phi[fluid].sum(), n_heavy=float(((phi >= 0.5) & fluid).sum()),
+                    p_heavy=P[fluid & (phi > 0.95)].mean(), p_light=P[fluid & (phi < 0.05)].mean(),
+                    u_max=np.sqrt(u2[fluid].max()), kinetic=(0.5 * m["rho"] * u2)[fluid].sum(),
+                    cl_count=float(cl.sum()), cl_mean=[X[cl].mean(), Y[cl].mean(), Z[cl].mean()],
+                    region_mass=phi[fluid & reg].sum())
+
+    for d, m in ((d_step, ref), (d_read, ref6)):
+        e = expect(m)
+        assert abs(d["mass"] - e["mass"]) <= tol * e["mass"]
+        assert abs(d["region_mass"] - e["region_mass"]) <= tol * max(e["region_mass"], 1.0)
+        assert d["n_heavy"] == e["n_heavy"]
+        assert d["cl_count"] == e["cl_count"] and d["cl_count"] > 0
+        assert np.allclose(d["cl_mean"], e["cl_mean"], rtol=1e-12)
+        ps = 2 * p["sigma"] / init["R"]
+        assert abs(d["p_heavy"] - e["p_heavy"]) <= max(tol, 1e-5) * ps
+        assert abs(d["p_light"] - e["p_light"]) <= max(tol, 1e-5) * ps
+        assert abs(d["u_max"] - e["u_max"]) <= TOL_U[storage]
+        assert abs(d["kinetic"] - e["kinetic"]) <= 1e-4 * e["kinetic"] + 1e-15
+        assert d["nonfinite"] == 0
