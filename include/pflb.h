@@ -214,6 +214,36 @@ int64_t pflb_estimate_bytes(const pflb_geometry *geom, int storage);
 pflb_status pflb_save(pflb_lattice *L, const char *path);
 pflb_status pflb_load(pflb_lattice *L, const char *path);
 
+/* Allocation-free field and diagnostic pass over caller-owned populations.
+ * No counterpart in the paper: this serves callers that cannot allocate
+ * device memory -- code whose device memory belongs to another allocator
+ * (a framework's memory pool that must account for every byte) or that runs
+ * in a latency-critical loop where cudaMalloc's implicit device
+ * synchronisation is not acceptable.  It calls no cudaMalloc, cudaFree or
+ * other allocating routine; its scratch (the phi field and the FP64
+ * diagnostic accumulators) lives in file-scope device arrays sized for at
+ * most 2^20 cells (about 4 MiB, held by every GPU that loads the library
+ * until the process exits).
+ *   nx, ny, nz : wall-free periodic lattice, nx*ny*nz <= 2^20, else
+ *                PFLB_ERR_ARG with a message naming the limit.
+ *   h_dev, g_dev : device, FP32, [19][N] each (direction-major, x fastest),
+ *                slot i holding the population arriving in direction i (the
+ *                layout pflb_save writes after an even number of steps).
+ *   params     : model parameters (host, read during the call).
+ *   fields_dev : device, 6*N doubles (phi, rho, P, ux, uy, uz), or NULL.
+ *   diag_out   : host, or NULL (at least one output); region_mass is the
+ *                whole box, the contact-line fields are zero, step is -1.
+ *   cuda_stream: stream to order the work on (NULL = legacy default); the
+ *                call synchronises it when diag_out is given.
+ * The first call on a device looks up the scratch addresses for that device
+ * (cudaGetSymbolAddress with the device current); make that first call
+ * before any stream capture.  Every call shares the same scratch, cleared at
+ * the start of each call: calls that overlap on the GPU (different streams
+ * or threads) race and must be serialised by the caller. */
+pflb_status pflb_fields_noalloc(int nx, int ny, int nz, const float *h_dev, const float *g_dev,
+                                const pflb_params *params, double *fields_dev,
+                                pflb_diag_t *diag_out, void *cuda_stream);
+
 /* Free the lattice (synchronises its stream first).  NULL is ignored. */
 void pflb_destroy(pflb_lattice *L);
 

@@ -212,6 +212,8 @@ void make_tmaps(Lattice *L) {
 
 }  // namespace
 
+void pflb::set_last_error(const char *msg) { g_err = msg ? msg : ""; }
+
 extern "C" {
 
 void pflb_default_params(pflb_params *p) {

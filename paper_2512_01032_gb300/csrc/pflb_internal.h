@@ -44,6 +44,9 @@ struct Lattice {
   int64_t dev_bytes = 0;
 };
 
+// Sets the thread-local message returned by pflb_last_error().
+void set_last_error(const char *msg);
+
 // Per-precision launchers (pflb_launch.cuh, instantiated per storage type).
 // All enqueue work on L.stream; none synchronises.
 template <class S, class R> cudaError_t launch_init(Lattice &L, const double *d_phi0, double P0);

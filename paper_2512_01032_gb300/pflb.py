@@ -123,6 +123,9 @@ def load(build_if_missing: bool = True):
     lib.pflb_load.restype = st
     lib.pflb_destroy.argtypes = [C.c_void_p]
     lib.pflb_destroy.restype = None
+    lib.pflb_fields_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                        _P(Params), C.c_void_p, _P(Diag), C.c_void_p]
+    lib.pflb_fields_noalloc.restype = st
     lib.pflb_last_error.argtypes = []
     lib.pflb_last_error.restype = C.c_char_p
     _lib = lib
@@ -180,6 +183,20 @@ def make_geometry(nx, ny, nz, solid=None, wall_normal=None, theta_cells=None):
                  nw.ctypes.data_as(_d) if nw is not None else None,
                  th.ctypes.data_as(_d) if th is not None else None)
     return g, (s, nw, th)
+
+
+def fields_noalloc(nx, ny, nz, h_ptr: int, g_ptr: int, params: Params, fields_ptr=None,
+                   stream=None, want_diag=True):
+    """pflb_fields_noalloc on caller-owned device arrays (raw device
+    pointers, e.g. ``tensor.data_ptr()``); returns the diagnostics dict or
+    None.  See include/pflb.h for the contract."""
+    d = Diag()
+    _check(load().pflb_fields_noalloc(int(nx), int(ny), int(nz), C.c_void_p(h_ptr),
+                                      C.c_void_p(g_ptr), C.byref(params),
+                                      C.c_void_p(fields_ptr) if fields_ptr else None,
+                                      C.byref(d) if want_diag else None,
+                                      C.c_void_p(_stream_handle(stream))))
+    return d.as_dict() if want_diag else None
 
 
 def estimate_bytes(nx, ny, nz, solid=None, storage=STORAGE_FP32) -> int:
