@@ -48,9 +48,12 @@ typedef enum {
   PFLB_ERR_STATE = 7    /* lattice poisoned by an earlier error */
 } pflb_status;
 
-/* Population storage (the collision always computes in FP32 for FP32
- * storage and in FP64 for FP64 storage). */
-enum { PFLB_STORAGE_FP64 = 0, PFLB_STORAGE_FP32 = 1 };
+/* Population storage.  The collision computes in FP64 for FP64 storage and
+ * in FP32 otherwise.  The 16-bit formats store weight-scaled deviations:
+ * h_i / w_i - 1/2 and g_i / w_i (bytes per cell and step: 305 at FP32,
+ * 153 at FP16/BF16, 609 at FP64). */
+enum { PFLB_STORAGE_FP64 = 0, PFLB_STORAGE_FP32 = 1, PFLB_STORAGE_FP16 = 2,
+       PFLB_STORAGE_BF16 = 3 };
 
 /* Fields for pflb_read. */
 enum { PFLB_FIELD_PHI = 0, PFLB_FIELD_RHO = 1, PFLB_FIELD_P = 2,

@@ -5,9 +5,12 @@
 // (solid, wall node), a wall-node list in cell order with each node's
 // solid-link bits, wall normal and contact angle (Sec. II B), then
 // everything is uploaded once.  Stepping only enqueues kernels.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <type_traits>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -44,18 +47,43 @@ pflb_status cuda_fail(Lattice *L, cudaError_t e, const char *what) {
 
 bool is_fp64(const Lattice *L) { return L->p.storage == PFLB_STORAGE_FP64; }
 
+// Storage-type dispatch (compute in FP64 for FP64 storage, else FP32).
+template <class F>
+cudaError_t dispatch(Lattice *L, F &&f) {
+  switch (L->p.storage) {
+    case PFLB_STORAGE_FP64: return f((double *)nullptr, (double *)nullptr);
+    case PFLB_STORAGE_FP32: return f((float *)nullptr, (float *)nullptr);
+    case PFLB_STORAGE_FP16: return f((__half *)nullptr, (float *)nullptr);
+    default: return f((__nv_bfloat16 *)nullptr, (float *)nullptr);
+  }
+}
 cudaError_t do_init(Lattice *L, const double *d_phi0, double P0) {
-  return is_fp64(L) ? pflb::launch_init<double, double>(*L, d_phi0, P0)
-                    : pflb::launch_init<float, float>(*L, d_phi0, P0);
+  return dispatch(L, [&](auto *s, auto *r) {
+    using S = std::remove_pointer_t<decltype(s)>;
+    using R = std::remove_pointer_t<decltype(r)>;
+    return pflb::launch_init<S, R>(*L, d_phi0, P0);
+  });
 }
 cudaError_t do_step(Lattice *L, bool diag) {
-  return is_fp64(L) ? pflb::launch_step<double, double>(*L, diag)
-                    : pflb::launch_step<float, float>(*L, diag);
+  return dispatch(L, [&](auto *s, auto *r) {
+    using S = std::remove_pointer_t<decltype(s)>;
+    using R = std::remove_pointer_t<decltype(r)>;
+    return pflb::launch_step<S, R>(*L, diag);
+  });
 }
 cudaError_t do_macro(Lattice *L, bool fields) {
-  return is_fp64(L) ? pflb::launch_macro<double, double>(*L, fields)
-                    : pflb::launch_macro<float, float>(*L, fields);
+  return dispatch(L, [&](auto *s, auto *r) {
+    using S = std::remove_pointer_t<decltype(s)>;
+    using R = std::remove_pointer_t<decltype(r)>;
+    return pflb::launch_macro<S, R>(*L, fields);
+  });
 }
+size_t storage_bytes(int storage) {
+  return storage == PFLB_STORAGE_FP64 ? 8 : (storage == PFLB_STORAGE_FP32 ? 4 : 2);
+}
+size_t compute_bytes(int storage) { return storage == PFLB_STORAGE_FP64 ? 8 : 4; }
+// h slots per cell: the 16-bit formats keep the rest population's remainder.
+size_t h_slots_of(int storage) { return storage_bytes(storage) == 2 ? 20 : 19; }
 
 pflb_status check_lattice(const pflb_lattice *L) {
   if (!L) return fail(PFLB_ERR_ARG, "null lattice");
@@ -72,7 +100,7 @@ pflb_status check_params(const pflb_params *p) {
   if (!(p->rho_H > 0) || !(p->rho_L > 0)) return fail(PFLB_ERR_ARG, "need rho_H, rho_L > 0");
   if (!(p->blend >= 0 && p->blend <= 1)) return fail(PFLB_ERR_ARG, "need 0 <= blend <= 1");
   if (!(p->D > 0) || !(p->F_width > 0)) return fail(PFLB_ERR_ARG, "need D > 0, F_width > 0");
-  if (p->storage != PFLB_STORAGE_FP64 && p->storage != PFLB_STORAGE_FP32)
+  if (p->storage < PFLB_STORAGE_FP64 || p->storage > PFLB_STORAGE_BF16)
     return fail(PFLB_ERR_ARG, "unknown storage");
   if (p->F_mode != 0 && p->F_mode != 1) return fail(PFLB_ERR_ARG, "F_mode must be 0 or 1");
   return PFLB_OK;
@@ -161,10 +189,10 @@ void free_all(Lattice *L) {
 }
 
 int64_t bytes_for(long long N, long long nw, int storage) {
-  const int64_t e = storage == PFLB_STORAGE_FP64 ? 8 : 4;
-  const int64_t r = e;
-  return 3 * 19 * N * e + 2 * 18 * nw * e + N * (1 + 4) + nw * 4 + 5 * nw * r + 18 * nw * r +
-         N * r + 96 * 8;
+  const int64_t e = (int64_t)storage_bytes(storage);
+  const int64_t r = (int64_t)compute_bytes(storage);
+  return (2 * (int64_t)h_slots_of(storage) + 19) * N * e + 2 * 18 * nw * e + N * (1 + 4) +
+         nw * 4 + 5 * nw * r + 18 * nw * r + N * r + 96 * 8 + 4;
 }
 
 // TMA descriptors of the two h buffers (4-D: x, y, z, direction; box
@@ -261,7 +289,7 @@ pflb_status pflb_create(const pflb_geometry *geom, const pflb_params *params, vo
   L->N = (long long)L->nx * L->ny * L->nz;
   L->p = *params;
   L->stream = (cudaStream_t)cuda_stream;
-  L->elem = is_fp64(L) ? 8 : 4;
+  L->elem = storage_bytes(L->p.storage);
   L->reg[1] = L->nx; L->reg[3] = L->ny; L->reg[5] = L->nz;
   L->lz = L->nz < 16 ? L->nz : 16;
 
@@ -274,15 +302,16 @@ pflb_status pflb_create(const pflb_geometry *geom, const pflb_params *params, vo
   }
   L->nw = (int)hg.wmask.size();
   const size_t N = (size_t)L->N, nw = (size_t)L->nw;
-  const size_t E = L->elem, Rb = L->elem;
+  const size_t E = L->elem, Rb = compute_bytes(L->p.storage);
   cudaError_t e = cudaSuccess;
   auto A = [&](void **p, size_t bytes) {
     if (e != cudaSuccess) return;
     e = cudaMalloc(p, bytes ? bytes : 1);
     if (e == cudaSuccess) L->dev_bytes += (int64_t)bytes;
   };
-  A(&L->h[0], 19 * N * E);
-  A(&L->h[1], 19 * N * E);
+  const size_t HS = h_slots_of(L->p.storage);
+  A(&L->h[0], HS * N * E);
+  A(&L->h[1], HS * N * E);
   A(&L->g, 19 * N * E);
   A(&L->wp[0], 18 * nw * E);
   A(&L->wp[1], 18 * nw * E);
@@ -316,7 +345,7 @@ pflb_status pflb_create(const pflb_geometry *geom, const pflb_params *params, vo
   if (e == cudaSuccess && nw)
     e = cudaMemcpyAsync(L->wgeo, wgeo_src, 5 * nw * Rb, cudaMemcpyHostToDevice, st);
   void *zero_bufs[] = {L->h[0], L->h[1], L->g, L->wp[0], L->wp[1], L->ghost, L->phi, L->err};
-  size_t zero_len[] = {19 * N * E, 19 * N * E, 19 * N * E, 18 * nw * E, 18 * nw * E,
+  size_t zero_len[] = {HS * N * E, HS * N * E, 19 * N * E, 18 * nw * E, 18 * nw * E,
                        18 * nw * Rb, N * Rb, sizeof(int)};
   for (int k = 0; k < 8 && e == cudaSuccess; ++k)
     if (zero_len[k]) e = cudaMemsetAsync(zero_bufs[k], 0, zero_len[k], st);
@@ -566,8 +595,10 @@ pflb_status pflb_save(pflb_lattice *L, const char *path) {
   if (!path) return fail(PFLB_ERR_ARG, "null path");
   const int rd = (int)(L->step & 1);
   const size_t N = (size_t)L->N, nw = (size_t)L->nw, E = L->elem;
+  const size_t Rb = compute_bytes(L->p.storage);
   std::vector<char> buf;
-  const size_t sizes[4] = {19 * N * E, 19 * N * E, 18 * nw * E, 18 * nw * E};
+  const size_t sizes[4] = {h_slots_of(L->p.storage) * N * E, 19 * N * E, 18 * nw * E,
+                           18 * nw * Rb};
   const void *src[4] = {L->h[rd], L->g, L->wp[rd], L->ghost};
   FILE *f = std::fopen(path, "wb");
   if (!f) return fail(PFLB_ERR_ARG, std::string("cannot open ") + path);
@@ -613,7 +644,9 @@ pflb_status pflb_load(pflb_lattice *L, const char *path) {
   L->step = hdr[5];
   const int rd = (int)(L->step & 1);
   const size_t N = (size_t)L->N, nw = (size_t)L->nw, E = L->elem;
-  const size_t sizes[4] = {19 * N * E, 19 * N * E, 18 * nw * E, 18 * nw * E};
+  const size_t Rb = compute_bytes(L->p.storage);
+  const size_t sizes[4] = {h_slots_of(L->p.storage) * N * E, 19 * N * E, 18 * nw * E,
+                           18 * nw * Rb};
   void *dst[4] = {L->h[rd], L->g, L->wp[rd], L->ghost};
   std::vector<char> buf;
   for (int k = 0; k < 4; ++k) {

@@ -35,8 +35,8 @@ struct Args {
   int nx, ny, nz, lz;
   int N;
   int nw;
-  const S *hin[Q];   // direction bases of the h buffer being read
-  S *hout[Q];        // direction bases of the h buffer being written
+  const S *hin[Q + 1];   // direction bases of the h buffer being read (+ rest remainder)
+  S *hout[Q + 1];        // direction bases of the h buffer being written
   S *g[Q];           // direction bases of the g buffer (in place)
   const uint8_t *flags;
   const int *widx;
@@ -100,18 +100,18 @@ __device__ __forceinline__ void gather_g(const Args<S, R> &a, int c, uint32_t lm
   if (lm == 0) {  // bulk cell: no solid link
 #pragma unroll
     for (int k = 0; k < Q; ++k)
-      g[k] = ODD ? (R)Store<S>::ld(a.g[opp_of(k)] + (c + nb.off(opp_of(k))))
-                 : (R)Store<S>::ld(a.g[k] + c);
+      g[k] = ODD ? ld_g<S, R>(a.g[opp_of(k)] + (c + nb.off(opp_of(k))), k)
+                 : ld_g<S, R>(a.g[k] + c, k);
     return;
   }
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
     if (k != 0 && ((lm >> opp_of(k)) & 1u)) {
-      g[k] = (R)a.wp_rd[(k - 1) * a.nw + rec];
+      g[k] = ld_g<S, R>(a.wp_rd + ((k - 1) * a.nw + rec), k);
     } else if (!ODD) {
-      g[k] = (R)Store<S>::ld(a.g[k] + c);
+      g[k] = ld_g<S, R>(a.g[k] + c, k);
     } else {
-      g[k] = (R)Store<S>::ld(a.g[opp_of(k)] + (c + nb.off(opp_of(k))));
+      g[k] = ld_g<S, R>(a.g[opp_of(k)] + (c + nb.off(opp_of(k))), k);
     }
   }
 }
@@ -177,16 +177,19 @@ __device__ __forceinline__ void finish_cell(const Args<S, R> &a, int x, int y, i
   }
 
   collide(m, h, g, mc, phi, gx, gy, gz, lap);
+  S he[Q], h_lo;
+  enc_h_cell<S, R>(h, he, &h_lo);
+  if constexpr (Codec<S>::scaled) a.hout[Q][c] = h_lo;  // rest population stays
 
   if (lm == 0) {  // bulk cell: plain streaming of both sets
 #pragma unroll
-    for (int i = 0; i < Q; ++i) Store<S>::st(a.hout[i] + (c + nb.off(i)), (S)h[i]);
+    for (int i = 0; i < Q; ++i) a.hout[i][c + nb.off(i)] = he[i];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       if (!ODD)
-        Store<S>::st(a.g[opp_of(i)] + c, (S)g[i]);
+        st_g<S, R>(a.g[opp_of(i)] + c, i, g[i]);
       else
-        Store<S>::st(a.g[i] + (c + nb.off(i)), (S)g[i]);
+        st_g<S, R>(a.g[i] + (c + nb.off(i)), i, g[i]);
     }
     return;
   }
@@ -194,9 +197,9 @@ __device__ __forceinline__ void finish_cell(const Args<S, R> &a, int x, int y, i
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     if (i != 0 && ((lm >> i) & 1u))
-      Store<S>::st(a.hout[opp_of(i)] + c, (S)h[i]);
+      a.hout[opp_of(i)][c] = he[i];  // same weight class as i
     else
-      Store<S>::st(a.hout[i] + (c + nb.off(i)), (S)h[i]);
+      a.hout[i][c + nb.off(i)] = he[i];
   }
   // g: A-A write; solid links go to the wall population buffer, either to
   // this node (bounce-back) or to the tangential neighbour (specular
@@ -221,11 +224,11 @@ __device__ __forceinline__ void finish_cell(const Args<S, R> &a, int x, int y, i
           }
         }
       }
-      a.wp_wr[(ddir - 1) * a.nw + drec] = (S)g[i];
+      st_g<S, R>(a.wp_wr + ((ddir - 1) * a.nw + drec), i, g[i]);
     } else if (!ODD) {
-      Store<S>::st(a.g[opp_of(i)] + c, (S)g[i]);
+      st_g<S, R>(a.g[opp_of(i)] + c, i, g[i]);
     } else {
-      Store<S>::st(a.g[i] + (c + nb.off(i)), (S)g[i]);
+      st_g<S, R>(a.g[i] + (c + nb.off(i)), i, g[i]);
     }
   }
 }
@@ -318,9 +321,11 @@ __device__ __forceinline__ void diag_block_flush(double *diag, R (*wacc)[32]) {
 template <class S, class R>
 __device__ __forceinline__ R cell_phi(const Args<S, R> &a, int c) {
   if (a.flags[c] & F_SOLID) return R(0);
+  R h[Q];
+  ld_h_cell<S, R>(a.hin, c, h);
   R s = R(0);
 #pragma unroll
-  for (int i = 0; i < Q; ++i) s += (R)ld_ro<S>(a.hin[i] + c);
+  for (int i = 0; i < Q; ++i) s += h[i];
   return s;
 }
 
@@ -366,11 +371,9 @@ __global__ void __launch_bounds__(256) k_cell(const __grid_constant__ Args<S, R>
       nb.init(x, y, z, a.nx, a.ny, a.nz);
       R h[Q], val[Q];
       R phi = R(0);
+      ld_h_cell<S, R>(a.hin, c, h);
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        h[i] = (R)ld_ro<S>(a.hin[i] + c);
-        phi += h[i];
-      }
+      for (int i = 0; i < Q; ++i) phi += h[i];
 #pragma unroll
       for (int i = 1; i < Q; ++i) val[i] = a.phi[c + nb.off(i)];
       update_cell<S, R, ODD, MODE, DIAG>(a, x, y, z, c, f, h, phi, val, acc);
@@ -438,7 +441,7 @@ __global__ void __launch_bounds__(256, PFLB_MIN_BLOCKS)
       if (!(f & F_SOLID)) {
         R h[Q], val[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) h[i] = (R)ld_ro<S>(a.hin[i] + c);
+        ld_h_cell<S, R>(a.hin, c, h);
         const R *p0 = sphi + (((z % 3) + 3) % 3) * PS;
         const R *pm = sphi + ((((z - 1) % 3) + 3) % 3) * PS;
         const R *pp = sphi + ((((z + 1) % 3) + 3) % 3) * PS;
@@ -471,7 +474,9 @@ __global__ void k_init(const __grid_constant__ Args<S, R> a, const double *phi0,
   const uint8_t f = a.flags[c];
   if (f & F_SOLID) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) { h0base[i * N + c] = (S)0; a.g[i][c] = (S)0; }
+    for (int i = 0; i < h_slots<S>(); ++i) h0base[i * N + c] = enc_pop<S, R>(R(0), 0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) st_g<S, R>(a.g[i] + c, i, R(0));
     return;
   }
   const int x = c % a.nx, y = (c / a.nx) % a.ny, z = c / (a.nx * a.ny);
@@ -496,6 +501,9 @@ __global__ void k_init(const __grid_constant__ Args<S, R> a, const double *phi0,
   R h[Q];
   h_equilibrium(m, h, phi, gx, gy, gz, lap);
   // g = g_eq(P0, u = 0) = w_i P0/T - K_i/2 with K_i = w_i (mu c_i.grad + c_i.F)/T.
+  S he[Q], h_lo;
+  enc_h_cell<S, R>(h, he, &h_lo);
+  if constexpr (Codec<S>::scaled) h0base[Q * N + c] = h_lo;
   const R mu = m.mu_a * phi * (phi - R(1)) * (phi - R(0.5)) - m.mu_b * lap;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
@@ -504,9 +512,9 @@ __global__ void k_init(const __grid_constant__ Args<S, R> a, const double *phi0,
     const R cF = R(cx_of(i)) * m.Fx + R(cy_of(i)) * m.Fy + R(cz_of(i)) * m.Fz;
     const R K = wi * R(3) * (mu * cg + cF);
     const R gi = wi * R(3) * (R)P0 - R(0.5) * K;
-    h0base[i * N + c] = (S)h[i];
-    a.g[i][c] = (S)gi;
-    if (i != 0 && ((lm >> opp_of(i)) & 1u)) wp0[(i - 1) * a.nw + rec] = (S)gi;
+    h0base[i * N + c] = he[i];
+    st_g<S, R>(a.g[i] + c, i, gi);
+    if (i != 0 && ((lm >> opp_of(i)) & 1u)) st_g<S, R>(wp0 + ((i - 1) * a.nw + rec), i, gi);
   }
 }
 

@@ -51,11 +51,12 @@ static Args<S, R> make_args(Lattice &L) {
   a.N = (int)L.N;
   a.nw = L.nw;
   const int rd = (int)(L.step & 1);
-  for (int i = 0; i < Q; ++i) {
-    a.hin[i] = (const S *)L.h[rd] + (size_t)i * L.N;
-    a.hout[i] = (S *)L.h[rd ^ 1] + (size_t)i * L.N;
-    a.g[i] = (S *)L.g + (size_t)i * L.N;
+  for (int i = 0; i < Q + 1; ++i) {
+    const bool have = i < h_slots<S>();
+    a.hin[i] = have ? (const S *)L.h[rd] + (size_t)i * L.N : nullptr;
+    a.hout[i] = have ? (S *)L.h[rd ^ 1] + (size_t)i * L.N : nullptr;
   }
+  for (int i = 0; i < Q; ++i) a.g[i] = (S *)L.g + (size_t)i * L.N;
   a.flags = L.flags;
   a.widx = L.widx;
   a.wmask = L.wmask;

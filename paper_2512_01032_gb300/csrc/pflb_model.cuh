@@ -16,6 +16,8 @@
 // Populations: h = phase field, g = hydrodynamic (the paper's g-bar).
 #pragma once
 #include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace pflb {
@@ -110,9 +112,96 @@ template <> struct Store<float> {
 // not, since the compiler may then move such loads past aliasing stores.
 template <class S> __device__ __forceinline__ S ld_ro(const S *p) { return __ldg(p); }
 
-template <class R> __device__ __forceinline__ R rsqrt_(R x);
-template <> __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
-template <> __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+// ------------------------------------------------------------ codecs
+// Populations are stored in S and computed in R.  FP64 and FP32 store the
+// value itself.  The 16-bit formats store each population divided by the
+// lattice weight of its direction (values of order phi in [0, 1] for h and
+// of order P/T for g, the rest value of g being w_i P / T), and the h set is
+// made mass-conserving: the rest population never moves, so each cell adds
+// the rounding error of the 18 moving h populations it writes to its own
+// rest population, which is kept as a pair of 16-bit values (a high part and
+// the remainder, about 22 significant bits).  The sum of all stored h then
+// equals the sum of the computed ones up to FP32 rounding, so total phi does
+// not drift.  i is a compile-time constant at every call, so the scale
+// folds into one multiply.
+template <class S> struct Codec {
+  template <class R> static __device__ __forceinline__ R to(S v) { return (R)v; }
+  template <class R> static __device__ __forceinline__ S from(R v) { return (S)v; }
+  static constexpr bool scaled = false;
+};
+template <> struct Codec<__half> {
+  template <class R> static __device__ __forceinline__ R to(__half v) { return (R)__half2float(v); }
+  template <class R> static __device__ __forceinline__ __half from(R v) {
+    return __float2half_rn((float)v);
+  }
+  static constexpr bool scaled = true;
+};
+template <> struct Codec<__nv_bfloat16> {
+  template <class R> static __device__ __forceinline__ R to(__nv_bfloat16 v) {
+    return (R)__bfloat162float(v);
+  }
+  template <class R> static __device__ __forceinline__ __nv_bfloat16 from(R v) {
+    return __float2bfloat16_rn((float)v);
+  }
+  static constexpr bool scaled = true;
+};
+
+// Number of h slots per cell: 19, plus the remainder of the rest population
+// for the 16-bit formats (slot 19).
+template <class S> __host__ __device__ constexpr int h_slots() { return Codec<S>::scaled ? Q + 1 : Q; }
+
+__host__ __device__ constexpr double inv_w_of(int i) { return i == 0 ? 3.0 : (i <= 6 ? 18.0 : 36.0); }
+
+template <class S, class R>
+__device__ __forceinline__ R dec_pop(S v, int i) {
+  if constexpr (Codec<S>::scaled)
+    return Codec<S>::template to<R>(v) * R(w_of(i));
+  else
+    return (R)v;
+}
+template <class S, class R>
+__device__ __forceinline__ S enc_pop(R v, int i) {
+  if constexpr (Codec<S>::scaled)
+    return Codec<S>::template from<R>(v * R(inv_w_of(i)));
+  else
+    return (S)v;
+}
+template <class S, class R> __device__ __forceinline__ R ld_g(const S *p, int i) {
+  return dec_pop<S, R>(*p, i);
+}
+template <class S, class R> __device__ __forceinline__ void st_g(S *p, int i, R v) {
+  *p = enc_pop<S, R>(v, i);
+}
+// Loads all 19 h of cell c from direction bases hb (read-only path); the
+// rest population of the 16-bit formats is high part + remainder.
+template <class S, class R>
+__device__ __forceinline__ void ld_h_cell(const S *const *hb, int c, R h[Q]) {
+#pragma unroll
+  for (int i = 0; i < Q; ++i) h[i] = dec_pop<S, R>(ld_ro<S>(hb[i] + c), i);
+  if constexpr (Codec<S>::scaled) h[0] += dec_pop<S, R>(ld_ro<S>(hb[Q] + c), 0);
+}
+// Encodes the 19 post-collision h of a cell; for the 16-bit formats the
+// rounding error of directions 1..18 is moved into the rest population,
+// whose high part goes to enc[0] and remainder to *rest_lo.
+template <class S, class R>
+__device__ __forceinline__ void enc_h_cell(const R h[Q], S enc[Q], S *rest_lo) {
+  if constexpr (Codec<S>::scaled) {
+    R err = R(0);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      enc[i] = enc_pop<S, R>(h[i], i);
+      err += dec_pop<S, R>(enc[i], i) - h[i];
+    }
+    const R h0 = h[0] - err;
+    enc[0] = enc_pop<S, R>(h0, 0);
+    *rest_lo = enc_pop<S, R>(h0 - dec_pop<S, R>(enc[0], 0), 0);
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) enc[i] = (S)h[i];
+    (void)rest_lo;
+  }
+}
+
 // Square root, reciprocal, quotient and tanh: IEEE versions in FP64 (the
 // parity path); in FP32, short hardware-approximation forms (a few ulp,
 // well inside the FP32 tolerance of the step) that cost a handful of

@@ -18,7 +18,7 @@ _P = C.POINTER
 _d = _P(C.c_double)
 
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NAN, ERR_TIMEOUT, ERR_BUDGET, ERR_STATE = range(8)
-STORAGE_FP64, STORAGE_FP32 = 0, 1
+STORAGE_FP64, STORAGE_FP32, STORAGE_FP16, STORAGE_BF16 = 0, 1, 2, 3
 FIELD_PHI, FIELD_RHO, FIELD_P, FIELD_UX, FIELD_UY, FIELD_UZ = range(6)
 FIELDS = {"phi": 0, "rho": 1, "P": 2, "ux": 3, "uy": 4, "uz": 5}
 KERNEL_FUSED, KERNEL_TWOPASS, KERNEL_FUSED_TMA = 0, 1, 2
@@ -146,7 +146,8 @@ def default_params(**kw) -> Params:
             for a in range(3):
                 p.Fex[a] = float(v[a])
         elif k == "storage" and isinstance(v, str):
-            p.storage = {"fp64": STORAGE_FP64, "fp32": STORAGE_FP32}[v]
+            p.storage = {"fp64": STORAGE_FP64, "fp32": STORAGE_FP32, "fp16": STORAGE_FP16,
+                         "bf16": STORAGE_BF16}[v]
         elif hasattr(p, k):
             setattr(p, k, v)
         else:

@@ -110,6 +110,6 @@ def test_estimate_bytes_counts_wall_nodes():
     solid[0] = 1
     walled = pflb.estimate_bytes(n, n, n, solid)
     N = n ** 3
-    assert empty == 3 * 19 * N * 4 + N * 5 + N * 4 + 96 * 8
+    assert empty == 3 * 19 * N * 4 + N * 5 + N * 4 + 96 * 8 + 4
     nw = 2 * n * n  # planes z = 1 and z = n-1 (periodic) touch the solid layer
     assert walled - empty == nw * (2 * 18 * 4 + 4 + 5 * 4 + 18 * 4)
