@@ -247,6 +247,40 @@ pflb_status pflb_fields_noalloc(int nx, int ny, int nz, const float *h_dev, cons
                                 const pflb_params *params, double *fields_dev,
                                 pflb_diag_t *diag_out, void *cuda_stream);
 
+/* ------------------------------------------------------------- batches
+ * Many independent lattices (of any sizes) advanced together by one
+ * persistent kernel: a grid of (SMs x blocks per SM) blocks pulls work
+ * items -- one per (lattice, tile column, chunk of z planes) -- from a device
+ * work list, so small lattices that could not fill the GPU on their own
+ * share it.  Every cell gets exactly the arithmetic of its lattice stepped
+ * alone (results are bit-identical).  Plain steps are replayed from a
+ * captured CUDA graph of 16 steps.  The batch does not own the lattices;
+ * they must outlive it, share one storage type, and appear once.  Work is
+ * ordered on the batch stream (cuda_stream, or a stream the batch creates
+ * when NULL), after and before the lattices' own streams. */
+typedef struct pflb_batch pflb_batch;
+
+pflb_status pflb_batch_create(pflb_lattice *const *lattices, int count, void *cuda_stream,
+                              pflb_batch **out);
+
+/* Launch shape: bx * by threads per block (same rules as pflb_set_kernel),
+ * lz planes per work item, blocks per SM (0 = as many as fit, at most 4);
+ * zeros keep the current values (default 32 x 4 x 16, 0). */
+pflb_status pflb_batch_set_launch(pflb_batch *b, int bx, int by, int lz, int blocks_per_sm);
+
+/* Autotuner: times trial_steps steps of each of a fixed set of launch shapes
+ * on the batch itself (the steps are real steps of every lattice), keeps the
+ * fastest and returns it in best (bx, by, lz, blocks per SM) if not NULL. */
+pflb_status pflb_batch_tune(pflb_batch *b, int trial_steps, int best[4]);
+
+/* Advance every lattice of the batch by nsteps (asynchronous).  With
+ * diag_last != 0 the last step accumulates each lattice's diagnostics,
+ * read afterwards with pflb_last_diag on that lattice. */
+pflb_status pflb_batch_step(pflb_batch *b, int64_t nsteps, int diag_last);
+
+/* Free the batch (not its lattices); NULL is ignored. */
+void pflb_batch_destroy(pflb_batch *b);
+
 /* Free the lattice (synchronises its stream first).  NULL is ignored. */
 void pflb_destroy(pflb_lattice *L);
 

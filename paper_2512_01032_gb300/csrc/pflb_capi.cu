@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -24,6 +25,22 @@
 using pflb::Lattice;
 
 struct pflb_lattice : public Lattice {};
+
+struct pflb_batch {
+  std::vector<Lattice *> lats;
+  int storage = PFLB_STORAGE_FP32;
+  pflb::BatchDev dev;
+  size_t desc_bytes = 0;
+  size_t items_cap = 0;
+  int blocks_per_sm = 0;  // requested; 0 = as many as fit, at most 4
+  int per_sm = 0;         // in use (the grid may be smaller when items are few)
+  int nsm = 0;
+  bool own_stream = false;
+  cudaEvent_t ev = nullptr;
+  cudaGraphExec_t graph = nullptr;  // kGraphSteps plain steps
+  bool poisoned = false;
+};
+static constexpr int kGraphSteps = 16;
 
 namespace {
 
@@ -78,6 +95,19 @@ cudaError_t do_macro(Lattice *L, bool fields) {
     return pflb::launch_macro<S, R>(*L, fields);
   });
 }
+template <class F>
+auto dispatch_storage(int storage, F &&f) {
+  switch (storage) {
+    case PFLB_STORAGE_FP64: return f((double *)nullptr, (double *)nullptr);
+    case PFLB_STORAGE_FP32: return f((float *)nullptr, (float *)nullptr);
+    case PFLB_STORAGE_FP16: return f((__half *)nullptr, (float *)nullptr);
+    default: return f((__nv_bfloat16 *)nullptr, (float *)nullptr);
+  }
+}
+#define PFLB_SR_TYPES                                   \
+  using S = std::remove_pointer_t<decltype(s_)>;       \
+  using R = std::remove_pointer_t<decltype(r_)>;
+
 size_t storage_bytes(int storage) {
   return storage == PFLB_STORAGE_FP64 ? 8 : (storage == PFLB_STORAGE_FP32 ? 4 : 2);
 }
@@ -669,6 +699,235 @@ pflb_status pflb_load(pflb_lattice *L, const char *path) {
   }
   std::fclose(f);
   return PFLB_OK;
+}
+
+// ------------------------------------------------------------- batches
+
+static pflb_status batch_fail(pflb_batch *b, cudaError_t e, const char *what) {
+  if (b) b->poisoned = true;
+  return fail(PFLB_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+#define BCK(b, call)                                         \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return batch_fail(b, e_, #call);  \
+  } while (0)
+
+static void batch_drop_graph(pflb_batch *b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+}
+
+// Work list for the current launch shape, and the persistent grid size.
+static pflb_status batch_build_items(pflb_batch *b) {
+  std::vector<int4> items;
+  const int bx = b->dev.bx, by = b->dev.by, lz = b->dev.lz;
+  for (int l = 0; l < (int)b->lats.size(); ++l) {
+    const Lattice *L = b->lats[l];
+    for (int z0 = 0; z0 < L->nz; z0 += lz)
+      for (int y0 = 0; y0 < L->ny; y0 += by)
+        for (int x0 = 0; x0 < L->nx; x0 += bx) items.push_back(make_int4(l, x0, y0, z0));
+  }
+  if (items.size() > b->items_cap) {
+    if (b->dev.items) cudaFree(b->dev.items);
+    b->dev.items = nullptr;
+    BCK(b, cudaMalloc(&b->dev.items, items.size() * sizeof(int4)));
+    b->items_cap = items.size();
+  }
+  b->dev.nitems = (int)items.size();
+  BCK(b, cudaMemcpyAsync(b->dev.items, items.data(), items.size() * sizeof(int4),
+                         cudaMemcpyHostToDevice, b->dev.stream));
+  const int fit = dispatch_storage(b->storage, [&](auto *s_, auto *r_) {
+    PFLB_SR_TYPES
+    return pflb::batch_max_blocks_per_sm<S, R>(bx, by);
+  });
+  b->per_sm = b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, fit) : std::min(fit, 4);
+  b->dev.grid = std::max(1, std::min(b->dev.nitems, b->per_sm * b->nsm));
+  batch_drop_graph(b);
+  BCK(b, cudaStreamSynchronize(b->dev.stream));
+  return PFLB_OK;
+}
+
+extern "C" pflb_status pflb_batch_create(pflb_lattice *const *lattices, int count, void *cuda_stream,
+                                         pflb_batch **out) {
+  if (!out) return fail(PFLB_ERR_ARG, "null out");
+  *out = nullptr;
+  if (!lattices || count < 1) return fail(PFLB_ERR_ARG, "need at least one lattice");
+  for (int l = 0; l < count; ++l) {
+    pflb_status st = check_lattice(lattices[l]);
+    if (st != PFLB_OK) return st;
+    if (lattices[l]->p.storage != lattices[0]->p.storage)
+      return fail(PFLB_ERR_ARG, "all lattices of a batch need the same storage");
+    for (int k = 0; k < l; ++k)
+      if (lattices[k] == lattices[l]) return fail(PFLB_ERR_ARG, "a lattice appears twice");
+  }
+  pflb_batch *b = new (std::nothrow) pflb_batch();
+  if (!b) return fail(PFLB_ERR_OOM, "host allocation failed");
+  for (int l = 0; l < count; ++l) b->lats.push_back(lattices[l]);
+  b->storage = lattices[0]->p.storage;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (b->nsm < 1) b->nsm = 1;
+  cudaError_t e = cudaSuccess;
+  if (cuda_stream) {
+    b->dev.stream = (cudaStream_t)cuda_stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&b->dev.stream, cudaStreamNonBlocking);
+    b->own_stream = true;
+  }
+  b->desc_bytes = dispatch_storage(b->storage, [&](auto *s_, auto *r_) {
+    PFLB_SR_TYPES
+    return pflb::batch_desc_bytes<S, R>();
+  });
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMalloc(&b->dev.descs, 2 * (size_t)count * b->desc_bytes);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&b->dev.par0, count * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&b->dev.counter, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&b->dev.bstep, sizeof(int));
+  if (e != cudaSuccess) {
+    pflb_batch_destroy(b);
+    cudaGetLastError();
+    return fail(PFLB_ERR_OOM, std::string("batch allocation failed: ") + cudaGetErrorString(e));
+  }
+  pflb_status st = batch_build_items(b);
+  if (st != PFLB_OK) {
+    pflb_batch_destroy(b);
+    return st;
+  }
+  *out = b;
+  return PFLB_OK;
+}
+
+extern "C" pflb_status pflb_batch_set_launch(pflb_batch *b, int bx, int by, int lz,
+                                             int blocks_per_sm) {
+  if (!b) return fail(PFLB_ERR_ARG, "null batch");
+  if (b->poisoned) return fail(PFLB_ERR_STATE, "batch poisoned by an earlier CUDA error");
+  const int nbx = bx > 0 ? bx : b->dev.bx, nby = by > 0 ? by : b->dev.by;
+  const int nlz = lz > 0 ? lz : b->dev.lz;
+  if (nbx * nby > 256 || 2 * (nbx + 2) + 2 * nby > nbx * nby || blocks_per_sm < 0)
+    return fail(PFLB_ERR_ARG, "bad launch shape");
+  b->dev.bx = nbx;
+  b->dev.by = nby;
+  b->dev.lz = nlz;
+  b->blocks_per_sm = blocks_per_sm;
+  return batch_build_items(b);
+}
+
+// Runs nsteps on the batch stream (graph replay for the plain steps).
+static pflb_status batch_run(pflb_batch *b, int64_t nsteps, bool diag_last) {
+  const int n = (int)b->lats.size();
+  // order after every lattice's own stream
+  for (Lattice *L : b->lats) {
+    if (L->stream == b->dev.stream) continue;
+    BCK(b, cudaEventRecord(b->ev, L->stream));
+    BCK(b, cudaStreamWaitEvent(b->dev.stream, b->ev, 0));
+  }
+  std::vector<char> host(2 * (size_t)n * b->desc_bytes);
+  std::vector<int> par(n);
+  dispatch_storage(b->storage, [&](auto *s_, auto *r_) {
+    PFLB_SR_TYPES
+    pflb::batch_build_descs<S, R>(b->lats.data(), n, host.data());
+    return 0;
+  });
+  for (int l = 0; l < n; ++l) par[l] = (int)(b->lats[l]->step & 1);
+  BCK(b, cudaMemcpyAsync(b->dev.descs, host.data(), host.size(), cudaMemcpyHostToDevice,
+                         b->dev.stream));
+  BCK(b, cudaMemcpyAsync(b->dev.par0, par.data(), n * sizeof(int), cudaMemcpyHostToDevice,
+                         b->dev.stream));
+  BCK(b, cudaMemsetAsync(b->dev.bstep, 0, sizeof(int), b->dev.stream));
+  auto launch = [&](bool diag) {
+    return dispatch_storage(b->storage, [&](auto *s_, auto *r_) {
+      PFLB_SR_TYPES
+      return pflb::batch_launch_step<S, R>(b->dev, diag);
+    });
+  };
+  int64_t plain = nsteps - (diag_last ? 1 : 0);
+  if (plain >= kGraphSteps && !b->graph) {
+    cudaGraph_t g = nullptr;
+    BCK(b, cudaStreamBeginCapture(b->dev.stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) e = launch(false);
+    cudaError_t e2 = cudaStreamEndCapture(b->dev.stream, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return batch_fail(b, e, "graph capture");
+  }
+  while (plain >= kGraphSteps) {
+    BCK(b, cudaGraphLaunch(b->graph, b->dev.stream));
+    plain -= kGraphSteps;
+  }
+  for (; plain > 0; --plain) BCK(b, launch(false));
+  if (diag_last) BCK(b, launch(true));
+  for (Lattice *L : b->lats) {
+    L->step += nsteps;
+    if (diag_last) {
+      L->last_diag_step = L->step - 1;
+      L->ndiag++;
+    }
+  }
+  // later work on each lattice's own stream comes after the batch
+  BCK(b, cudaEventRecord(b->ev, b->dev.stream));
+  for (Lattice *L : b->lats)
+    if (L->stream != b->dev.stream) BCK(b, cudaStreamWaitEvent(L->stream, b->ev, 0));
+  return PFLB_OK;
+}
+
+extern "C" pflb_status pflb_batch_step(pflb_batch *b, int64_t nsteps, int diag_last) {
+  if (!b) return fail(PFLB_ERR_ARG, "null batch");
+  if (b->poisoned) return fail(PFLB_ERR_STATE, "batch poisoned by an earlier CUDA error");
+  if (nsteps < 0 || (diag_last && nsteps < 1)) return fail(PFLB_ERR_ARG, "bad step count");
+  for (Lattice *L : b->lats)
+    if (L->poisoned) return fail(PFLB_ERR_STATE, "a lattice of the batch is poisoned");
+  if (nsteps == 0) return PFLB_OK;
+  return batch_run(b, nsteps, diag_last != 0);
+}
+
+extern "C" pflb_status pflb_batch_tune(pflb_batch *b, int trial_steps, int best[4]) {
+  if (!b) return fail(PFLB_ERR_ARG, "null batch");
+  if (b->poisoned) return fail(PFLB_ERR_STATE, "batch poisoned by an earlier CUDA error");
+  if (trial_steps < 1) return fail(PFLB_ERR_ARG, "trial_steps must be >= 1");
+  static const int cand[][4] = {{32, 4, 16, 0}, {32, 4, 8, 0}, {32, 8, 16, 2}, {32, 8, 8, 2},
+                                {16, 8, 16, 0}, {64, 4, 16, 2}, {32, 4, 32, 0}, {16, 16, 8, 2}};
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  BCK(b, cudaEventCreate(&t0));
+  BCK(b, cudaEventCreate(&t1));
+  float best_ms = 1e30f;
+  int bi = 0;
+  for (int k = 0; k < (int)(sizeof cand / sizeof cand[0]); ++k) {
+    pflb_status st = pflb_batch_set_launch(b, cand[k][0], cand[k][1], cand[k][2], cand[k][3]);
+    if (st != PFLB_OK) continue;
+    st = batch_run(b, 1, false);  // warm the new shape
+    if (st != PFLB_OK) return st;
+    BCK(b, cudaEventRecord(t0, b->dev.stream));
+    st = batch_run(b, trial_steps, false);
+    if (st != PFLB_OK) return st;
+    BCK(b, cudaEventRecord(t1, b->dev.stream));
+    BCK(b, cudaEventSynchronize(t1));
+    float ms = 0;
+    BCK(b, cudaEventElapsedTime(&ms, t0, t1));
+    if (ms < best_ms) { best_ms = ms; bi = k; }
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  pflb_status st = pflb_batch_set_launch(b, cand[bi][0], cand[bi][1], cand[bi][2], cand[bi][3]);
+  if (st != PFLB_OK) return st;
+  if (best)
+    for (int k = 0; k < 4; ++k) best[k] = k < 3 ? cand[bi][k] : b->per_sm;
+  return PFLB_OK;
+}
+
+extern "C" void pflb_batch_destroy(pflb_batch *b) {
+  if (!b) return;
+  if (b->dev.stream) cudaStreamSynchronize(b->dev.stream);
+  batch_drop_graph(b);
+  void *ptrs[] = {b->dev.descs, b->dev.par0, b->dev.items, b->dev.counter, b->dev.bstep};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  if (b->ev) cudaEventDestroy(b->ev);
+  if (b->own_stream && b->dev.stream) cudaStreamDestroy(b->dev.stream);
+  delete b;
 }
 
 void pflb_destroy(pflb_lattice *L) {

@@ -44,6 +44,18 @@ struct Lattice {
   int64_t dev_bytes = 0;
 };
 
+// Device side of a batch of lattices stepped by one persistent kernel.
+struct BatchDev {
+  void *descs = nullptr;   // [nlat][2] step descriptors (Args), both parities
+  int *par0 = nullptr;     // [nlat] parity of each lattice at batch step 0
+  void *items = nullptr;   // [nitems] int4 (lattice, x0, y0, z0)
+  int nitems = 0;
+  int *counter = nullptr;  // work-list cursor, reset before each step
+  int *bstep = nullptr;    // batch steps since par0 was set
+  int bx = 32, by = 4, lz = 16, grid = 0;
+  cudaStream_t stream = nullptr;
+};
+
 // Sets the thread-local message returned by pflb_last_error().
 void set_last_error(const char *msg);
 
@@ -54,5 +66,12 @@ template <class S, class R> cudaError_t launch_step(Lattice &L, bool diag);
 template <class S, class R> cudaError_t launch_macro(Lattice &L, bool fields);
 template <class S, class R> cudaError_t set_model(Lattice &L);
 template <class S, class R> int max_block_threads();
+// Batch: size of one descriptor, host-side descriptor build (2 per lattice,
+// diagnostics pointers for the next diagnostic launch), one step launch,
+// and the occupancy-limited blocks per SM of the batch kernel.
+template <class S, class R> size_t batch_desc_bytes();
+template <class S, class R> void batch_build_descs(Lattice *const *lats, int n, char *host);
+template <class S, class R> cudaError_t batch_launch_step(const BatchDev &b, bool diag);
+template <class S, class R> int batch_max_blocks_per_sm(int bx, int by);
 
 }  // namespace pflb

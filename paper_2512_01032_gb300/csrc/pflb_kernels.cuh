@@ -387,24 +387,20 @@ __global__ void __launch_bounds__(256) k_cell(const __grid_constant__ Args<S, R>
 
 // ------------------------------------------------------------ fused path
 // One thread per (x, y) column of a BX x BY tile, marching z over a chunk
-// of lz planes.  phi of three consecutive planes over the tile plus a
+// of planes.  phi of three consecutive planes over the tile plus a
 // one-cell ring is kept in shared memory; each plane's phi is recomputed
 // from the h populations (own cells and ring cells), so no phi field is
-// stored in HBM.
+// stored in HBM.  march_tile does one tile column [zb, ze) of lattice a;
+// sphi holds 3 (BX+2)(BY+2) values, wacc the per-warp diagnostic slots
+// (zeroed by the caller; the first use follows a barrier).
 template <class S, class R, bool ODD, bool DIAG>
-__global__ void __launch_bounds__(256, PFLB_MIN_BLOCKS)
-    k_fused(const __grid_constant__ Args<S, R> a, int BX, int BY) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  R *sphi = reinterpret_cast<R *>(smem_raw);
-  zero_next_diag(a);
+__device__ __forceinline__ void march_tile(const Args<S, R> &a, int x0, int y0, int zb, int ze,
+                                           int BX, int BY, R *sphi, R (*wacc)[32]) {
   const int PW = BX + 2, PS = (BX + 2) * (BY + 2);
   const int tid = threadIdx.x;
   const int tx = tid % BX, ty = tid / BX;
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const int sz = nx * ny;
-  const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
-  const int zb = blockIdx.z * a.lz;
-  const int ze = min(zb + a.lz, nz);
   const bool active = ty < BY;
   const bool valid = active && (x0 + tx) < nx && (y0 + ty) < ny;
   const int gx = (x0 + tx) % nx, gy = (y0 + ty) % ny;
@@ -426,8 +422,6 @@ __global__ void __launch_bounds__(256, PFLB_MIN_BLOCKS)
     if (rx >= 0) dst[ry * PW + rx] = cell_phi(a, rcol + sz * zw);
   };
 
-  __shared__ R wacc[DIAG_MAX_WARPS][32];
-  if (DIAG) diag_block_zero(wacc);  // first use follows a barrier below
   plane(zb - 1);
   plane(zb);
   for (int z = zb; z < ze; ++z) {
@@ -440,7 +434,6 @@ __global__ void __launch_bounds__(256, PFLB_MIN_BLOCKS)
       const uint8_t f = a.flags[c];
       if (!(f & F_SOLID)) {
         R h[Q], val[Q];
-#pragma unroll
         ld_h_cell<S, R>(a.hin, c, h);
         const R *p0 = sphi + (((z % 3) + 3) % 3) * PS;
         const R *pm = sphi + ((((z - 1) % 3) + 3) % 3) * PS;
@@ -458,6 +451,19 @@ __global__ void __launch_bounds__(256, PFLB_MIN_BLOCKS)
     if (DIAG && active) diag_warp_add(wacc[tid >> 5], acc);
     __syncthreads();
   }
+}
+
+template <class S, class R, bool ODD, bool DIAG>
+__global__ void __launch_bounds__(256, PFLB_MIN_BLOCKS)
+    k_fused(const __grid_constant__ Args<S, R> a, int BX, int BY) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R *sphi = reinterpret_cast<R *>(smem_raw);
+  zero_next_diag(a);
+  __shared__ R wacc[DIAG_MAX_WARPS][32];
+  if (DIAG) diag_block_zero(wacc);
+  const int zb = blockIdx.z * a.lz;
+  march_tile<S, R, ODD, DIAG>(a, blockIdx.x * BX, blockIdx.y * BY, zb, min(zb + a.lz, a.nz), BX,
+                              BY, sphi, wacc);
   if (DIAG) diag_block_flush(a.diag, wacc);
 }
 

@@ -1,9 +1,11 @@
 // pflb_launch.cuh -- per-precision kernel launchers (included by one
 // translation unit per storage type).
 #pragma once
+#include <cstring>
 #include <type_traits>
 
 #include "pflb_async.cuh"
+#include "pflb_batch.cuh"
 #include "pflb_internal.h"
 #include "pflb_kernels.cuh"
 
@@ -179,7 +181,60 @@ cudaError_t launch_macro(Lattice &L, bool fields) {
   return launch_cell_t<S, R, false, MODE_MACRO, true>(L, a);
 }
 
+template <class S, class R>
+size_t batch_desc_bytes() { return sizeof(Args<S, R>); }
+
+template <class S, class R>
+void batch_build_descs(Lattice *const *lats, int n, char *host) {
+  for (int l = 0; l < n; ++l) {
+    for (int p = 0; p < 2; ++p) {
+      Lattice tmp = *lats[l];
+      tmp.step = p;  // selects buffers and A-A parity
+      Args<S, R> a = make_args<S, R>(tmp);
+      a.diag = lats[l]->diag + 32 * (lats[l]->ndiag & 1);
+      a.diag_zero = lats[l]->diag + 32 * ((lats[l]->ndiag + 1) & 1);
+      std::memcpy(host + (2 * (size_t)l + p) * sizeof(Args<S, R>), &a, sizeof a);
+    }
+  }
+}
+
+template <class S, class R>
+cudaError_t batch_launch_step(const BatchDev &b, bool diag) {
+  cudaError_t e = cudaMemsetAsync(b.counter, 0, sizeof(int), b.stream);
+  if (e != cudaSuccess) return e;
+  const size_t smem = batch_smem<S, R>(b.bx, b.by);
+  const Args<S, R> *d = (const Args<S, R> *)b.descs;
+  const int4 *it = (const int4 *)b.items;
+  if (diag)
+    k_batch<S, R, true><<<b.grid, b.bx * b.by, smem, b.stream>>>(d, b.par0, it, b.nitems,
+                                                                 b.counter, b.bstep, b.bx, b.by,
+                                                                 b.lz);
+  else
+    k_batch<S, R, false><<<b.grid, b.bx * b.by, smem, b.stream>>>(d, b.par0, it, b.nitems,
+                                                                  b.counter, b.bstep, b.bx,
+                                                                  b.by, b.lz);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_batch_tick<<<1, 1, 0, b.stream>>>(b.bstep);
+  return cudaGetLastError();
+}
+
+template <class S, class R>
+int batch_max_blocks_per_sm(int bx, int by) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<S, R, true>, bx * by,
+                                                    batch_smem<S, R>(bx, by)) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return nb > 0 ? nb : 1;
+}
+
 #define PFLB_INSTANTIATE(S, R)                                                   \
+  template size_t batch_desc_bytes<S, R>();                                      \
+  template void batch_build_descs<S, R>(Lattice *const *, int, char *);         \
+  template cudaError_t batch_launch_step<S, R>(const BatchDev &, bool);          \
+  template int batch_max_blocks_per_sm<S, R>(int, int);                          \
   template cudaError_t launch_init<S, R>(Lattice &, const double *, double);     \
   template cudaError_t launch_step<S, R>(Lattice &, bool);                       \
   template cudaError_t launch_macro<S, R>(Lattice &, bool);                      \

@@ -126,6 +126,16 @@ def load(build_if_missing: bool = True):
     lib.pflb_fields_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                         _P(Params), C.c_void_p, _P(Diag), C.c_void_p]
     lib.pflb_fields_noalloc.restype = st
+    lib.pflb_batch_create.argtypes = [_P(C.c_void_p), C.c_int, C.c_void_p, _P(C.c_void_p)]
+    lib.pflb_batch_create.restype = st
+    lib.pflb_batch_set_launch.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]
+    lib.pflb_batch_set_launch.restype = st
+    lib.pflb_batch_tune.argtypes = [C.c_void_p, C.c_int, _P(C.c_int)]
+    lib.pflb_batch_tune.restype = st
+    lib.pflb_batch_step.argtypes = [C.c_void_p, C.c_int64, C.c_int]
+    lib.pflb_batch_step.restype = st
+    lib.pflb_batch_destroy.argtypes = [C.c_void_p]
+    lib.pflb_batch_destroy.restype = None
     lib.pflb_last_error.argtypes = []
     lib.pflb_last_error.restype = C.c_char_p
     _lib = lib
@@ -309,3 +319,40 @@ class Lattice:
 
     def load(self, path):
         _check(self._lib.pflb_load(self._h, os.fsencode(path)))
+
+
+class Batch:
+    """Many lattices advanced together by one persistent kernel (the lattices
+    stay owned by the caller and must outlive the batch)."""
+
+    def __init__(self, lattices, stream=None):
+        self._lib = load()
+        self.lattices = list(lattices)
+        arr = (C.c_void_p * len(self.lattices))(*[L.handle.value for L in self.lattices])
+        h = C.c_void_p()
+        _check(self._lib.pflb_batch_create(arr, len(self.lattices),
+                                           C.c_void_p(_stream_handle(stream)), C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.pflb_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_launch(self, bx=0, by=0, lz=0, blocks_per_sm=0):
+        _check(self._lib.pflb_batch_set_launch(self._h, int(bx), int(by), int(lz),
+                                               int(blocks_per_sm)))
+
+    def tune(self, trial_steps=4) -> tuple:
+        best = (C.c_int * 4)()
+        _check(self._lib.pflb_batch_tune(self._h, int(trial_steps), best))
+        return tuple(best)
+
+    def step(self, n=1, diag_last=False):
+        _check(self._lib.pflb_batch_step(self._h, int(n), 1 if diag_last else 0))

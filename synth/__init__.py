@@ -226,6 +226,21 @@ def channel_batch_specs(count=64, seed=2512010320):
     return out
 
 
+def channel_lattice(spec: dict):
+    """(geometry, params, init) of one channel_batch_specs entry: square duct
+    along x, droplet at x = Nx/4 on the axis, carrier driven by a uniform body
+    force giving the mean laminar speed u_in of a square duct of side a
+    (mean u = f a^2 / (28.45 rho nu) for a force density f)."""
+    nx, ny, nz = spec["nx"], spec["ny"], spec["nz"]
+    g = square_channel(nx, ny, nz, spec["theta"])
+    p = sessile_sphere_params(spec["theta"])
+    a = ny - 2.0
+    f = 28.45 * p["rho_L"] * p["nu_L"] * spec["u_in"] / (a * a)
+    p = dict(p, Fex=(f, 0.0, 0.0))
+    init = dict(shape=0, center=(nx / 4.0, (ny - 1) / 2.0, (nz - 1) / 2.0), R=spec["R"])
+    return g, p, init
+
+
 def square_channel(nx, ny, nz, theta_deg):
     """Square duct along x: walls on the four sides (y, z = 0 and n-1)."""
     shapes = [Plane((0, 0.5, 0), (0, 1, 0)), Plane((0, ny - 1.5, 0), (0, -1, 0)),

@@ -99,6 +99,15 @@ def test_create_rejects_bad_geometry():
     assert lib.pflb_step(None, 1) == pflb.ERR_ARG
     assert lib.pflb_get_step(None) == -1
     lib.pflb_destroy(None)
+    # batches: empty or null lattice lists and null batches are rejected
+    b = C.c_void_p()
+    assert lib.pflb_batch_create(None, 0, None, C.byref(b)) == pflb.ERR_ARG
+    arr = (C.c_void_p * 2)(None, None)
+    assert lib.pflb_batch_create(arr, 2, None, C.byref(b)) == pflb.ERR_ARG
+    assert lib.pflb_batch_step(None, 1, 0) == pflb.ERR_ARG
+    assert lib.pflb_batch_set_launch(None, 32, 4, 16, 0) == pflb.ERR_ARG
+    assert lib.pflb_batch_tune(None, 1, None) == pflb.ERR_ARG
+    lib.pflb_batch_destroy(None)
 
 
 def test_estimate_bytes_counts_wall_nodes():

@@ -1,0 +1,193 @@
+"""Batched stepping: many uneven lattices advanced by one persistent kernel.
+
+A lattice advanced inside a mix of other lattices gets exactly (bitwise)
+the result it gets in a batch of its own, whatever the launch shape, the
+A-A parity each lattice starts from, and the split of the step count into
+captured-graph replays and single launches: the per-cell code is the same
+compiled function and no cell reads another lattice's data.
+
+Against the single-lattice fused kernel the agreement is to rounding: the
+two kernels are compiled separately, so the compiler may contract a
+multiply and an add into one FMA in one and not in the other (a difference
+of one rounding, 1e-16 relative in FP64, that the step map then carries)."""
+import numpy as np
+import pytest
+
+from tests import _cases as CS
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("phi", "rho", "P", "ux", "uy", "uz")
+
+
+def _cases():
+    return [CS.droplet_case(24, 6.0),
+            CS.channel_case(40, 14, 12),
+            CS.channel_case(33, 10, 7, theta=60.0),
+            CS.sessile_case(32, 120.0),
+            CS.slit_case(96, 16, 4)]
+
+
+def _lattice(case, storage):
+    from paper_2512_01032_gb300 import pflb
+    g, p, init = case
+    L = pflb.Lattice(g.nx, g.ny, g.nz, solid=g.solid, wall_normal=g.normals(),
+                     theta_cells=g.theta(), storage=storage, **p)
+    L.init_tanh(init.get("shape", 0), init["center"], init.get("R", 0.0), init.get("normal"))
+    return L
+
+
+def _pairs(storage):
+    cases = _cases()
+    alone = [_lattice(c, storage) for c in cases]
+    mixed = [_lattice(c, storage) for c in cases]
+    # start two lattices at odd A-A parity
+    for k in (1, 3):
+        alone[k].step(1)
+        mixed[k].step(1)
+    return alone, mixed
+
+
+def _assert_same(A, B):
+    assert A.t == B.t
+    for f in FIELDS:
+        a, b = A.read(f), B.read(f)
+        assert np.array_equal(a, b, equal_nan=True), (f, np.nanmax(np.abs(a - b)))
+
+
+# Batch vs single-lattice kernel after n steps, relative to the field's scale
+# (velocities to at least 1e-2, the spurious currents being far smaller than
+# the lattice speeds they are computed from): FP64 and FP32 at the parity bars
+# against the oracle; BF16 with the storage-rounding bound of the precision
+# tests (one flip of a stored population per cell per step, 2 (1 - w_0) 2^-9).
+CLOSE = {"fp64": 1e-11, "fp32": 1e-5}
+
+
+def _assert_close(A, B, storage, n):
+    assert A.t == B.t
+    for f in FIELDS:
+        a, b = A.read(f), B.read(f)
+        floor = 1e-2 if f in ("ux", "uy", "uz") else (1e-3 if f != "phi" else 1.0)
+        scale = max(np.max(np.abs(a)), floor)
+        tol = CLOSE.get(storage, n * 2 * (2.0 / 3.0) * 2.0 ** -9)
+        assert np.max(np.abs(a - b)) <= tol * scale, (f, np.max(np.abs(a - b)) / scale)
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32", "bf16"])
+def test_batch_mix_bitwise_equals_batch_of_one(storage):
+    from paper_2512_01032_gb300 import pflb
+    ones, mixed = _pairs(storage)
+    n = 37  # two graph replays of 16 steps, then single launches, the last with diagnostics
+    B = pflb.Batch(mixed)
+    B.set_launch(16, 8, 8, 1)  # another launch shape than the batches of one
+    B.step(n, diag_last=True)
+    for L in ones:
+        b1 = pflb.Batch([L])
+        b1.step(n, diag_last=True)
+        b1.close()
+    for A, M in zip(ones, mixed):
+        _assert_same(A, M)
+        da, dm = A.last_diag(), M.last_diag()
+        assert da["step"] == dm["step"] == A.t - 1
+        # per-block partial sums run in the compute precision, and the launch
+        # shapes differ, so the summation order differs
+        rel = 1e-12 if storage == "fp64" else 1e-6
+        for k in ("mass", "n_heavy", "p_heavy", "p_light", "u_max", "kinetic"):
+            assert dm[k] == pytest.approx(da[k], rel=rel, abs=1e-300), k
+    B.close()
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32", "bf16"])
+def test_batch_matches_single_lattice_kernel(storage):
+    from paper_2512_01032_gb300 import pflb
+    alone, mixed = _pairs(storage)
+    B = pflb.Batch(mixed)
+    n = 37
+    B.step(n, diag_last=True)
+    for L in alone:
+        L.step(n - 1)
+        L.step_diag(1)
+    for A, M in zip(alone, mixed):
+        _assert_close(A, M, storage, n)
+        da, dm = A.last_diag(), M.last_diag()
+        assert da["step"] == dm["step"] == A.t - 1
+        assert dm["mass"] == pytest.approx(da["mass"], rel=1e-6)
+    B.close()
+
+
+def _batch_of_one_reference(storage, steps):
+    from paper_2512_01032_gb300 import pflb
+    ones, mixed = _pairs(storage)
+    for L, n in zip(ones, steps):
+        b1 = pflb.Batch([L])
+        b1.step(n)
+        b1.close()
+    return ones, mixed
+
+
+@pytest.mark.parametrize("shape", [(32, 4, 16, 0), (16, 8, 4, 1), (64, 4, 32, 2), (16, 16, 8, 0)])
+def test_batch_launch_shapes(shape):
+    from paper_2512_01032_gb300 import pflb
+    ones, mixed = _batch_of_one_reference("fp32", [23] * 5)
+    B = pflb.Batch(mixed)
+    B.set_launch(*shape)
+    B.step(5)
+    B.step(18)
+    for A, M in zip(ones, mixed):
+        _assert_same(A, M)
+
+
+def test_batch_tune_then_step():
+    from paper_2512_01032_gb300 import pflb
+    ones, mixed = _pairs("fp32")
+    B = pflb.Batch(mixed)
+    best = B.tune(trial_steps=2)
+    bx, by, lz, bps = best
+    assert bx * by <= 256 and lz >= 1 and bps >= 1
+    B.step(20)
+    done = mixed[0].t - ones[0].t
+    assert done > 20  # the tuner's trial steps are real steps
+    for L in ones:
+        b1 = pflb.Batch([L])
+        b1.step(done)
+        b1.close()
+    for A, M in zip(ones, mixed):
+        _assert_same(A, M)
+
+
+def test_batch_interleaves_with_single_steps():
+    """Single-lattice steps and diagnostics between batch steps keep the
+    lattice state consistent (parity, step counter, diagnostic buffers)."""
+    from paper_2512_01032_gb300 import pflb
+    alone, mixed = _pairs("fp64")
+    B = pflb.Batch(mixed)
+    B.step(3)
+    mixed[2].step_diag(1)
+    B.step(17, diag_last=True)
+    d = mixed[4].last_diag()
+    assert d["step"] == mixed[4].t - 1
+    mixed[0].step(2)
+    B.step(1)
+    for k, L in enumerate(alone):
+        n = 3 + (1 if k == 2 else 0) + 17 + (2 if k == 0 else 0) + 1
+        L.step(n)
+    for A, M in zip(alone, mixed):
+        _assert_close(A, M, "fp64", 0)
+
+
+def test_batch_rejects_bad_input():
+    from paper_2512_01032_gb300 import pflb
+    a = _lattice(CS.droplet_case(16, 4.0), "fp32")
+    b = _lattice(CS.droplet_case(16, 4.0), "fp64")
+    with pytest.raises(pflb.PflbError):
+        pflb.Batch([a, b])
+    with pytest.raises(pflb.PflbError):
+        pflb.Batch([a, a])
+    B = pflb.Batch([a])
+    with pytest.raises(pflb.PflbError):
+        B.step(0, diag_last=True)
+    with pytest.raises(pflb.PflbError):
+        B.set_launch(64, 8, 16, 0)
+    B.step(0)
+    assert a.t == 0
+    B.close()
