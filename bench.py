@@ -310,6 +310,84 @@ def main_channels(args):
     return 0
 
 
+def serve_trace(server, prepared, trace):
+    """Replay a request trace in real time: each request is submitted once
+    the wall clock passes its arrival time, the server ticking in between."""
+    t0 = time.perf_counter()
+    tickets, k = [], 0
+    while True:
+        now = time.perf_counter() - t0
+        while k < len(trace) and trace[k]["t_arrival"] <= now:
+            g, p, spec = prepared[k]
+            tickets.append(server.submit(g.nx, g.ny, g.nz, spec, solid=g.solid,
+                                         wall_normal=g.normals(), theta_cells=g.theta(), **p))
+            k += 1
+        n = server.tick()
+        if k == len(trace) and n == 0 and server.stats()["queued"] == 0:
+            break
+        if n == 0 and k < len(trace):
+            time.sleep(max(0.0, min(0.01, trace[k]["t_arrival"] - now)))
+    return tickets, time.perf_counter() - t0
+
+
+def main_serve(args):
+    """Critical-pressure solves served from a Poisson trace: continuous
+    batching (one persistent batch kernel per step over all resident
+    requests, admission by HBM budget) against the plain server (one request
+    at a time, FP32, one fused launch per step) on the same trace."""
+    import torch
+    from paper_2512_01032_gb300 import pflb
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    trace = synth.serving_trace(args.count)
+    prepared = []
+    for req in trace:
+        r = synth.constriction_request(req, ramp_every=args.ramp_every,
+                                       max_steps=13 * args.ramp_every)
+        prepared.append((r["geometry"], r["params"], synth.constriction_spec(r)))
+    out = {}
+    modes = [("batched", dict(storage="fp32", batched=True)),
+             ("plain", dict(storage="fp32", batched=False, max_active=1))]
+    if args.storage != "fp32":
+        modes.insert(1, (f"batched_{args.storage}", dict(storage=args.storage, batched=True)))
+    for name, cfg in modes:
+        S = pflb.Server(hbm_budget_bytes=int(args.budget_gb * (1 << 30)),
+                        steps_per_tick=args.ramp_every // 2, **cfg)
+        clk = ClockSampler(dev.index)
+        clk.start()
+        tickets, wall = serve_trace(S, prepared, trace)
+        clocks = clk.stop()
+        st = S.stats()
+        res = [S.poll(t) for t in tickets]
+        out[name] = dict(solves_per_s=st["solves_per_s"], p50_s=st["p50_s"], p99_s=st["p99_s"],
+                         mean_s=st["mean_s"], makespan_s=st["makespan_s"],
+                         completed=st["completed"], failed=st["failed"],
+                         rejected=st["rejected"], peak_gb=st["peak_bytes"] / 2 ** 30,
+                         mlups=st["cell_updates"] / max(st["makespan_s"], 1e-9) / 1e6,
+                         broke_through=sum(r["broke_through"] for r in res),
+                         steps=[r["steps"] for r in res], clocks=clocks)
+        S.close()
+    same = out["batched"]["steps"] == out["plain"]["steps"]
+    for v in out.values():
+        v.pop("steps")
+    extra = {k: v for k, v in out.items() if k not in ("batched", "plain")}
+    b = out["batched"]
+    line = {"metric": "served critical-pressure solves/s", "value": b["solves_per_s"],
+            "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "p50_s": b["p50_s"], "p99_s": b["p99_s"],
+            "config": {"workload": f"first {args.count} requests of the seeded Poisson trace "
+                                   f"(20/s): square constriction channels 4w x w x w, "
+                                   f"w in 48..96, beta ramp 0.7..1.3 every {args.ramp_every} "
+                                   f"steps, at most {13 * args.ramp_every} steps",
+                       "storage": "fp32", "budget_gb": args.budget_gb,
+                       "steps_per_tick": args.ramp_every // 2},
+            "batched": out["batched"], "plain_sequential_fp32": out["plain"], **extra,
+            "same_step_counts": same}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -319,18 +397,24 @@ def main(argv=None):
     ap.add_argument("--tile", type=str, default="", help="bx,by,lz of the fused kernel")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["sessile", "channels"], default="sessile",
+    ap.add_argument("--workload", choices=["sessile", "channels", "serve"], default="sessile",
                     help="sessile: the 128^3 sessile droplet (default); channels: many "
-                         "uneven channel lattices advanced as one batch")
+                         "uneven channel lattices advanced as one batch; serve: a request "
+                         "trace through the batching server and the plain server")
     ap.add_argument("--storage", choices=["fp32", "fp16", "bf16", "fp64"], default="bf16",
                     help="population storage of the channels workload")
-    ap.add_argument("--count", type=int, default=64, help="lattices of the channels workload")
+    ap.add_argument("--count", type=int, default=64,
+                    help="lattices of the channels workload / requests of the serve workload")
+    ap.add_argument("--ramp-every", type=int, default=500, help="serve: steps per beta level")
+    ap.add_argument("--budget-gb", type=float, default=16.0, help="serve: HBM budget")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return main_reference(args)
     args.warmup = max(args.warmup, 3)
     if args.workload == "channels":
         return main_channels(args)
+    if args.workload == "serve":
+        return main_serve(args)
 
     import torch
     import torch.distributed as dist

@@ -188,6 +188,10 @@ pflb_status pflb_last_diag(pflb_lattice *L, pflb_diag_t *out);
  * return those (as pflb_last_diag; synchronises). */
 pflb_status pflb_step_diag(pflb_lattice *L, int64_t nsteps, pflb_diag_t *out);
 
+/* Advance nsteps steps asynchronously; with diag_last != 0 (then nsteps >= 1)
+ * the last step accumulates diagnostics, read later with pflb_last_diag. */
+pflb_status pflb_step_ex(pflb_lattice *L, int64_t nsteps, int diag_last);
+
 /* Copy one macroscopic field of the current state (as the next step would
  * see it: phi = sum h, ghosts updated, P and u recovered) into host_out
  * (nx*ny*nz doubles; zero on solid cells).  Synchronises. */
@@ -280,6 +284,97 @@ pflb_status pflb_batch_step(pflb_batch *b, int64_t nsteps, int diag_last);
 
 /* Free the batch (not its lattices); NULL is ignored. */
 void pflb_batch_destroy(pflb_batch *b);
+
+/* ------------------------------------------------------------- serving
+ * A native request server for many independent solves of the kind the
+ * paper runs to find a critical (breakthrough) pressure (Sec. IV): each
+ * request is a lattice, an initial state and a pressure ramp applied as a
+ * body force, F_ex(t) = dir * beta(t) * p_ref / length with
+ *   beta(t) = min(beta0 + dbeta * floor(t / ramp_every), beta_max),
+ * run until breakthrough (the phi summed over the request's region box
+ * exceeds threshold) or max_steps.  Continuous batching: every tick admits
+ * queued requests in arrival order while their estimated device footprint
+ * (pflb_estimate_bytes) fits the HBM budget, advances every resident
+ * request by steps_per_tick steps (one persistent batch kernel per step, or
+ * one launch per request in plain mode), checks each request's
+ * diagnostics once, and retires the finished ones, freeing their memory.
+ * A request's trajectory does not depend on what it is batched with.
+ * Latency = time from submit to the tick that finishes the request (host
+ * steady clock).  Not thread-safe: one host thread drives a server. */
+typedef struct pflb_server pflb_server;
+
+typedef struct {
+  size_t hbm_budget_bytes; /* admission limit on the sum of resident footprints */
+  int storage;             /* population storage of every request (PFLB_STORAGE_*) */
+  int steps_per_tick;      /* steps between breakthrough checks (>= 1) */
+  int max_active;          /* resident request cap, 0 = budget only */
+  int batched;             /* 1: one batch kernel per step; 0: one launch per request */
+} pflb_server_config;
+
+typedef struct {
+  int init_shape;          /* pflb_init_tanh shape, centre, R and normal */
+  double center[3];
+  double R;
+  double normal[3];
+  double p_ref;            /* reference pressure (e.g. the capillary entry pressure) */
+  double length;           /* length over which the ramp pressure acts */
+  double dir[3];           /* unit force direction */
+  double beta0, dbeta, beta_max;
+  int64_t ramp_every;      /* multiple of steps_per_tick */
+  int64_t max_steps;       /* multiple of steps_per_tick */
+  int region[6];           /* breakthrough box x0,x1,y0,y1,z0,z1 */
+  double threshold;        /* breakthrough when region_mass > threshold */
+  int keep_phi;            /* keep the final phi field for pflb_server_fetch_phi */
+} pflb_solve_spec;
+
+enum { PFLB_REQ_QUEUED = 0, PFLB_REQ_RUNNING = 1, PFLB_REQ_DONE = 2, PFLB_REQ_FAILED = 3,
+       PFLB_REQ_REJECTED = 4 };
+
+typedef struct {
+  int state;               /* PFLB_REQ_* */
+  int broke_through;       /* 1 if the region threshold was crossed */
+  double beta;             /* ramp value at the finishing tick */
+  int64_t steps;           /* steps run */
+  double latency_s;        /* submit -> finish (0 until finished) */
+  double queue_s;          /* submit -> admission */
+  double region_mass, mass, u_max;  /* diagnostics of the last step */
+} pflb_solve_result;
+
+typedef struct {
+  int64_t submitted, completed, failed, rejected, active, queued;
+  double p50_s, p99_s, mean_s, max_s; /* latency percentiles of completed requests */
+  double makespan_s;       /* first submit -> last completion */
+  double solves_per_s;     /* completed / makespan_s */
+  double cell_updates;     /* fluid-or-solid cells x steps advanced */
+  size_t bytes_in_use, peak_bytes;
+  int64_t ticks;
+} pflb_server_stats;
+
+/* cuda_stream as pflb_create (NULL: the server creates its own). */
+pflb_status pflb_server_create(const pflb_server_config *cfg, void *cuda_stream,
+                               pflb_server **out);
+
+/* Queue a request (the geometry arrays are copied).  A request whose
+ * footprint alone exceeds the budget is REJECTED at once; the call still
+ * returns PFLB_OK and a ticket (>= 1). */
+pflb_status pflb_server_submit(pflb_server *s, const pflb_geometry *geom,
+                               const pflb_params *params, const pflb_solve_spec *spec,
+                               int64_t *ticket);
+
+/* One tick: admit, advance, retire (synchronises once).  n_active (may be
+ * NULL) receives the number of resident requests after the tick. */
+pflb_status pflb_server_tick(pflb_server *s, int *n_active);
+
+pflb_status pflb_server_poll(pflb_server *s, int64_t ticket, pflb_solve_result *out);
+
+/* Copy the final phi (nx*ny*nz doubles, solids 0) of a finished request
+ * submitted with keep_phi; n is the capacity of out in doubles. */
+pflb_status pflb_server_fetch_phi(pflb_server *s, int64_t ticket, double *out, int64_t n);
+
+pflb_status pflb_server_stats_get(pflb_server *s, pflb_server_stats *out);
+
+/* Free the server and every resident lattice; NULL is ignored. */
+void pflb_server_destroy(pflb_server *s);
 
 /* Free the lattice (synchronises its stream first).  NULL is ignored. */
 void pflb_destroy(pflb_lattice *L);

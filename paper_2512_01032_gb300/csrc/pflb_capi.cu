@@ -551,6 +551,14 @@ static pflb_status fetch_diag(pflb_lattice *L, const double *dev, pflb_diag_t *o
   return PFLB_OK;
 }
 
+pflb_status pflb_step_ex(pflb_lattice *L, int64_t nsteps, int diag_last) {
+  pflb_status s = check_lattice(L);
+  if (s != PFLB_OK) return s;
+  if (nsteps < 0 || (diag_last && nsteps < 1)) return fail(PFLB_ERR_ARG, "bad step count");
+  for (int64_t k = 0; k < nsteps; ++k) CK(L, do_step(L, diag_last && k == nsteps - 1));
+  return PFLB_OK;
+}
+
 pflb_status pflb_step_diag(pflb_lattice *L, int64_t nsteps, pflb_diag_t *out) {
   pflb_status s = check_lattice(L);
   if (s != PFLB_OK) return s;

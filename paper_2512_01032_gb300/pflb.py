@@ -27,6 +27,43 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NAN"
                 5: "ERR_TIMEOUT", 6: "ERR_BUDGET", 7: "ERR_STATE"}
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("storage", C.c_int),
+                ("steps_per_tick", C.c_int), ("max_active", C.c_int), ("batched", C.c_int)]
+
+
+class SolveSpec(C.Structure):
+    _fields_ = [("init_shape", C.c_int), ("center", C.c_double * 3), ("R", C.c_double),
+                ("normal", C.c_double * 3), ("p_ref", C.c_double), ("length", C.c_double),
+                ("dir", C.c_double * 3), ("beta0", C.c_double), ("dbeta", C.c_double),
+                ("beta_max", C.c_double), ("ramp_every", C.c_int64), ("max_steps", C.c_int64),
+                ("region", C.c_int * 6), ("threshold", C.c_double), ("keep_phi", C.c_int)]
+
+
+class SolveResult(C.Structure):
+    _fields_ = [("state", C.c_int), ("broke_through", C.c_int), ("beta", C.c_double),
+                ("steps", C.c_int64), ("latency_s", C.c_double), ("queue_s", C.c_double),
+                ("region_mass", C.c_double), ("mass", C.c_double), ("u_max", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("rejected", C.c_int64), ("active", C.c_int64), ("queued", C.c_int64),
+                ("p50_s", C.c_double), ("p99_s", C.c_double), ("mean_s", C.c_double),
+                ("max_s", C.c_double), ("makespan_s", C.c_double), ("solves_per_s", C.c_double),
+                ("cell_updates", C.c_double), ("bytes_in_use", C.c_size_t),
+                ("peak_bytes", C.c_size_t), ("ticks", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_REJECTED = range(5)
+
+
 class PflbError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -136,6 +173,23 @@ def load(build_if_missing: bool = True):
     lib.pflb_batch_step.restype = st
     lib.pflb_batch_destroy.argtypes = [C.c_void_p]
     lib.pflb_batch_destroy.restype = None
+    lib.pflb_step_ex.argtypes = [C.c_void_p, C.c_int64, C.c_int]
+    lib.pflb_step_ex.restype = st
+    lib.pflb_server_create.argtypes = [_P(ServerConfig), C.c_void_p, _P(C.c_void_p)]
+    lib.pflb_server_create.restype = st
+    lib.pflb_server_submit.argtypes = [C.c_void_p, _P(Geometry), _P(Params), _P(SolveSpec),
+                                       _P(C.c_int64)]
+    lib.pflb_server_submit.restype = st
+    lib.pflb_server_tick.argtypes = [C.c_void_p, _P(C.c_int)]
+    lib.pflb_server_tick.restype = st
+    lib.pflb_server_poll.argtypes = [C.c_void_p, C.c_int64, _P(SolveResult)]
+    lib.pflb_server_poll.restype = st
+    lib.pflb_server_fetch_phi.argtypes = [C.c_void_p, C.c_int64, _d, C.c_int64]
+    lib.pflb_server_fetch_phi.restype = st
+    lib.pflb_server_stats_get.argtypes = [C.c_void_p, _P(ServerStats)]
+    lib.pflb_server_stats_get.restype = st
+    lib.pflb_server_destroy.argtypes = [C.c_void_p]
+    lib.pflb_server_destroy.restype = None
     lib.pflb_last_error.argtypes = []
     lib.pflb_last_error.restype = C.c_char_p
     _lib = lib
@@ -148,6 +202,10 @@ def _check(status: int):
         raise PflbError(status, msg)
 
 
+_STORAGE_NAMES = {"fp64": STORAGE_FP64, "fp32": STORAGE_FP32, "fp16": STORAGE_FP16,
+                  "bf16": STORAGE_BF16}
+
+
 def default_params(**kw) -> Params:
     p = Params()
     load().pflb_default_params(C.byref(p))
@@ -156,8 +214,7 @@ def default_params(**kw) -> Params:
             for a in range(3):
                 p.Fex[a] = float(v[a])
         elif k == "storage" and isinstance(v, str):
-            p.storage = {"fp64": STORAGE_FP64, "fp32": STORAGE_FP32, "fp16": STORAGE_FP16,
-                         "bf16": STORAGE_BF16}[v]
+            p.storage = _STORAGE_NAMES[v]
         elif hasattr(p, k):
             setattr(p, k, v)
         else:
@@ -356,3 +413,74 @@ class Batch:
 
     def step(self, n=1, diag_last=False):
         _check(self._lib.pflb_batch_step(self._h, int(n), 1 if diag_last else 0))
+
+
+class Server:
+    """Request server with continuous batching (``pflb_server``).
+
+    ``submit`` takes a geometry (solid mask, optional normals and angles),
+    model parameters and a solve spec (dict with the SolveSpec fields);
+    ``tick`` advances the resident requests; ``poll`` / ``stats`` report."""
+
+    def __init__(self, hbm_budget_bytes=16 << 30, storage="fp32", steps_per_tick=250,
+                 max_active=0, batched=True, stream=None):
+        self._lib = load()
+        self.storage = _STORAGE_NAMES[storage] if isinstance(storage, str) else int(storage)
+        cfg = ServerConfig(int(hbm_budget_bytes), self.storage, int(steps_per_tick),
+                           int(max_active), 1 if batched else 0)
+        h = C.c_void_p()
+        _check(self._lib.pflb_server_create(C.byref(cfg), C.c_void_p(_stream_handle(stream)),
+                                            C.byref(h)))
+        self._h = h
+        self._dims = {}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.pflb_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, nx, ny, nz, spec: dict, solid=None, wall_normal=None, theta_cells=None,
+               **params) -> int:
+        params.pop("storage", None)  # every request runs at the server's storage
+        p = default_params(storage=self.storage, **params)
+        g, keep = make_geometry(nx, ny, nz, solid, wall_normal, theta_cells)
+        sp = SolveSpec()
+        for k, v in spec.items():
+            f = getattr(sp, k)
+            if isinstance(f, C.Array):
+                for i, x in enumerate(v):
+                    f[i] = x
+            else:
+                setattr(sp, k, v)
+        t = C.c_int64()
+        _check(self._lib.pflb_server_submit(self._h, C.byref(g), C.byref(p), C.byref(sp),
+                                            C.byref(t)))
+        self._dims[t.value] = int(nx) * int(ny) * int(nz)
+        return t.value
+
+    def tick(self) -> int:
+        n = C.c_int()
+        _check(self._lib.pflb_server_tick(self._h, C.byref(n)))
+        return n.value
+
+    def poll(self, ticket) -> dict:
+        r = SolveResult()
+        _check(self._lib.pflb_server_poll(self._h, int(ticket), C.byref(r)))
+        return r.as_dict()
+
+    def fetch_phi(self, ticket) -> np.ndarray:
+        n = self._dims[int(ticket)]
+        out = np.empty(n, np.float64)
+        _check(self._lib.pflb_server_fetch_phi(self._h, int(ticket), out.ctypes.data_as(_d), n))
+        return out
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(self._lib.pflb_server_stats_get(self._h, C.byref(st)))
+        return st.as_dict()

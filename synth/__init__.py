@@ -262,6 +262,52 @@ def constriction_channel(w, ratio, theta_deg):
     return Geometry(nx, ny, nz, shapes, theta_deg=theta_deg), d
 
 
+def constriction_params(theta_deg):
+    """Slug through a constriction: density ratio 1000, dynamic viscosity
+    ratio 50 (nu_H = 1/60, nu_L = 1/3), sigma = 0.01, W = 4, M = 0.1666,
+    optimised model."""
+    return dict(sigma=0.01, W=4.0, M=0.1666, rho_H=1.0, rho_L=1e-3, nu_H=1.0 / 60.0,
+                nu_L=1.0 / 3.0, theta_deg=theta_deg, F_mode=1, mobility_corr=1, free_slip=1,
+                blend=0.95)
+
+
+def critical_pressure(sigma, theta_deg, d, H):
+    """Capillary entry pressure of a square constriction of side d in a square
+    duct of side H (3-D square-duct analogue of the paper's 2-D estimate):
+    4 sigma |cos theta| (1/d - 1/H)."""
+    return 4.0 * sigma * abs(math.cos(math.radians(theta_deg))) * (1.0 / d - 1.0 / H)
+
+
+def constriction_request(req: dict, ramp_every=2000, max_steps=26000):
+    """Geometry, parameters, initial slug and breakthrough test of one
+    serving_trace entry.  The slug (liquid, phi = 1) fills the duct for
+    0.25 w <= x < 1.25 w, upstream of the constriction [1.5 w, 2.5 w).  The
+    pressure ramp is a body force F_x with F_x L = beta P_crit (L = 4 w, the
+    periodic length), beta = 0.7, 0.75, ... raised every ramp_every steps up
+    to 1.3.  Breakthrough: liquid volume beyond the constriction exit + W
+    (region 2.5 w + W <= x < 3.75 w) above half a constriction cross-section."""
+    w = req["w"]
+    g, d = constriction_channel(w, req["ratio"], req["theta"])
+    p = constriction_params(req["theta"])
+    pc = critical_pressure(p["sigma"], req["theta"], d, w)
+    init = dict(shape=2, center=(0.75 * w - 0.5, 0.0, 0.0), R=0.5 * w, normal=(1.0, 0.0, 0.0))
+    x_lo = int(math.ceil(2.5 * w + p["W"]))
+    region = (x_lo, int(3.75 * w), 0, g.ny, 0, g.nz)  # x0, x1, y0, y1, z0, z1
+    return dict(geometry=g, params=p, init=init, d=d, p_crit=pc, length=float(g.nx),
+                beta0=0.7, dbeta=0.05, beta_max=1.3, ramp_every=ramp_every,
+                max_steps=max_steps, region=region, threshold=0.5 * d * d)
+
+
+def constriction_spec(r: dict, keep_phi=False) -> dict:
+    """The pflb_solve_spec fields of a constriction_request."""
+    i = r["init"]
+    return dict(init_shape=i["shape"], center=i["center"], R=i["R"], normal=i["normal"],
+                p_ref=r["p_crit"], length=r["length"], dir=(1.0, 0.0, 0.0), beta0=r["beta0"],
+                dbeta=r["dbeta"], beta_max=r["beta_max"], ramp_every=r["ramp_every"],
+                max_steps=r["max_steps"], region=r["region"], threshold=r["threshold"],
+                keep_phi=1 if keep_phi else 0)
+
+
 def serving_trace(count=200, rate=20.0, seed=2512010321):
     """Poisson arrivals of critical-pressure solves (seeded)."""
     rng = np.random.Generator(np.random.PCG64(seed))

@@ -62,6 +62,32 @@ int main(void) {
     assert got["cl_m2"] == pflb.Diag.cl_m2.offset
 
 
+def test_server_struct_layouts_match_header(tmp_path):
+    """The serving structs: sizeof and every field offset equal the ctypes
+    mirrors."""
+    import ctypes as C
+    from paper_2512_01032_gb300 import pflb
+    structs = {"pflb_server_config": pflb.ServerConfig, "pflb_solve_spec": pflb.SolveSpec,
+               "pflb_solve_result": pflb.SolveResult, "pflb_server_stats": pflb.ServerStats}
+    lines = []
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    src = tmp_path / "layout2.c"
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"pflb.h\"\n"
+                   "int main(void) {\n" + "\n".join(lines) + "\n  return 0;\n}\n")
+    exe = tmp_path / "layout2"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    for line in out.strip().splitlines():
+        cname, f, v = line.split()
+        py = structs[cname]
+        want = C.sizeof(py) if f == "size" else getattr(py, f).offset
+        assert int(v) == want, (cname, f)
+
+
 def test_default_params_are_the_papers():
     from paper_2512_01032_gb300 import pflb
     gold = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_constants.json")))
@@ -108,6 +134,22 @@ def test_create_rejects_bad_geometry():
     assert lib.pflb_batch_set_launch(None, 32, 4, 16, 0) == pflb.ERR_ARG
     assert lib.pflb_batch_tune(None, 1, None) == pflb.ERR_ARG
     lib.pflb_batch_destroy(None)
+    # server: null and invalid arguments are rejected before any device call
+    srv = C.c_void_p()
+    assert lib.pflb_server_create(None, None, C.byref(srv)) == pflb.ERR_ARG
+    cfg = pflb.ServerConfig(1 << 30, pflb.STORAGE_FP32, 0, 0, 1)
+    assert lib.pflb_server_create(C.byref(cfg), None, C.byref(srv)) == pflb.ERR_ARG
+    cfg = pflb.ServerConfig(0, pflb.STORAGE_FP32, 10, 0, 1)
+    assert lib.pflb_server_create(C.byref(cfg), None, C.byref(srv)) == pflb.ERR_ARG
+    t = C.c_int64()
+    assert lib.pflb_server_submit(None, None, None, None, C.byref(t)) == pflb.ERR_ARG
+    assert lib.pflb_server_tick(None, None) == pflb.ERR_ARG
+    r = pflb.SolveResult()
+    assert lib.pflb_server_poll(None, 1, C.byref(r)) == pflb.ERR_ARG
+    st = pflb.ServerStats()
+    assert lib.pflb_server_stats_get(None, C.byref(st)) == pflb.ERR_ARG
+    lib.pflb_server_destroy(None)
+    assert lib.pflb_step_ex(None, 1, 0) == pflb.ERR_ARG
 
 
 def test_estimate_bytes_counts_wall_nodes():

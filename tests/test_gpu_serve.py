@@ -1,0 +1,129 @@
+"""Request server (continuous batching, HBM-budget admission): a request's
+result does not depend on what it was served with, admission respects the
+budget, breakthrough and failure are reported per request."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TICK = 25
+
+
+def _requests(count=4):
+    reqs = []
+    for k, (w, ratio, theta) in enumerate([(16, 0.5, 120.0), (20, 0.4, 135.0), (18, 0.6, 100.0),
+                                          (24, 0.5, 150.0)][:count]):
+        r = synth.constriction_request(dict(w=w, ratio=ratio, theta=theta), ramp_every=50,
+                                       max_steps=150 + 25 * k)
+        reqs.append(r)
+    return reqs
+
+
+def _submit(S, r, keep_phi=True, **override):
+    g = r["geometry"]
+    p = dict(r["params"], **override)
+    return S.submit(g.nx, g.ny, g.nz, synth.constriction_spec(r, keep_phi), solid=g.solid,
+                    wall_normal=g.normals(), theta_cells=g.theta(), **p)
+
+
+def _drain(S, limit=10000):
+    for _ in range(limit):
+        if S.tick() == 0 and S.stats()["queued"] == 0:
+            return
+    raise AssertionError("server did not drain")
+
+
+def _serve(reqs, **cfg):
+    from paper_2512_01032_gb300 import pflb
+    S = pflb.Server(steps_per_tick=TICK, **cfg)
+    tickets = [_submit(S, r) for r in reqs]
+    _drain(S)
+    out = [(S.poll(t), S.fetch_phi(t)) for t in tickets]
+    st = S.stats()
+    S.close()
+    return out, st
+
+
+@pytest.mark.parametrize("storage", ["fp32", "bf16"])
+def test_alone_equals_mixed(storage):
+    """Each request served alone and in a mix (all at once, and under a
+    budget that forces queueing and batch rebuilds) gives bitwise the same
+    final phi, step count and ramp value."""
+    from paper_2512_01032_gb300 import pflb
+    reqs = _requests()
+    alone = [_serve([r], storage=storage)[0][0] for r in reqs]
+    mixed, st = _serve(reqs, storage=storage)
+    sizes = [pflb.estimate_bytes(r["geometry"].nx, r["geometry"].ny, r["geometry"].nz,
+                                 r["geometry"].solid, storage=pflb._STORAGE_NAMES[storage])
+             for r in reqs]
+    budget = sorted(sizes)[-1] + sorted(sizes)[-2]
+    queued, st2 = _serve(reqs, storage=storage, hbm_budget_bytes=budget)
+    assert st["completed"] == st2["completed"] == len(reqs)
+    assert st2["peak_bytes"] <= budget
+    for (ra, pa), (rm, pm), (rq, pq) in zip(alone, mixed, queued):
+        for res in (rm, rq):
+            assert res["state"] == pflb.REQ_DONE
+            assert res["steps"] == ra["steps"] and res["beta"] == ra["beta"]
+            assert res["broke_through"] == ra["broke_through"]
+        assert np.array_equal(pa, pm) and np.array_equal(pa, pq)
+        assert np.isfinite(pa).all()
+
+
+def test_max_steps_and_ramp():
+    from paper_2512_01032_gb300 import pflb
+    reqs = _requests()
+    res, st = _serve(reqs, storage="fp32")
+    for r, (out, _) in zip(reqs, res):
+        assert out["state"] == pflb.REQ_DONE
+        assert out["steps"] == r["max_steps"] and not out["broke_through"]
+        # beta0 + dbeta * floor((max_steps - 1) / ramp_every)
+        want = min(r["beta0"] + r["dbeta"] * ((r["max_steps"] - 1) // r["ramp_every"]),
+                   r["beta_max"])
+        assert out["beta"] == pytest.approx(want, abs=1e-12)
+        assert out["latency_s"] >= out["queue_s"] >= 0
+    assert st["p50_s"] <= st["p99_s"] <= st["max_s"]
+    assert st["cell_updates"] == sum(r["geometry"].N * r["max_steps"] for r in reqs)
+
+
+def test_breakthrough_retires_at_first_check():
+    """A region box over the slug itself holds liquid from the start: the
+    request is finished as broken through at the first tick."""
+    from paper_2512_01032_gb300 import pflb
+    r = _requests(1)[0]
+    g = r["geometry"]
+    r = dict(r, region=(0, g.nx // 2, 0, g.ny, 0, g.nz), threshold=1.0)
+    (out, phi), = _serve([r], storage="fp32")[0]
+    assert out["state"] == pflb.REQ_DONE and out["broke_through"] == 1
+    assert out["steps"] == TICK and out["region_mass"] > 1.0
+
+
+def test_budget_rejects_and_invalid_request_fails_alone():
+    from paper_2512_01032_gb300 import pflb
+    reqs = _requests(3)
+    S = pflb.Server(steps_per_tick=TICK, storage="fp32", hbm_budget_bytes=64 << 20)
+    big = synth.constriction_request(dict(w=96, ratio=0.5, theta=120.0))
+    t_big = _submit(S, big, keep_phi=False)
+    assert S.poll(t_big)["state"] == pflb.REQ_REJECTED
+    t_bad = _submit(S, reqs[0], nu_H=0.0)  # tau = 1/2: refused at admission
+    t_ok = [_submit(S, r) for r in reqs[1:]]
+    _drain(S)
+    assert S.poll(t_bad)["state"] == pflb.REQ_FAILED
+    for t in t_ok:
+        assert S.poll(t)["state"] == pflb.REQ_DONE
+    st = S.stats()
+    assert (st["rejected"], st["failed"], st["completed"]) == (1, 1, 2)
+    assert st["bytes_in_use"] == 0 and st["active"] == 0
+    S.close()
+
+
+def test_plain_sequential_matches_batched():
+    """The plain mode (one request at a time, one fused launch per step) and
+    the batched mode agree to FP32 rounding."""
+    reqs = _requests(3)
+    plain, _ = _serve(reqs, storage="fp32", batched=False, max_active=1)
+    batched, _ = _serve(reqs, storage="fp32")
+    for (rp, pp), (rb, pb) in zip(plain, batched):
+        assert rp["steps"] == rb["steps"]
+        assert np.max(np.abs(pp - pb)) < 1e-4
