@@ -319,8 +319,9 @@ def serve_trace(server, prepared, trace):
         now = time.perf_counter() - t0
         while k < len(trace) and trace[k]["t_arrival"] <= now:
             g, p, spec = prepared[k]
-            tickets.append(server.submit(g.nx, g.ny, g.nz, spec, solid=g.solid,
-                                         wall_normal=g.normals(), theta_cells=g.theta(), **p))
+            tickets.append(server.submit(g["nx"], g["ny"], g["nz"], spec, solid=g["solid"],
+                                         wall_normal=g["normals"], theta_cells=g["theta"],
+                                         **p))
             k += 1
         n = server.tick()
         if k == len(trace) and n == 0 and server.stats()["queued"] == 0:
@@ -344,12 +345,18 @@ def main_serve(args):
     for req in trace:
         r = synth.constriction_request(req, ramp_every=args.ramp_every,
                                        max_steps=13 * args.ramp_every)
-        prepared.append((r["geometry"], r["params"], synth.constriction_spec(r)))
+        g = r["geometry"]
+        # the client's geometry (mask, normals, angles) is ready before the trace starts
+        geo = dict(nx=g.nx, ny=g.ny, nz=g.nz, solid=g.solid, normals=g.normals(),
+                   theta=g.theta())
+        prepared.append((geo, r["params"], synth.constriction_spec(r)))
     out = {}
-    modes = [("batched", dict(storage="fp32", batched=True)),
+    modes = [("batched", dict(storage="fp32", batched=True,
+                              max_active_cells=args.max_cells)),
              ("plain", dict(storage="fp32", batched=False, max_active=1))]
     if args.storage != "fp32":
-        modes.insert(1, (f"batched_{args.storage}", dict(storage=args.storage, batched=True)))
+        modes.insert(1, (f"batched_{args.storage}", dict(storage=args.storage, batched=True,
+                                                         max_active_cells=args.max_cells)))
     for name, cfg in modes:
         S = pflb.Server(hbm_budget_bytes=int(args.budget_gb * (1 << 30)),
                         steps_per_tick=args.ramp_every // 2, **cfg)
@@ -365,6 +372,8 @@ def main_serve(args):
                          rejected=st["rejected"], peak_gb=st["peak_bytes"] / 2 ** 30,
                          mlups=st["cell_updates"] / max(st["makespan_s"], 1e-9) / 1e6,
                          broke_through=sum(r["broke_through"] for r in res),
+                         host_s={k: st[k] for k in ("admit_s", "wait_s", "retire_s")},
+                         wall_s=wall,
                          steps=[r["steps"] for r in res], clocks=clocks)
         S.close()
     same = out["batched"]["steps"] == out["plain"]["steps"]
@@ -381,6 +390,7 @@ def main_serve(args):
                                    f"w in 48..96, beta ramp 0.7..1.3 every {args.ramp_every} "
                                    f"steps, at most {13 * args.ramp_every} steps",
                        "storage": "fp32", "budget_gb": args.budget_gb,
+                       "max_active_cells": args.max_cells,
                        "steps_per_tick": args.ramp_every // 2},
             "batched": out["batched"], "plain_sequential_fp32": out["plain"], **extra,
             "same_step_counts": same}
@@ -407,6 +417,8 @@ def main(argv=None):
                     help="lattices of the channels workload / requests of the serve workload")
     ap.add_argument("--ramp-every", type=int, default=500, help="serve: steps per beta level")
     ap.add_argument("--budget-gb", type=float, default=16.0, help="serve: HBM budget")
+    ap.add_argument("--max-cells", type=int, default=8 << 20,
+                    help="serve: cap on resident cells of the batching server (0 = none)")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return main_reference(args)

@@ -150,7 +150,9 @@ pflb_status pflb_create(const pflb_geometry *geom, const pflb_params *params, vo
  *           distance from center (cell centres at integer coordinates);
  *   shape 1 (half space): phi = (1 + tanh(2 d/W))/2, d = (center - x).normal;
  *   shape 2 (slab): phi = (1 + tanh(2 (R - |d|)/W))/2.
- * normal may be NULL for shape 0.  phi is zero on solid cells. */
+ * normal may be NULL for shape 0.  phi is zero on solid cells.  The
+ * initialisation runs asynchronously on the lattice stream (the host data is
+ * copied before return). */
 pflb_status pflb_init_tanh(pflb_lattice *L, int shape, const double center[3], double R,
                            const double normal[3], double P0);
 
@@ -294,10 +296,13 @@ void pflb_batch_destroy(pflb_batch *b);
  * run until breakthrough (the phi summed over the request's region box
  * exceeds threshold) or max_steps.  Continuous batching: every tick admits
  * queued requests in arrival order while their estimated device footprint
- * (pflb_estimate_bytes) fits the HBM budget, advances every resident
- * request by steps_per_tick steps (one persistent batch kernel per step, or
- * one launch per request in plain mode), checks each request's
- * diagnostics once, and retires the finished ones, freeing their memory.
+ * (pflb_estimate_bytes) fits the HBM budget (and the optional caps on
+ * resident requests and cells), advances every resident request by
+ * steps_per_tick steps (one persistent batch kernel per step, or one launch
+ * per request in plain mode), checks each request's diagnostics once, and
+ * retires the finished ones, freeing their memory.  Admission's host work
+ * (building and uploading a new lattice) runs while the tick's steps run on
+ * the GPU; admitted requests start at the next tick.
  * A request's trajectory does not depend on what it is batched with.
  * Latency = time from submit to the tick that finishes the request (host
  * steady clock).  Not thread-safe: one host thread drives a server. */
@@ -309,6 +314,8 @@ typedef struct {
   int steps_per_tick;      /* steps between breakthrough checks (>= 1) */
   int max_active;          /* resident request cap, 0 = budget only */
   int batched;             /* 1: one batch kernel per step; 0: one launch per request */
+  int64_t max_active_cells;/* cap on the summed cells of resident requests, 0 = none (a
+                              request larger than the cap still runs when it is alone) */
 } pflb_server_config;
 
 typedef struct {
@@ -348,6 +355,9 @@ typedef struct {
   double cell_updates;     /* fluid-or-solid cells x steps advanced */
   size_t bytes_in_use, peak_bytes;
   int64_t ticks;
+  double admit_s;          /* host time spent admitting (lattice build and upload) */
+  double wait_s;           /* host time blocked on the GPU at the end of ticks */
+  double retire_s;         /* host time spent checking and retiring requests */
 } pflb_server_stats;
 
 /* cuda_stream as pflb_create (NULL: the server creates its own). */

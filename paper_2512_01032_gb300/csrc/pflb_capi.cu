@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "pflb_internal.h"
@@ -141,6 +142,57 @@ inline long long wrap(long long a, long long n) {
   return a < 0 ? a + n : a;
 }
 
+// Runs fn(z0, z1) over [0, nz) split into contiguous chunks on up to 16
+// host threads (the chunks write disjoint outputs).
+template <class F>
+void parallel_z(int nz, long long cells, F &&fn) {
+  unsigned hw = std::thread::hardware_concurrency();
+  int nt = (int)std::min<unsigned>(hw ? hw : 1, 16u);
+  if (cells < (1 << 16)) nt = 1;
+  nt = std::max(1, std::min(nt, nz));
+  if (nt == 1) {
+    fn(0, nz);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t) {
+    const int z0 = (int)((long long)nz * t / nt), z1 = (int)((long long)nz * (t + 1) / nt);
+    th.emplace_back([&fn, z0, z1] { fn(z0, z1); });
+  }
+  for (auto &t : th) t.join();
+}
+
+// Solid-link bits (bit i set when x + c_i is solid, periodic wrap) of every
+// fluid cell; 0 for solid cells.
+std::vector<uint32_t> link_masks(const pflb_geometry *g) {
+  const int nx = g->nx, ny = g->ny, nz = g->nz;
+  const long long N = (long long)nx * ny * nz;
+  std::vector<uint32_t> mask((size_t)N, 0);
+  std::vector<int> xw(nx + 2), yw(ny + 2), zw(nz + 2);  // coordinate + 1 -> wrapped
+  for (int a = -1; a <= nx; ++a) xw[a + 1] = (int)wrap(a, nx);
+  for (int a = -1; a <= ny; ++a) yw[a + 1] = (int)wrap(a, ny);
+  for (int a = -1; a <= nz; ++a) zw[a + 1] = (int)wrap(a, nz);
+  const uint8_t *solid = g->solid;
+  parallel_z(nz, N, [&](int z0, int z1) {
+    for (int z = z0; z < z1; ++z)
+      for (int y = 0; y < ny; ++y) {
+        const long long row = (long long)nx * (y + (long long)ny * z);
+        for (int x = 0; x < nx; ++x) {
+          if (solid[row + x]) continue;
+          uint32_t m = 0;
+          for (int i = 1; i < pflb::Q; ++i) {
+            const long long nb = xw[x + pflb::cx_of(i) + 1] +
+                                 (long long)nx * (yw[y + pflb::cy_of(i) + 1] +
+                                                  (long long)ny * zw[z + pflb::cz_of(i) + 1]);
+            if (solid[nb]) m |= 1u << i;
+          }
+          mask[(size_t)(row + x)] = m;
+        }
+      }
+  });
+  return mask;
+}
+
 struct HostGeom {
   std::vector<uint8_t> flags;
   std::vector<int> widx;
@@ -150,8 +202,8 @@ struct HostGeom {
 
 // Flags, wall list (cell order), solid-link masks, normals and angles.
 void build_geometry(const pflb_geometry *g, const pflb_params *p, HostGeom &hg) {
-  const int nx = g->nx, ny = g->ny, nz = g->nz;
-  const long long N = (long long)nx * ny * nz;
+  const long long N = (long long)g->nx * g->ny * g->nz;
+  const std::vector<uint32_t> all = link_masks(g);
   hg.flags.assign(N, 0);
   hg.widx.assign(N, -1);
   std::vector<uint32_t> masks;
@@ -159,20 +211,11 @@ void build_geometry(const pflb_geometry *g, const pflb_params *p, HostGeom &hg) 
   for (long long c = 0; c < N; ++c) {
     if (g->solid[c]) {
       hg.flags[c] = pflb::F_SOLID;
-      continue;
-    }
-    const long long x = c % nx, y = (c / nx) % ny, z = c / ((long long)nx * ny);
-    uint32_t m = 0;
-    for (int i = 1; i < pflb::Q; ++i) {
-      long long xx = wrap(x + pflb::cx_of(i), nx), yy = wrap(y + pflb::cy_of(i), ny),
-                zz = wrap(z + pflb::cz_of(i), nz);
-      if (g->solid[xx + nx * (yy + (long long)ny * zz)]) m |= 1u << i;
-    }
-    if (m) {
+    } else if (all[c]) {
       hg.flags[c] = pflb::F_WALL;
       hg.widx[c] = (int)cells.size();
       cells.push_back(c);
-      masks.push_back(m);
+      masks.push_back(all[c]);
     }
   }
   const size_t nw = cells.size();
@@ -216,6 +259,10 @@ void free_all(Lattice *L) {
                   L->wgeo, L->ghost, L->phi, L->diag, L->out, L->phi0, L->err};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+  if (L->aux) cudaStreamDestroy(L->aux);
+  if (L->ev_init) cudaEventDestroy(L->ev_init);
+  L->aux = nullptr;
+  L->ev_init = nullptr;
 }
 
 int64_t bytes_for(long long N, long long nw, int storage) {
@@ -366,8 +413,14 @@ pflb_status pflb_create(const pflb_geometry *geom, const pflb_params *params, vo
     wgeo_f.assign(hg.wgeo.begin(), hg.wgeo.end());
     wgeo_src = wgeo_f.data();
   }
-  cudaStream_t st = L->stream;
-  e = cudaMemcpyAsync(L->flags, hg.flags.data(), N, cudaMemcpyHostToDevice, st);
+  // The upload runs on a private stream: the new buffers are not referenced
+  // by anything queued on the lattice's stream, so creating a lattice does
+  // not wait for the caller's work in flight (e.g. other lattices' steps).
+  e = cudaStreamCreateWithFlags(&L->aux, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L->ev_init, cudaEventDisableTiming);
+  cudaStream_t st = L->aux;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(L->flags, hg.flags.data(), N, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(L->widx, hg.widx.data(), N * sizeof(int), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && nw)
@@ -390,9 +443,11 @@ pflb_status pflb_create(const pflb_geometry *geom, const pflb_params *params, vo
   return PFLB_OK;
 }
 
+// Initial state from L->phi0, asynchronous on the lattice stream; the
+// event marks when phi0 may be overwritten again.
 static pflb_status init_from_device_phi(pflb_lattice *L, double P0) {
   CK(L, do_init(L, L->phi0, P0));
-  CK(L, cudaStreamSynchronize(L->stream));
+  CK(L, cudaEventRecord(L->ev_init, L->stream));
   return PFLB_OK;
 }
 
@@ -409,8 +464,13 @@ pflb_status pflb_init_phi(pflb_lattice *L, const double *phi_host, double P0) {
     }
     L->dev_bytes += L->N * 8;
   }
+  // The copy runs on the private stream (after any earlier init of this
+  // lattice has read phi0) and the host waits for the copy alone, not for
+  // the work queued on the lattice stream.
+  CK(L, cudaStreamWaitEvent(L->aux, L->ev_init, 0));
   CK(L, cudaMemcpyAsync(L->phi0, phi_host, (size_t)L->N * sizeof(double), cudaMemcpyHostToDevice,
-                        L->stream));
+                        L->aux));
+  CK(L, cudaStreamSynchronize(L->aux));
   return init_from_device_phi(L, P0);
 }
 
@@ -434,8 +494,10 @@ pflb_status pflb_init_tanh(pflb_lattice *L, int shape, const double center[3], d
   }
   const double W = L->p.W;
   const int dims[3] = {L->nx, L->ny, L->nz};
-  for (long long c = 0; c < L->N; ++c) {
-    const long long pos[3] = {c % L->nx, (c / L->nx) % L->ny, c / ((long long)L->nx * L->ny)};
+  const long long plane = (long long)L->nx * L->ny;
+  parallel_z(L->nz, L->N, [&](int z0, int z1) {
+  for (long long c = z0 * plane; c < z1 * plane; ++c) {
+    const long long pos[3] = {c % L->nx, (c / L->nx) % L->ny, c / plane};
     double d[3];
     for (int a = 0; a < 3; ++a) {
       double dd = (double)pos[a] - center[a];
@@ -451,6 +513,7 @@ pflb_status pflb_init_tanh(pflb_lattice *L, int shape, const double center[3], d
     }
     phi[c] = 0.5 * (1.0 + std::tanh(2.0 * arg / W));  // Eq. 12
   }
+  });
   return pflb_init_phi(L, phi.data(), P0);
 }
 
@@ -612,16 +675,7 @@ int64_t pflb_estimate_bytes(const pflb_geometry *geom, int storage) {
   if (!geom || !geom->solid || geom->nx < 1 || geom->ny < 1 || geom->nz < 1) return -1;
   const long long N = (long long)geom->nx * geom->ny * geom->nz;
   long long nw = 0;
-  for (long long c = 0; c < N; ++c) {
-    if (geom->solid[c]) continue;
-    const long long x = c % geom->nx, y = (c / geom->nx) % geom->ny,
-                    z = c / ((long long)geom->nx * geom->ny);
-    for (int i = 1; i < pflb::Q; ++i) {
-      long long xx = wrap(x + pflb::cx_of(i), geom->nx), yy = wrap(y + pflb::cy_of(i), geom->ny),
-                zz = wrap(z + pflb::cz_of(i), geom->nz);
-      if (geom->solid[xx + geom->nx * (yy + (long long)geom->ny * zz)]) { ++nw; break; }
-    }
-  }
+  for (uint32_t m : link_masks(geom)) nw += m != 0;
   return bytes_for(N, nw, storage);
 }
 

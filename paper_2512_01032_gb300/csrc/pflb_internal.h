@@ -16,6 +16,8 @@ struct Lattice {
   int nw = 0;                 // wall nodes
   pflb_params p{};
   cudaStream_t stream = nullptr;
+  cudaStream_t aux = nullptr;       // private stream for host uploads
+  cudaEvent_t ev_init = nullptr;    // recorded after each init launch
   size_t elem = 4;            // bytes per stored population
   // device buffers
   void *h[2] = {nullptr, nullptr};  // [19][N] each

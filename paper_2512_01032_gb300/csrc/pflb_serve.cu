@@ -1,12 +1,13 @@
 // pflb_serve.cu -- request server with continuous batching over the lattice
 // and batch C API (host code only).
 //
-// Each tick: admit queued requests in arrival order while the budget holds,
-// set each resident request's ramp force for its own step count, advance all
-// resident requests by steps_per_tick steps (one persistent batch kernel per
-// step, or one fused launch per request), synchronise once, read each
-// request's diagnostics of the last step, retire the finished ones.  The
-// batch is rebuilt only when the resident set changes.
+// Each tick: set each resident request's ramp force for its own step count
+// and launch steps_per_tick steps for all of them (one persistent batch
+// kernel per step, or one fused launch per request); while the GPU runs,
+// admit queued requests in arrival order while the budget holds; then
+// synchronise once, read each stepped request's diagnostics of the last
+// step and retire the finished ones.  The batch is rebuilt only when the
+// resident set changes.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -78,11 +79,13 @@ struct pflb_server {
   pflb_batch *batch = nullptr;
   bool batch_dirty = true;
   size_t bytes_in_use = 0, peak_bytes = 0;
+  int64_t cells_in_use = 0;
   std::vector<double> latencies;
   bool any_submit = false;
   Clock::time_point t_first, t_last_done;
   double cell_updates = 0;
   int64_t ticks = 0, completed = 0, failed = 0, rejected = 0;
+  double admit_s = 0, wait_s = 0, retire_s = 0;
 };
 
 static pflb_status server_poison(pflb_server *s, const std::string &m) {
@@ -97,7 +100,7 @@ extern "C" pflb_status pflb_server_create(const pflb_server_config *cfg, void *c
   if (cfg->steps_per_tick < 1) return sfail(PFLB_ERR_ARG, "steps_per_tick must be >= 1");
   if (cfg->storage < PFLB_STORAGE_FP64 || cfg->storage > PFLB_STORAGE_BF16)
     return sfail(PFLB_ERR_ARG, "unknown storage");
-  if (cfg->max_active < 0 || cfg->hbm_budget_bytes == 0)
+  if (cfg->max_active < 0 || cfg->max_active_cells < 0 || cfg->hbm_budget_bytes == 0)
     return sfail(PFLB_ERR_ARG, "need a positive budget and max_active >= 0");
   pflb_server *s = new (std::nothrow) pflb_server();
   if (!s) return sfail(PFLB_ERR_OOM, "host allocation failed");
@@ -176,6 +179,7 @@ static void retire(pflb_server *s, Request *r, int state) {
   pflb_destroy(r->L);
   r->L = nullptr;
   s->bytes_in_use -= r->bytes;
+  s->cells_in_use -= (int64_t)r->nx * r->ny * r->nz;
   // the geometry copies are no longer needed
   std::vector<uint8_t>().swap(r->solid);
   std::vector<double>().swap(r->normal);
@@ -187,6 +191,10 @@ static pflb_status admit(pflb_server *s) {
     Request *r = s->queue.front();
     if (s->cfg.max_active > 0 && (int)s->active.size() >= s->cfg.max_active) break;
     if (s->bytes_in_use + r->bytes > s->cfg.hbm_budget_bytes) break;
+    const int64_t cells = (int64_t)r->nx * r->ny * r->nz;
+    if (s->cfg.max_active_cells > 0 && !s->active.empty() &&
+        s->cells_in_use + cells > s->cfg.max_active_cells)
+      break;
     s->queue.pop_front();
     const pflb_geometry g = r->geometry();
     pflb_status st = pflb_create(&g, &r->params, s->stream, &r->L);
@@ -208,6 +216,7 @@ static pflb_status admit(pflb_server *s) {
     r->res.queue_s = seconds(r->t_submit, r->t_admit);
     r->res.state = PFLB_REQ_RUNNING;
     s->bytes_in_use += r->bytes;
+    s->cells_in_use += cells;
     s->peak_bytes = std::max(s->peak_bytes, s->bytes_in_use);
     s->active.push_back(r);
     s->batch_dirty = true;
@@ -218,10 +227,11 @@ static pflb_status admit(pflb_server *s) {
 extern "C" pflb_status pflb_server_tick(pflb_server *s, int *n_active) {
   if (!s) return sfail(PFLB_ERR_ARG, "null server");
   if (s->poisoned) return sfail(PFLB_ERR_STATE, "server poisoned by an earlier error");
-  admit(s);
   const int n = s->cfg.steps_per_tick;
-  if (!s->active.empty()) {
-    for (Request *r : s->active) {
+  // 1. launch this tick's steps for the resident requests (asynchronous)
+  std::vector<Request *> stepped = s->active;
+  if (!stepped.empty()) {
+    for (Request *r : stepped) {
       const double F = r->beta_at(r->res.steps) * r->spec.p_ref / r->spec.length;
       const double f[3] = {F * r->spec.dir[0], F * r->spec.dir[1], F * r->spec.dir[2]};
       if (pflb_set_force(r->L, f) != PFLB_OK) return server_poison(s, "set_force failed");
@@ -231,7 +241,7 @@ extern "C" pflb_status pflb_server_tick(pflb_server *s, int *n_active) {
         pflb_batch_destroy(s->batch);
         s->batch = nullptr;
         std::vector<pflb_lattice *> ls;
-        for (Request *r : s->active) ls.push_back(r->L);
+        for (Request *r : stepped) ls.push_back(r->L);
         if (pflb_batch_create(ls.data(), (int)ls.size(), s->stream, &s->batch) != PFLB_OK)
           return server_poison(s, std::string("batch: ") + pflb_last_error());
         s->batch_dirty = false;
@@ -239,42 +249,56 @@ extern "C" pflb_status pflb_server_tick(pflb_server *s, int *n_active) {
       if (pflb_batch_step(s->batch, n, 1) != PFLB_OK)
         return server_poison(s, std::string("batch step: ") + pflb_last_error());
     } else {
-      for (Request *r : s->active)
+      for (Request *r : stepped)
         if (pflb_step_ex(r->L, n, 1) != PFLB_OK)
           return server_poison(s, std::string("step: ") + pflb_last_error());
     }
-    cudaError_t e = cudaStreamSynchronize(s->stream);
-    if (e != cudaSuccess) return server_poison(s, std::string("sync: ") + cudaGetErrorString(e));
-    std::vector<Request *> keep;
-    for (Request *r : s->active) {
-      pflb_diag_t d{};
-      const pflb_status st = pflb_last_diag(r->L, &d);
-      r->res.steps += n;
-      s->cell_updates += (double)r->nx * r->ny * r->nz * n;
-      r->res.beta = r->beta_at(r->res.steps - 1);
-      r->res.region_mass = d.region_mass;
-      r->res.mass = d.mass;
-      r->res.u_max = d.u_max;
-      if (st == PFLB_ERR_NAN || d.nonfinite > 0) {
-        retire(s, r, PFLB_REQ_FAILED);
-      } else if (st != PFLB_OK) {
-        return server_poison(s, std::string("diag: ") + pflb_last_error());
-      } else if (d.region_mass > r->spec.threshold || r->res.steps >= r->spec.max_steps) {
-        r->res.broke_through = d.region_mass > r->spec.threshold;
-        if (r->spec.keep_phi) {
-          r->phi.resize((size_t)r->nx * r->ny * r->nz);
-          if (pflb_read(r->L, PFLB_FIELD_PHI, r->phi.data()) != PFLB_OK)
-            return server_poison(s, std::string("read: ") + pflb_last_error());
-        }
-        retire(s, r, PFLB_REQ_DONE);
-      } else {
-        keep.push_back(r);
-      }
-    }
-    if (keep.size() != s->active.size()) s->batch_dirty = true;
-    s->active.swap(keep);
-    s->ticks++;
   }
+  // 2. admission while the GPU runs; new requests start at the next tick
+  const auto t0 = Clock::now();
+  admit(s);
+  const auto t1 = Clock::now();
+  // 3. wait, then check and retire the requests that were stepped
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return server_poison(s, std::string("sync: ") + cudaGetErrorString(e));
+  const auto t2 = Clock::now();
+  s->admit_s += seconds(t0, t1);
+  s->wait_s += seconds(t1, t2);
+  std::vector<Request *> keep;
+  bool changed = false;
+  for (Request *r : stepped) {
+    pflb_diag_t d{};
+    const pflb_status st = pflb_last_diag(r->L, &d);
+    r->res.steps += n;
+    s->cell_updates += (double)r->nx * r->ny * r->nz * n;
+    r->res.beta = r->beta_at(r->res.steps - 1);
+    r->res.region_mass = d.region_mass;
+    r->res.mass = d.mass;
+    r->res.u_max = d.u_max;
+    if (st == PFLB_ERR_NAN || d.nonfinite > 0) {
+      retire(s, r, PFLB_REQ_FAILED);
+      changed = true;
+    } else if (st != PFLB_OK) {
+      return server_poison(s, std::string("diag: ") + pflb_last_error());
+    } else if (d.region_mass > r->spec.threshold || r->res.steps >= r->spec.max_steps) {
+      r->res.broke_through = d.region_mass > r->spec.threshold;
+      if (r->spec.keep_phi) {
+        r->phi.resize((size_t)r->nx * r->ny * r->nz);
+        if (pflb_read(r->L, PFLB_FIELD_PHI, r->phi.data()) != PFLB_OK)
+          return server_poison(s, std::string("read: ") + pflb_last_error());
+      }
+      retire(s, r, PFLB_REQ_DONE);
+      changed = true;
+    } else {
+      keep.push_back(r);
+    }
+  }
+  // requests admitted in this tick follow the ones still running
+  for (size_t k = stepped.size(); k < s->active.size(); ++k) keep.push_back(s->active[k]);
+  if (changed) s->batch_dirty = true;
+  s->active.swap(keep);
+  if (!stepped.empty()) s->ticks++;
+  s->retire_s += seconds(t2, Clock::now());
   if (n_active) *n_active = (int)s->active.size();
   return PFLB_OK;
 }
@@ -328,6 +352,9 @@ extern "C" pflb_status pflb_server_stats_get(pflb_server *s, pflb_server_stats *
   st.bytes_in_use = s->bytes_in_use;
   st.peak_bytes = s->peak_bytes;
   st.ticks = s->ticks;
+  st.admit_s = s->admit_s;
+  st.wait_s = s->wait_s;
+  st.retire_s = s->retire_s;
   *out = st;
   return PFLB_OK;
 }

@@ -29,7 +29,8 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NAN"
 
 class ServerConfig(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("storage", C.c_int),
-                ("steps_per_tick", C.c_int), ("max_active", C.c_int), ("batched", C.c_int)]
+                ("steps_per_tick", C.c_int), ("max_active", C.c_int), ("batched", C.c_int),
+                ("max_active_cells", C.c_int64)]
 
 
 class SolveSpec(C.Structure):
@@ -55,7 +56,8 @@ class ServerStats(C.Structure):
                 ("p50_s", C.c_double), ("p99_s", C.c_double), ("mean_s", C.c_double),
                 ("max_s", C.c_double), ("makespan_s", C.c_double), ("solves_per_s", C.c_double),
                 ("cell_updates", C.c_double), ("bytes_in_use", C.c_size_t),
-                ("peak_bytes", C.c_size_t), ("ticks", C.c_int64)]
+                ("peak_bytes", C.c_size_t), ("ticks", C.c_int64), ("admit_s", C.c_double),
+                ("wait_s", C.c_double), ("retire_s", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -423,11 +425,11 @@ class Server:
     ``tick`` advances the resident requests; ``poll`` / ``stats`` report."""
 
     def __init__(self, hbm_budget_bytes=16 << 30, storage="fp32", steps_per_tick=250,
-                 max_active=0, batched=True, stream=None):
+                 max_active=0, batched=True, max_active_cells=0, stream=None):
         self._lib = load()
         self.storage = _STORAGE_NAMES[storage] if isinstance(storage, str) else int(storage)
         cfg = ServerConfig(int(hbm_budget_bytes), self.storage, int(steps_per_tick),
-                           int(max_active), 1 if batched else 0)
+                           int(max_active), 1 if batched else 0, int(max_active_cells))
         h = C.c_void_p()
         _check(self._lib.pflb_server_create(C.byref(cfg), C.c_void_p(_stream_handle(stream)),
                                             C.byref(h)))

@@ -137,9 +137,9 @@ def test_create_rejects_bad_geometry():
     # server: null and invalid arguments are rejected before any device call
     srv = C.c_void_p()
     assert lib.pflb_server_create(None, None, C.byref(srv)) == pflb.ERR_ARG
-    cfg = pflb.ServerConfig(1 << 30, pflb.STORAGE_FP32, 0, 0, 1)
+    cfg = pflb.ServerConfig(1 << 30, pflb.STORAGE_FP32, 0, 0, 1, 0)
     assert lib.pflb_server_create(C.byref(cfg), None, C.byref(srv)) == pflb.ERR_ARG
-    cfg = pflb.ServerConfig(0, pflb.STORAGE_FP32, 10, 0, 1)
+    cfg = pflb.ServerConfig(0, pflb.STORAGE_FP32, 10, 0, 1, 0)
     assert lib.pflb_server_create(C.byref(cfg), None, C.byref(srv)) == pflb.ERR_ARG
     t = C.c_int64()
     assert lib.pflb_server_submit(None, None, None, None, C.byref(t)) == pflb.ERR_ARG

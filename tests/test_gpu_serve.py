@@ -60,14 +60,16 @@ def test_alone_equals_mixed(storage):
              for r in reqs]
     budget = sorted(sizes)[-1] + sorted(sizes)[-2]
     queued, st2 = _serve(reqs, storage=storage, hbm_budget_bytes=budget)
-    assert st["completed"] == st2["completed"] == len(reqs)
+    cells = max(r["geometry"].N for r in reqs)
+    capped, st3 = _serve(reqs, storage=storage, max_active_cells=cells)
+    assert st["completed"] == st2["completed"] == st3["completed"] == len(reqs)
     assert st2["peak_bytes"] <= budget
-    for (ra, pa), (rm, pm), (rq, pq) in zip(alone, mixed, queued):
-        for res in (rm, rq):
+    for (ra, pa), (rm, pm), (rq, pq), (rc, pc) in zip(alone, mixed, queued, capped):
+        for res in (rm, rq, rc):
             assert res["state"] == pflb.REQ_DONE
             assert res["steps"] == ra["steps"] and res["beta"] == ra["beta"]
             assert res["broke_through"] == ra["broke_through"]
-        assert np.array_equal(pa, pm) and np.array_equal(pa, pq)
+        assert np.array_equal(pa, pm) and np.array_equal(pa, pq) and np.array_equal(pa, pc)
         assert np.isfinite(pa).all()
 
 
