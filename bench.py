@@ -227,6 +227,19 @@ ALGO_BYTES = {"fp32": ALGO_BYTES_FP32, "fp64": 2 * 19 * 2 * 8 + 1,
               "fp16": 2 * 19 * 2 * 2 + 2 * 2 + 1, "bf16": 2 * 19 * 2 * 2 + 2 * 2 + 1}
 
 
+def init_ranks():
+    """(world, rank) from the torchrun environment; joins the NCCL process
+    group when world > 1 and selects this rank's GPU."""
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl")
+    return world, rank
+
+
 def main_channels(args):
     """Many uneven lattices at once: the 64 droplet-in-square-channel
     lattices of synth.channel_batch_specs advanced by one persistent kernel
@@ -234,14 +247,16 @@ def main_channels(args):
     replayed from a captured CUDA graph.  Also timed: the same lattices
     stepped one launch each per step (the per-lattice loop)."""
     import torch
-    from paper_2512_01032_gb300 import pflb
+    from paper_2512_01032_gb300 import pflb, shard
+    world, rank = init_ranks()
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
-    torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(device=dev)
     storage = args.storage
     specs = synth.channel_batch_specs(args.count)
+    # each rank advances its own share of the lattices (no data exchange)
+    mine = shard.my_items([sp["nx"] * sp["ny"] * sp["nz"] for sp in specs], rank, world)
     lats, fluid, cells = [], 0, 0
-    for sp in specs:
+    for sp in (specs[i] for i in mine):
         g, p, init = synth.channel_lattice(sp)
         L = pflb.Lattice(g.nx, g.ny, g.nz, solid=g.solid, wall_normal=g.normals(),
                          theta_cells=g.theta(), stream=stream, storage=storage, **p)
@@ -262,7 +277,7 @@ def main_channels(args):
             L.step(1)
     b.record(stream)
     b.synchronize()
-    loop_ms = a.elapsed_time(b)
+    loop_ms, = shard.reduce_max([a.elapsed_time(b)], device=dev)
 
     B = pflb.Batch(lats, stream=stream)
     best = B.tune(trial_steps=4)
@@ -277,15 +292,17 @@ def main_channels(args):
     b.record(stream)
     b.synchronize()
     clocks = clk.stop()
-    ms = a.elapsed_time(b)
+    ms, = shard.reduce_max([a.elapsed_time(b)], device=dev)
     nonfinite = sum(L.last_diag(allow_nan=True)["nonfinite"] for L in lats)
+    fluid, cells, nonfinite = (int(v) for v in shard.reduce_sum([fluid, cells, nonfinite],
+                                                                 device=dev))
     ms_step = ms / args.steps
     value = fluid * args.steps / (ms * 1e-3) / 1e6
     peak, peak_kind = hbm_peak()
     achieved = fluid * ALGO_BYTES[storage] / (ms_step * 1e-3) / 1e9
     line = {"metric": "batched AC+NS LB step MLUPS (many lattices)", "value": value,
-            "unit": "MLUPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f32" if storage != "fp64" else "f64",
             "data": "synthetic",
             "config": {"workload": f"{args.count} droplet-in-square-channel lattices "
@@ -303,7 +320,8 @@ def main_channels(args):
             "per_lattice_loop": {"value": fluid * args.steps / (loop_ms * 1e-3) / 1e6,
                                  "unit": "MLUPS", "launches_per_step": len(lats)},
             "gpu_launches": 2 * args.steps, "clocks": clocks, "nonfinite": nonfinite}
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     B.close()
     for L in lats:
         L.close()
@@ -336,11 +354,15 @@ def main_serve(args):
     batching (one persistent batch kernel per step over all resident
     requests, admission by HBM budget) against the plain server (one request
     at a time, FP32, one fused launch per step) on the same trace."""
+    import math
     import torch
-    from paper_2512_01032_gb300 import pflb
+    from paper_2512_01032_gb300 import pflb, shard
+    world, rank = init_ranks()
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
-    torch.cuda.set_device(dev)
     trace = synth.serving_trace(args.count)
+    # each rank serves its own share of the requests, keeping arrival times
+    mine = shard.my_items([4 * r["w"] * (r["w"] + 2) ** 2 for r in trace], rank, world)
+    trace = [trace[i] for i in mine]
     prepared = []
     for req in trace:
         r = synth.constriction_request(req, ramp_every=args.ramp_every,
@@ -366,23 +388,32 @@ def main_serve(args):
         clocks = clk.stop()
         st = S.stats()
         res = [S.poll(t) for t in tickets]
-        out[name] = dict(solves_per_s=st["solves_per_s"], p50_s=st["p50_s"], p99_s=st["p99_s"],
-                         mean_s=st["mean_s"], makespan_s=st["makespan_s"],
-                         completed=st["completed"], failed=st["failed"],
-                         rejected=st["rejected"], peak_gb=st["peak_bytes"] / 2 ** 30,
-                         mlups=st["cell_updates"] / max(st["makespan_s"], 1e-9) / 1e6,
-                         broke_through=sum(r["broke_through"] for r in res),
-                         host_s={k: st[k] for k in ("admit_s", "wait_s", "retire_s")},
-                         wall_s=wall,
-                         steps=[r["steps"] for r in res], clocks=clocks)
         S.close()
+        # over ranks: latencies and step counts gathered, makespan max, counters summed
+        lat = sorted(x for r in shard.gather([q["latency_s"] for q in res
+                                              if q["state"] == pflb.REQ_DONE]) for x in r)
+        steps = [x for r in shard.gather([q["steps"] for q in res]) for x in r]
+        makespan, = shard.reduce_max([st["makespan_s"]], device=dev)
+        tot = shard.reduce_sum([st["completed"], st["failed"], st["rejected"],
+                                st["cell_updates"],
+                                sum(q["broke_through"] for q in res)], device=dev)
+        pct = (lambda q: lat[min(len(lat), max(1, math.ceil(q * len(lat)))) - 1]
+               if lat else 0.0)
+        out[name] = dict(solves_per_s=tot[0] / max(makespan, 1e-9), p50_s=pct(0.5),
+                         p99_s=pct(0.99), mean_s=sum(lat) / max(len(lat), 1),
+                         makespan_s=makespan, completed=int(tot[0]), failed=int(tot[1]),
+                         rejected=int(tot[2]), peak_gb=st["peak_bytes"] / 2 ** 30,
+                         mlups=tot[3] / max(makespan, 1e-9) / 1e6,
+                         broke_through=int(tot[4]),
+                         host_s={k: st[k] for k in ("admit_s", "wait_s", "retire_s")},
+                         wall_s=wall, steps=steps, clocks=clocks)
     same = out["batched"]["steps"] == out["plain"]["steps"]
     for v in out.values():
         v.pop("steps")
     extra = {k: v for k, v in out.items() if k not in ("batched", "plain")}
     b = out["batched"]
     line = {"metric": "served critical-pressure solves/s", "value": b["solves_per_s"],
-            "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
+            "unit": "solves/s", "n_gpus": world, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "p50_s": b["p50_s"], "p99_s": b["p99_s"],
             "config": {"workload": f"first {args.count} requests of the seeded Poisson trace "
@@ -394,7 +425,8 @@ def main_serve(args):
                        "steps_per_tick": args.ramp_every // 2},
             "batched": out["batched"], "plain_sequential_fp32": out["plain"], **extra,
             "same_step_counts": same}
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     return 0
 
 
