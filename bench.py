@@ -135,7 +135,7 @@ def config_of(g, fluid):
     return {"workload": f"FP32 sessile droplet on a curved wall, {g.nx}x{g.ny}x{g.nz} D3Q19, "
                         f"solid sphere R=30, drop R=20, theta={THETA:g} deg, density ratio 1000",
             "lattice": [g.nx, g.ny, g.nz], "fluid_cells": int(fluid), "storage": "fp32",
-            "kernel": "fused z-marching, 32x4 tiles, 16 planes per block (one launch per step, diagnostics on)",
+            "kernel": "fused z-marching (one launch per step, diagnostics on)",
             "l2": "inputs larger than L2 (no flush)"}
 
 
@@ -562,7 +562,8 @@ def main(argv=None):
         line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32", "data": "synthetic", "config": config_of(g, fluid),
+                "dtype": "f32", "data": "synthetic",
+                "config": dict(config_of(g, fluid), launch=L.get_kernel()),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": args.steps, "clocks": clocks,
                 "diag_last": {"mass": d["mass"], "dp": d["dp"], "u_max": d["u_max"],

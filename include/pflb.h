@@ -168,8 +168,14 @@ pflb_status pflb_set_region(pflb_lattice *L, const int box[6]);
 /* Choose the step kernel and its launch shape: tile bx * by threads
  * (bx * by <= 256, 2 (bx+2) + 2 by <= bx * by) marching lz planes in z
  * (the TMA kernel always uses 32 x 8 and takes only lz).  Defaults:
- * 32 x 4 x 16.  Zeros keep the current values. */
+ * 32 x 4 and automatic lz.  Zeros keep the current values; lz = -1 returns
+ * to the automatic choice, which minimises the launch's rounds of resident
+ * blocks times the planes per block (plus its halo cost) over lz in
+ * [2, 32], from the device's SM count and the kernel's occupancy. */
 pflb_status pflb_set_kernel(pflb_lattice *L, int kind, int bx, int by, int lz);
+
+/* The launch shape in effect: out = {kind, bx, by, lz}. */
+pflb_status pflb_get_kernel(const pflb_lattice *L, int out[4]);
 
 /* Advance nsteps time steps (asynchronous on the lattice stream). */
 pflb_status pflb_step(pflb_lattice *L, int64_t nsteps);

@@ -116,6 +116,15 @@ size_t compute_bytes(int storage) { return storage == PFLB_STORAGE_FP64 ? 8 : 4;
 // h slots per cell: the 16-bit formats keep the rest population's remainder.
 size_t h_slots_of(int storage) { return storage_bytes(storage) == 2 ? 20 : 19; }
 
+// Planes per block in effect: the requested value, else the automatic one.
+int resolve_lz(Lattice *L) {
+  if (L->lz_req > 0) return L->lz_req;
+  return dispatch_storage(L->p.storage, [&](auto *s_, auto *r_) {
+    PFLB_SR_TYPES
+    return pflb::auto_lz<S, R>(*L);
+  });
+}
+
 pflb_status check_lattice(const pflb_lattice *L) {
   if (!L) return fail(PFLB_ERR_ARG, "null lattice");
   if (L->poisoned) return fail(PFLB_ERR_STATE, "lattice poisoned by an earlier CUDA error");
@@ -368,7 +377,7 @@ pflb_status pflb_create(const pflb_geometry *geom, const pflb_params *params, vo
   L->stream = (cudaStream_t)cuda_stream;
   L->elem = storage_bytes(L->p.storage);
   L->reg[1] = L->nx; L->reg[3] = L->ny; L->reg[5] = L->nz;
-  L->lz = L->nz < 16 ? L->nz : 16;
+  L->lz = L->nz < 16 ? L->nz : 16;  // replaced by the automatic choice once created
 
   HostGeom hg;
   try {
@@ -439,6 +448,7 @@ pflb_status pflb_create(const pflb_geometry *geom, const pflb_params *params, vo
     return fail(PFLB_ERR_CUDA, std::string("upload failed: ") + cudaGetErrorString(e));
   }
   make_tmaps(L);
+  L->lz = resolve_lz(L);
   *out = L;
   return PFLB_OK;
 }
@@ -538,7 +548,8 @@ pflb_status pflb_set_kernel(pflb_lattice *L, int kind, int bx, int by, int lz) {
   if (s != PFLB_OK) return s;
   if (kind != PFLB_KERNEL_FUSED && kind != PFLB_KERNEL_TWOPASS && kind != PFLB_KERNEL_FUSED_TMA)
     return fail(PFLB_ERR_ARG, "unknown kernel");
-  const int nbx = bx > 0 ? bx : L->bx, nby = by > 0 ? by : L->by, nlz = lz > 0 ? lz : L->lz;
+  if (lz < -1) return fail(PFLB_ERR_ARG, "lz must be > 0, 0 (keep) or -1 (automatic)");
+  const int nbx = bx > 0 ? bx : L->bx, nby = by > 0 ? by : L->by;
   if (nbx * nby > 256 || nbx < 1 || nby < 1)
     return fail(PFLB_ERR_ARG, "bx*by must be in [1, 256]");
   if (2 * (nbx + 2) + 2 * nby > nbx * nby)
@@ -546,7 +557,22 @@ pflb_status pflb_set_kernel(pflb_lattice *L, int kind, int bx, int by, int lz) {
   L->kernel = kind;
   L->bx = nbx;
   L->by = nby;
-  L->lz = nlz;
+  if (lz > 0) L->lz_req = lz;
+  if (lz == -1) L->lz_req = 0;
+  L->lz = resolve_lz(L);
+  return PFLB_OK;
+}
+
+pflb_status pflb_get_kernel(const pflb_lattice *L, int out[4]) {
+  pflb_status s = check_lattice(L);
+  if (s != PFLB_OK) return s;
+  if (!out) return fail(PFLB_ERR_ARG, "null output");
+  const bool tma = L->kernel == PFLB_KERNEL_FUSED_TMA && L->p.storage == PFLB_STORAGE_FP32 &&
+                   L->tma_ok;
+  out[0] = L->kernel;
+  out[1] = tma ? 32 : L->bx;
+  out[2] = tma ? 8 : L->by;
+  out[3] = L->lz;
   return PFLB_OK;
 }
 

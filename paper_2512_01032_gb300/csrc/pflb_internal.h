@@ -40,7 +40,8 @@ struct Lattice {
   int64_t last_diag_step = -1;
   int diag_every = 0;         // pflb_step accumulates diagnostics every k-th step
   int kernel = PFLB_KERNEL_FUSED;
-  int bx = 32, by = 4, lz = 16;
+  int bx = 32, by = 4, lz = 16;   // lz: planes per block in effect
+  int lz_req = 0;                  // requested planes per block, 0 = automatic
   int reg[6] = {0, 0, 0, 0, 0, 0};
   bool poisoned = false;
   int64_t dev_bytes = 0;
@@ -68,6 +69,7 @@ template <class S, class R> cudaError_t launch_step(Lattice &L, bool diag);
 template <class S, class R> cudaError_t launch_macro(Lattice &L, bool fields);
 template <class S, class R> cudaError_t set_model(Lattice &L);
 template <class S, class R> int max_block_threads();
+template <class S, class R> int auto_lz(const Lattice &L);
 // Batch: size of one descriptor, host-side descriptor build (2 per lattice,
 // diagnostics pointers for the next diagnostic launch), one step launch,
 // and the occupancy-limited blocks per SM of the batch kernel.

@@ -101,7 +101,7 @@ inline bool async_eligible(const Lattice &L) {
 }
 
 template <bool ODD, bool DIAG>
-static cudaError_t launch_async_t(Lattice &L, Args<float, float> &a) {
+static cudaError_t async_attrs() {
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_fused_async<ODD, DIAG>,
@@ -112,6 +112,13 @@ static cudaError_t launch_async_t(Lattice &L, Args<float, float> &a) {
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
+  return cudaSuccess;
+}
+
+template <bool ODD, bool DIAG>
+static cudaError_t launch_async_t(Lattice &L, Args<float, float> &a) {
+  cudaError_t e0 = async_attrs<ODD, DIAG>();
+  if (e0 != cudaSuccess) return e0;
   dim3 grid((L.nx + AB_X - 1) / AB_X, (L.ny + AB_Y - 1) / AB_Y, (L.nz + L.lz - 1) / L.lz);
   k_fused_async<ODD, DIAG><<<grid, AB_X * AB_Y, AB_SMEM, L.stream>>>(a, L.tmap[L.step & 1], L.err);
   return cudaGetLastError();
@@ -138,6 +145,54 @@ static cudaError_t launch_cell_t(Lattice &L, Args<S, R> &a) {
   if (e != cudaSuccess) return e;
   k_cell<S, R, ODD, MODE, DIAG><<<(unsigned)B, T, 0, L.stream>>>(a);
   return cudaGetLastError();
+}
+
+// Planes per block for the fused kernels.  Blocks all do the same work, so
+// a launch takes ceil(blocks / resident slots) rounds of one block's time;
+// a block of lz planes also recomputes phi on two halo planes (about 0.3 of
+// a plane's cost each).  Chooses lz in [2, 32] minimising
+// rounds x (lz + 0.6), e.g. 7 for 128^3 with 32 x 4 tiles on 152 SMs x 4
+// blocks (19 chunks x 128 columns = 4 full rounds).
+template <class S, class R>
+int auto_lz(const Lattice &L) {
+  int dev = 0, nsm = 0, per = 0;
+  bool tma = false;
+  if constexpr (std::is_same<S, float>::value && std::is_same<R, float>::value)
+    tma = async_eligible(L);
+  const int bx = tma ? AB_X : L.bx, by = tma ? AB_Y : L.by;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) {
+    if (tma) {
+      if constexpr (std::is_same<S, float>::value && std::is_same<R, float>::value) {
+        e = async_attrs<false, true>();
+        if (e == cudaSuccess)
+          e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused_async<false, true>,
+                                                            bx * by, AB_SMEM);
+      }
+    } else {
+      const size_t smem = 3 * (size_t)(bx + 2) * (by + 2) * sizeof(R);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused<S, R, false, true>,
+                                                        bx * by, smem);
+    }
+  }
+  if (e != cudaSuccess || nsm < 1 || per < 1) {
+    cudaGetLastError();
+    return L.nz < 16 ? L.nz : 16;
+  }
+  const long long slots = (long long)nsm * per;
+  const long long cols = (long long)((L.nx + bx - 1) / bx) * ((L.ny + by - 1) / by);
+  int best = L.nz < 16 ? L.nz : 16;
+  double best_cost = 1e300;
+  for (int lz = (L.nz < 32 ? L.nz : 32); lz >= 2; --lz) {
+    const long long blocks = cols * ((L.nz + lz - 1) / lz);
+    const double cost = (double)((blocks + slots - 1) / slots) * (lz + 0.6);
+    if (cost < best_cost - 1e-9) {
+      best_cost = cost;
+      best = lz;
+    }
+  }
+  return best;
 }
 
 template <class S, class R>
@@ -239,6 +294,7 @@ int batch_max_blocks_per_sm(int bx, int by) {
   template cudaError_t launch_step<S, R>(Lattice &, bool);                       \
   template cudaError_t launch_macro<S, R>(Lattice &, bool);                      \
   template cudaError_t set_model<S, R>(Lattice &);                               \
-  template int max_block_threads<S, R>();
+  template int max_block_threads<S, R>();                                        \
+  template int auto_lz<S, R>(const Lattice &);
 
 }  // namespace pflb

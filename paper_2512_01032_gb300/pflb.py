@@ -138,6 +138,8 @@ def load(build_if_missing: bool = True):
     lib.pflb_set_region.restype = st
     lib.pflb_set_kernel.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]
     lib.pflb_set_kernel.restype = st
+    lib.pflb_get_kernel.argtypes = [C.c_void_p, _P(C.c_int)]
+    lib.pflb_get_kernel.restype = st
     lib.pflb_step.argtypes = [C.c_void_p, C.c_int64]
     lib.pflb_step.restype = st
     lib.pflb_step_diag.argtypes = [C.c_void_p, C.c_int64, _P(Diag)]
@@ -331,6 +333,11 @@ class Lattice:
 
     def set_kernel(self, kind=KERNEL_FUSED, bx=0, by=0, lz=0):
         _check(self._lib.pflb_set_kernel(self._h, int(kind), int(bx), int(by), int(lz)))
+
+    def get_kernel(self) -> dict:
+        out = (C.c_int * 4)()
+        _check(self._lib.pflb_get_kernel(self._h, out))
+        return dict(kind=out[0], bx=out[1], by=out[2], lz=out[3])
 
     def step(self, n=1):
         _check(self._lib.pflb_step(self._h, int(n)))

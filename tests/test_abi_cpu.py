@@ -150,6 +150,7 @@ def test_create_rejects_bad_geometry():
     assert lib.pflb_server_stats_get(None, C.byref(st)) == pflb.ERR_ARG
     lib.pflb_server_destroy(None)
     assert lib.pflb_step_ex(None, 1, 0) == pflb.ERR_ARG
+    assert lib.pflb_get_kernel(None, (C.c_int * 4)()) == pflb.ERR_ARG
 
 
 def test_estimate_bytes_counts_wall_nodes():
