@@ -166,7 +166,8 @@ pflb_status pflb_set_force(pflb_lattice *L, const double Fex[3]);
 pflb_status pflb_set_region(pflb_lattice *L, const int box[6]);
 
 /* Choose the step kernel and its launch shape: tile bx * by threads
- * (bx * by <= 256, 2 (bx+2) + 2 by <= bx * by) marching lz planes in z
+ * (bx * by a multiple of 32 up to 256, 2 (bx+2) + 2 by <= bx * by; whole
+ * warps, for the warp reductions of the diagnostics) marching lz planes in z
  * (the TMA kernel always uses 32 x 8 and takes only lz).  Defaults:
  * 32 x 4 and automatic lz.  Zeros keep the current values; lz = -1 returns
  * to the automatic choice, which minimises the launch's rounds of resident

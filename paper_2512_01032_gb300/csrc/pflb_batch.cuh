@@ -17,9 +17,11 @@ namespace pflb {
 
 __host__ __device__ constexpr size_t batch_align16(size_t b) { return (b + 15) & ~size_t(15); }
 
+// phi ring, per-thread diagnostic slots (diagnostic launches only), step
+// descriptor
 template <class S, class R>
-__host__ __device__ constexpr size_t batch_smem(int BX, int BY) {
-  return batch_align16(3 * (size_t)(BX + 2) * (BY + 2) * sizeof(R)) + sizeof(Args<S, R>);
+__host__ __device__ constexpr size_t batch_smem(int BX, int BY, bool diag) {
+  return fused_smem_bytes<R>(BX, BY, diag) + sizeof(Args<S, R>);
 }
 
 template <class S, class R, bool DIAG>
@@ -29,8 +31,8 @@ __global__ void __launch_bounds__(256, PFLB_MIN_BLOCKS)
             int BY, int LZ) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R *sphi = reinterpret_cast<R *>(smem_raw);
-  Args<S, R> *sa = reinterpret_cast<Args<S, R> *>(
-      smem_raw + batch_align16(3 * (size_t)(BX + 2) * (BY + 2) * sizeof(R)));
+  R *tacc = reinterpret_cast<R *>(smem_raw + fused_phi_bytes<R>(BX, BY));
+  Args<S, R> *sa = reinterpret_cast<Args<S, R> *>(smem_raw + fused_smem_bytes<R>(BX, BY, DIAG));
   __shared__ R wacc[DIAG_MAX_WARPS][32];
   __shared__ int s_item;
   const int tid = threadIdx.x;
@@ -45,17 +47,17 @@ __global__ void __launch_bounds__(256, PFLB_MIN_BLOCKS)
     const int *src = reinterpret_cast<const int *>(descs + 2 * it.x + p);
     int *dst = reinterpret_cast<int *>(sa);
     for (int k = tid; k < (int)(sizeof(Args<S, R>) / 4); k += blockDim.x) dst[k] = src[k];
-    if (DIAG) diag_block_zero(wacc);
+    if (DIAG) diag_thread_zero(tacc);
     __syncthreads();
     const Args<S, R> &a = *sa;
     if (DIAG && it.y == 0 && it.z == 0 && it.w == 0 && tid < 32 && a.diag_zero)
       a.diag_zero[tid] = 0.0;
     const int ze = min(it.w + LZ, a.nz);
     if (p)
-      march_tile<S, R, true, DIAG>(a, it.y, it.z, it.w, ze, BX, BY, sphi, wacc);
+      march_tile<S, R, true, DIAG>(a, it.y, it.z, it.w, ze, BX, BY, sphi, tacc);
     else
-      march_tile<S, R, false, DIAG>(a, it.y, it.z, it.w, ze, BX, BY, sphi, wacc);
-    if (DIAG) diag_block_flush(a.diag, wacc);
+      march_tile<S, R, false, DIAG>(a, it.y, it.z, it.w, ze, BX, BY, sphi, tacc);
+    if (DIAG) diag_thread_flush(a.diag, tacc, wacc);
     __syncthreads();  // shared descriptor and phi ring are reused by the next item
   }
 }

@@ -550,8 +550,8 @@ pflb_status pflb_set_kernel(pflb_lattice *L, int kind, int bx, int by, int lz) {
     return fail(PFLB_ERR_ARG, "unknown kernel");
   if (lz < -1) return fail(PFLB_ERR_ARG, "lz must be > 0, 0 (keep) or -1 (automatic)");
   const int nbx = bx > 0 ? bx : L->bx, nby = by > 0 ? by : L->by;
-  if (nbx * nby > 256 || nbx < 1 || nby < 1)
-    return fail(PFLB_ERR_ARG, "bx*by must be in [1, 256]");
+  if (nbx * nby > 256 || nbx < 1 || nby < 1 || (nbx * nby) % 32)
+    return fail(PFLB_ERR_ARG, "bx*by must be a multiple of 32 in [32, 256]");
   if (2 * (nbx + 2) + 2 * nby > nbx * nby)
     return fail(PFLB_ERR_ARG, "tile too thin: halo ring larger than the block");
   L->kernel = kind;
@@ -893,8 +893,10 @@ extern "C" pflb_status pflb_batch_set_launch(pflb_batch *b, int bx, int by, int 
   if (b->poisoned) return fail(PFLB_ERR_STATE, "batch poisoned by an earlier CUDA error");
   const int nbx = bx > 0 ? bx : b->dev.bx, nby = by > 0 ? by : b->dev.by;
   const int nlz = lz > 0 ? lz : b->dev.lz;
-  if (nbx * nby > 256 || 2 * (nbx + 2) + 2 * nby > nbx * nby || blocks_per_sm < 0)
-    return fail(PFLB_ERR_ARG, "bad launch shape");
+  if (nbx < 1 || nby < 1 || nbx * nby > 256 || (nbx * nby) % 32 ||
+      2 * (nbx + 2) + 2 * nby > nbx * nby || blocks_per_sm < 0)
+    return fail(PFLB_ERR_ARG, "bad launch shape (bx*by a multiple of 32 in [32, 256], halo "
+                              "ring no larger than the block)");
   b->dev.bx = nbx;
   b->dev.by = nby;
   b->dev.lz = nlz;

@@ -317,6 +317,53 @@ __device__ __forceinline__ void diag_block_flush(double *diag, R (*wacc)[32]) {
   }
 }
 
+// Per-thread diagnostic slots in shared memory, laid out [quantity][thread]:
+// each fluid cell adds its contributions to its own thread's slots (no
+// cross-lane work per plane), and the block reduces the slots once, at the
+// end of its tile column, through the per-warp slots above.
+template <class R>
+__host__ __device__ constexpr size_t diag_thread_bytes(int threads) {
+  return (size_t)D_COUNT * threads * sizeof(R);
+}
+
+template <class R>
+__device__ __forceinline__ void diag_thread_zero(R *tacc) {
+  const int nt = blockDim.x, t = threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < D_COUNT; ++k) tacc[k * nt + t] = R(0);
+}
+
+template <class R>
+__device__ __forceinline__ void diag_thread_add(R *tacc, const DiagAcc<R> &d) {
+  const int nt = blockDim.x, t = threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < D_CLN; ++k) tacc[k * nt + t] += d.v[k];
+  if (d.v[D_CLN] != R(0)) {  // contact-line band cells (rare)
+#pragma unroll
+    for (int k = D_CLN; k <= D_CLZZ; ++k) tacc[k * nt + t] += d.v[k];
+  }
+#pragma unroll
+  for (int k = D_KIN; k < D_UMAX; ++k) tacc[k * nt + t] += d.v[k];
+  R &um = tacc[D_UMAX * nt + t];
+  um = um > d.umax ? um : d.umax;
+}
+
+// Block reduction of the per-thread slots into the device accumulator
+// (called by every thread of the block, after the last diag_thread_add).
+template <class R>
+__device__ __forceinline__ void diag_thread_flush(double *diag, const R *tacc,
+                                                  R (*wacc)[32]) {
+  const int nt = blockDim.x, t = threadIdx.x;
+  diag_block_zero(wacc);
+  __syncthreads();
+  DiagAcc<R> d;
+#pragma unroll
+  for (int k = 0; k < D_UMAX; ++k) d.v[k] = tacc[k * nt + t];
+  d.umax = tacc[D_UMAX * nt + t];
+  diag_warp_add(wacc[t >> 5], d);
+  diag_block_flush(diag, wacc);
+}
+
 // phi of one cell from the h buffer being read (0 for solid cells).
 template <class S, class R>
 __device__ __forceinline__ R cell_phi(const Args<S, R> &a, int c) {
@@ -391,11 +438,11 @@ __global__ void __launch_bounds__(256) k_cell(const __grid_constant__ Args<S, R>
 // one-cell ring is kept in shared memory; each plane's phi is recomputed
 // from the h populations (own cells and ring cells), so no phi field is
 // stored in HBM.  march_tile does one tile column [zb, ze) of lattice a;
-// sphi holds 3 (BX+2)(BY+2) values, wacc the per-warp diagnostic slots
-// (zeroed by the caller; the first use follows a barrier).
+// sphi holds 3 (BX+2)(BY+2) values, tacc the per-thread diagnostic slots
+// (zeroed by the caller, each thread its own).
 template <class S, class R, bool ODD, bool DIAG>
 __device__ __forceinline__ void march_tile(const Args<S, R> &a, int x0, int y0, int zb, int ze,
-                                           int BX, int BY, R *sphi, R (*wacc)[32]) {
+                                           int BX, int BY, R *sphi, R *tacc) {
   const int PW = BX + 2, PS = (BX + 2) * (BY + 2);
   const int tid = threadIdx.x;
   const int tx = tid % BX, ty = tid / BX;
@@ -446,11 +493,22 @@ __device__ __forceinline__ void march_tile(const Args<S, R> &a, int x0, int y0, 
           val[i] = pl[o + cy_of(i) * PW + cx_of(i)];
         }
         update_cell<S, R, ODD, MODE_STEP, DIAG>(a, gx, gy, z, c, f, h, phi, val, acc);
+        if (DIAG) diag_thread_add(tacc, acc);
       }
     }
-    if (DIAG && active) diag_warp_add(wacc[tid >> 5], acc);
     __syncthreads();
   }
+}
+
+// Dynamic shared memory of the fused kernel: the 3-plane phi ring, then
+// (with diagnostics) the per-thread diagnostic slots.
+template <class R>
+__host__ __device__ constexpr size_t fused_phi_bytes(int BX, int BY) {
+  return (3 * (size_t)(BX + 2) * (BY + 2) * sizeof(R) + 15) & ~size_t(15);
+}
+template <class R>
+__host__ __device__ constexpr size_t fused_smem_bytes(int BX, int BY, bool diag) {
+  return fused_phi_bytes<R>(BX, BY) + (diag ? diag_thread_bytes<R>(BX * BY) : 0);
 }
 
 template <class S, class R, bool ODD, bool DIAG>
@@ -458,13 +516,14 @@ __global__ void __launch_bounds__(256, PFLB_MIN_BLOCKS)
     k_fused(const __grid_constant__ Args<S, R> a, int BX, int BY) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R *sphi = reinterpret_cast<R *>(smem_raw);
+  R *tacc = reinterpret_cast<R *>(smem_raw + fused_phi_bytes<R>(BX, BY));
   zero_next_diag(a);
   __shared__ R wacc[DIAG_MAX_WARPS][32];
-  if (DIAG) diag_block_zero(wacc);
+  if (DIAG) diag_thread_zero(tacc);
   const int zb = blockIdx.z * a.lz;
   march_tile<S, R, ODD, DIAG>(a, blockIdx.x * BX, blockIdx.y * BY, zb, min(zb + a.lz, a.nz), BX,
-                              BY, sphi, wacc);
-  if (DIAG) diag_block_flush(a.diag, wacc);
+                              BY, sphi, tacc);
+  if (DIAG) diag_thread_flush(a.diag, tacc, wacc);
 }
 
 // ------------------------------------------------------------ init

@@ -131,7 +131,7 @@ static cudaError_t launch_fused_t(Lattice &L, Args<S, R> &a) {
   }
   const int bx = L.bx, by = L.by;
   dim3 grid((L.nx + bx - 1) / bx, (L.ny + by - 1) / by, (L.nz + L.lz - 1) / L.lz);
-  const size_t smem = 3 * (size_t)(bx + 2) * (by + 2) * sizeof(R);
+  const size_t smem = fused_smem_bytes<R>(bx, by, DIAG);
   k_fused<S, R, ODD, DIAG><<<grid, bx * by, smem, L.stream>>>(a, bx, by);
   return cudaGetLastError();
 }
@@ -171,9 +171,9 @@ int auto_lz(const Lattice &L) {
                                                             bx * by, AB_SMEM);
       }
     } else {
-      const size_t smem = 3 * (size_t)(bx + 2) * (by + 2) * sizeof(R);
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused<S, R, false, true>,
-                                                        bx * by, smem);
+                                                        bx * by,
+                                                        fused_smem_bytes<R>(bx, by, true));
     }
   }
   if (e != cudaSuccess || nsm < 1 || per < 1) {
@@ -257,7 +257,7 @@ template <class S, class R>
 cudaError_t batch_launch_step(const BatchDev &b, bool diag) {
   cudaError_t e = cudaMemsetAsync(b.counter, 0, sizeof(int), b.stream);
   if (e != cudaSuccess) return e;
-  const size_t smem = batch_smem<S, R>(b.bx, b.by);
+  const size_t smem = batch_smem<S, R>(b.bx, b.by, diag);
   const Args<S, R> *d = (const Args<S, R> *)b.descs;
   const int4 *it = (const int4 *)b.items;
   if (diag)
@@ -278,7 +278,7 @@ template <class S, class R>
 int batch_max_blocks_per_sm(int bx, int by) {
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<S, R, true>, bx * by,
-                                                    batch_smem<S, R>(bx, by)) != cudaSuccess) {
+                                                    batch_smem<S, R>(bx, by, true)) != cudaSuccess) {
     cudaGetLastError();
     return 1;
   }
