@@ -226,6 +226,23 @@ def channel_batch_specs(count=64, seed=2512010320):
     return out
 
 
+def static_slug(theta_deg, H=32, length=64, nx=192, nz=4):
+    """Liquid slug at rest between two flat plates (the gap is H fluid cells:
+    solid rows y = 0 and y = H + 1, periodic in x and z): liquid for
+    |x - nx/2 + 1/2| < length/2 with flat initial menisci; theta on both
+    plates, density ratio 1000, sigma = 0.01, W = 4, tau = 0.8, M = 0.02,
+    optimised model (tanh F, free-slip band, ghost blend 0.95: the flat
+    initial menisci are far from the wetting angle, and without the blend
+    the jump at 160 degrees drives the light phase unstable within 40 steps)."""
+    ny = H + 2
+    shapes = [Plane((0, 0.5, 0), (0, 1, 0)), Plane((0, ny - 1.5, 0), (0, -1, 0))]
+    g = Geometry(nx, ny, nz, shapes, theta_deg=theta_deg)
+    p = dict(sigma=0.01, W=4.0, M=0.02, rho_H=1.0, rho_L=1e-3, nu_H=0.1, nu_L=0.1,
+             theta_deg=theta_deg, F_mode=1, mobility_corr=1, free_slip=1, blend=0.95)
+    init = dict(shape=2, center=(nx / 2.0 - 0.5, 0.0, 0.0), R=length / 2.0, normal=(1.0, 0.0, 0.0))
+    return g, p, init
+
+
 def channel_lattice(spec: dict):
     """(geometry, params, init) of one channel_batch_specs entry: square duct
     along x, droplet at x = Nx/4 on the axis, carrier driven by a uniform body

@@ -106,3 +106,38 @@ def test_lucas_washburn_filling():
     assert all(0.65 < q < 1.0 for q in ratios), ratios
     assert np.mean(ratios[-10:]) > np.mean(ratios[:10])
     assert 80.0 < zs[-1] < 120.0
+
+
+@pytest.mark.parametrize("theta", [20.0, 40.0, 60.0, 90.0, 120.0, 140.0, 160.0])
+def test_static_slug_between_plates(theta):
+    """Liquid slug at rest between flat plates 32 cells apart (192 x 34 x 4,
+    periodic in x and z): after 20000 steps each meniscus is a circular arc
+    meeting the plates at the input angle (circle fit to the phi = 0.5
+    contour, within 2 degrees; flat at 90 degrees), the pressure jump has
+    the sign and, within 10 %, the size of -2 sigma cos(theta) / H (it
+    settles about 6 % below it, as the Laplace jump of large drops does),
+    and the spurious currents stay below 1e-3."""
+    g, p, init = synth.static_slug(theta)
+    L = _lattice(g, p)
+    L.init_tanh(init["shape"], init["center"], init["R"], init["normal"])
+    L.step(20000)
+    d = L.diag()
+    assert d["nonfinite"] == 0 and d["u_max"] < 1e-3
+    phi = L.read("phi").reshape(g.nz, g.ny, g.nx)[0]
+    sub = phi[1:g.ny - 1, g.nx // 2:]
+    pts = synth.contour_points(sub, 0.5)
+    pts[:, 0] += g.nx // 2
+    pts[:, 1] += 1.0
+    core = pts[(pts[:, 1] > 3.5) & (pts[:, 1] < g.ny - 4.5)]  # W/2 off the plates
+    H = g.ny - 2
+    if theta == 90.0:
+        assert np.ptp(core[:, 0]) < 0.05
+        assert abs(d["dp"]) < 1e-5
+        return
+    cx, cy, r = synth.fit_circle(core)
+    c = min(1.0, (H / 2.0) / r)
+    wetting = cx > core[:, 0].mean()  # centre of curvature on the gas side
+    got = math.degrees(math.acos(c)) if wetting else 180.0 - math.degrees(math.acos(c))
+    assert abs(got - theta) < 2.0, got
+    want = -2 * p["sigma"] * math.cos(math.radians(theta)) / H
+    assert 0.9 < d["dp"] / want < 1.02, (d["dp"], want)
