@@ -193,6 +193,26 @@ pflb_status pflb_set_diag_every(pflb_lattice *L, int k);
  * filled) when a non-finite value was found. */
 pflb_status pflb_last_diag(pflb_lattice *L, pflb_diag_t *out);
 
+/* Asynchronous form of pflb_last_diag, for stepping loops that read every
+ * step's diagnostics without stalling the GPU.  pflb_last_diag_async queues,
+ * on the lattice stream, a copy of the raw accumulators of the most recent
+ * diagnostic step (and the device error flag) into raw, caller host memory
+ * that must stay valid until the matching wait (page-locked memory keeps the
+ * call from blocking on the copy), and returns a ticket.  pflb_diag_wait
+ * blocks until that copy has landed and decodes raw into out (status as
+ * pflb_last_diag).  At most 16 reads per lattice may be outstanding; a
+ * ticket is valid until 16 newer reads have been queued. */
+typedef struct {
+  double acc[32];
+  int64_t step;
+  int32_t err;
+  int32_t pad;
+} pflb_diag_raw_t;
+
+pflb_status pflb_last_diag_async(pflb_lattice *L, pflb_diag_raw_t *raw, int64_t *ticket);
+pflb_status pflb_diag_wait(pflb_lattice *L, int64_t ticket, const pflb_diag_raw_t *raw,
+                           pflb_diag_t *out);
+
 /* Advance nsteps >= 1 steps, the last of them accumulating diagnostics, and
  * return those (as pflb_last_diag; synchronises). */
 pflb_status pflb_step_diag(pflb_lattice *L, int64_t nsteps, pflb_diag_t *out);

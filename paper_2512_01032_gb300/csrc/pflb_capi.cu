@@ -270,6 +270,8 @@ void free_all(Lattice *L) {
     if (p) cudaFree(p);
   if (L->aux) cudaStreamDestroy(L->aux);
   if (L->ev_init) cudaEventDestroy(L->ev_init);
+  for (cudaEvent_t &ev : L->aev)
+    if (ev) cudaEventDestroy(ev), ev = nullptr;
   L->aux = nullptr;
   L->ev_init = nullptr;
 }
@@ -608,13 +610,10 @@ static pflb_status check_device_flag(pflb_lattice *L) {
   return PFLB_OK;
 }
 
-static pflb_status fetch_diag(pflb_lattice *L, const double *dev, pflb_diag_t *out) {
-  double d[32];
-  CK(L, cudaMemcpyAsync(d, dev, sizeof d, cudaMemcpyDeviceToHost, L->stream));
-  pflb_status fs = check_device_flag(L);
-  if (fs != PFLB_OK) return fs;
+// Raw accumulators (32 doubles, see pflb_model.cuh D_*) to the public struct.
+static pflb_status decode_diag(const double *d, int64_t step, pflb_diag_t *out) {
   std::memset(out, 0, sizeof *out);
-  out->step = L->step;
+  out->step = step;
   out->mass = d[pflb::D_MASS];
   out->n_heavy = d[pflb::D_NHEAVY];
   out->n_p_heavy = d[pflb::D_NPH];
@@ -638,6 +637,45 @@ static pflb_status fetch_diag(pflb_lattice *L, const double *dev, pflb_diag_t *o
   if (out->nonfinite > 0 || !std::isfinite(out->mass))
     return fail(PFLB_ERR_NAN, "non-finite values in the fields");
   return PFLB_OK;
+}
+
+static pflb_status fetch_diag(pflb_lattice *L, const double *dev, pflb_diag_t *out) {
+  double d[32];
+  CK(L, cudaMemcpyAsync(d, dev, sizeof d, cudaMemcpyDeviceToHost, L->stream));
+  pflb_status fs = check_device_flag(L);
+  if (fs != PFLB_OK) return fs;
+  return decode_diag(d, L->step, out);
+}
+
+pflb_status pflb_last_diag_async(pflb_lattice *L, pflb_diag_raw_t *raw, int64_t *ticket) {
+  pflb_status s = check_lattice(L);
+  if (s != PFLB_OK) return s;
+  if (!raw || !ticket) return fail(PFLB_ERR_ARG, "null output");
+  if (L->ndiag == 0) return fail(PFLB_ERR_STATE, "no step has computed diagnostics yet");
+  const int k = (int)(L->aticket % pflb::kAsyncReads);
+  if (!L->aev[k]) CK(L, cudaEventCreateWithFlags(&L->aev[k], cudaEventDisableTiming));
+  raw->step = L->last_diag_step;
+  CK(L, cudaMemcpyAsync(raw->acc, L->diag + 32 * ((L->ndiag - 1) & 1), sizeof raw->acc,
+                        cudaMemcpyDeviceToHost, L->stream));
+  CK(L, cudaMemcpyAsync(&raw->err, L->err, sizeof raw->err, cudaMemcpyDeviceToHost, L->stream));
+  CK(L, cudaEventRecord(L->aev[k], L->stream));
+  *ticket = L->aticket++;
+  return PFLB_OK;
+}
+
+pflb_status pflb_diag_wait(pflb_lattice *L, int64_t ticket, const pflb_diag_raw_t *raw,
+                           pflb_diag_t *out) {
+  pflb_status s = check_lattice(L);
+  if (s != PFLB_OK) return s;
+  if (!raw || !out) return fail(PFLB_ERR_ARG, "null argument");
+  if (ticket < 0 || ticket >= L->aticket || ticket < L->aticket - pflb::kAsyncReads)
+    return fail(PFLB_ERR_ARG, "ticket not outstanding (at most 16 reads in flight)");
+  CK(L, cudaEventSynchronize(L->aev[ticket % pflb::kAsyncReads]));
+  if (raw->err) {
+    L->poisoned = true;
+    return fail(PFLB_ERR_TIMEOUT, "a bounded wait in the step kernel ran out; state is invalid");
+  }
+  return decode_diag(raw->acc, raw->step, out);
 }
 
 pflb_status pflb_step_ex(pflb_lattice *L, int64_t nsteps, int diag_last) {

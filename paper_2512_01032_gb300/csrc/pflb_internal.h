@@ -10,6 +10,8 @@
 
 namespace pflb {
 
+constexpr int kAsyncReads = 16;  // asynchronous diagnostic reads in flight per lattice
+
 struct Lattice {
   int nx = 0, ny = 0, nz = 0;
   long long N = 0;
@@ -18,6 +20,8 @@ struct Lattice {
   cudaStream_t stream = nullptr;
   cudaStream_t aux = nullptr;       // private stream for host uploads
   cudaEvent_t ev_init = nullptr;    // recorded after each init launch
+  cudaEvent_t aev[16] = {};         // completion of asynchronous diagnostic reads
+  int64_t aticket = 0;              // next asynchronous read ticket
   size_t elem = 4;            // bytes per stored population
   // device buffers
   void *h[2] = {nullptr, nullptr};  // [19][N] each

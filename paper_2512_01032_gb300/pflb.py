@@ -27,6 +27,11 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NAN"
                 5: "ERR_TIMEOUT", 6: "ERR_BUDGET", 7: "ERR_STATE"}
 
 
+class DiagRaw(C.Structure):
+    _fields_ = [("acc", C.c_double * 32), ("step", C.c_int64), ("err", C.c_int32),
+                ("pad", C.c_int32)]
+
+
 class ServerConfig(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("storage", C.c_int),
                 ("steps_per_tick", C.c_int), ("max_active", C.c_int), ("batched", C.c_int),
@@ -138,6 +143,10 @@ def load(build_if_missing: bool = True):
     lib.pflb_set_region.restype = st
     lib.pflb_set_kernel.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]
     lib.pflb_set_kernel.restype = st
+    lib.pflb_last_diag_async.argtypes = [C.c_void_p, C.c_void_p, _P(C.c_int64)]
+    lib.pflb_last_diag_async.restype = st
+    lib.pflb_diag_wait.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, _P(Diag)]
+    lib.pflb_diag_wait.restype = st
     lib.pflb_get_kernel.argtypes = [C.c_void_p, _P(C.c_int)]
     lib.pflb_get_kernel.restype = st
     lib.pflb_step.argtypes = [C.c_void_p, C.c_int64]
@@ -333,6 +342,21 @@ class Lattice:
 
     def set_kernel(self, kind=KERNEL_FUSED, bx=0, by=0, lz=0):
         _check(self._lib.pflb_set_kernel(self._h, int(kind), int(bx), int(by), int(lz)))
+
+    def last_diag_async(self, raw_ptr: int) -> int:
+        """Queue a copy of the last diagnostics into the DiagRaw at host
+        address raw_ptr (page-locked for an asynchronous copy); returns a
+        ticket for diag_wait."""
+        t = C.c_int64()
+        _check(self._lib.pflb_last_diag_async(self._h, C.c_void_p(raw_ptr), C.byref(t)))
+        return t.value
+
+    def diag_wait(self, ticket: int, raw_ptr: int, allow_nan=False) -> dict:
+        d = Diag()
+        s = self._lib.pflb_diag_wait(self._h, int(ticket), C.c_void_p(raw_ptr), C.byref(d))
+        if not (allow_nan and s == ERR_NAN):
+            _check(s)
+        return d.as_dict()
 
     def get_kernel(self) -> dict:
         out = (C.c_int * 4)()

@@ -6,6 +6,8 @@ this method's step.  u is near zero in these static cases (spurious
 currents ~1e-4), so it is checked with an absolute bound: 1e-12 (FP64) and
 2e-5 (FP32; u = j/rho divides FP32 rounding of j by rho_L = 1e-3).
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -257,3 +259,36 @@ def test_diagnostics_match_oracle_fields(storage, kernel):
         assert abs(d["u_max"] - e["u_max"]) <= TOL_U[storage]
         assert abs(d["kinetic"] - e["kinetic"]) <= 1e-4 * e["kinetic"] + 1e-15
         assert d["nonfinite"] == 0
+
+
+def test_async_diagnostics_match_sync_reads():
+    """Diagnostics read asynchronously into page-locked memory, one step
+    behind the stepping (the pattern of the end-to-end loop), equal the
+    synchronous reads of a twin lattice stepped in lockstep."""
+    import torch
+    from paper_2512_01032_gb300 import pflb
+    g, p, init = CS.droplet_case()
+    A = pflb.Lattice(g.nx, g.ny, g.nz, storage="fp32", **p)
+    B = pflb.Lattice(g.nx, g.ny, g.nz, storage="fp32", **p)
+    for L in (A, B):
+        L.init_tanh(0, init["center"], init["R"])
+        L.set_diag_every(1)
+    n = ctypes.sizeof(pflb.DiagRaw)
+    raw = torch.empty(2 * n, dtype=torch.uint8, pin_memory=True)
+    rp = [raw.data_ptr(), raw.data_ptr() + n]
+    want, got, prev = [], [], None
+    for k in range(40):
+        A.step(1)
+        tk = A.last_diag_async(rp[k & 1])
+        if prev is not None:
+            got.append(A.diag_wait(prev, rp[(k - 1) & 1]))
+        prev = tk
+        B.step(1)
+        want.append(B.last_diag())
+    got.append(A.diag_wait(prev, rp[39 & 1]))
+    for a, b in zip(got, want):
+        assert a["step"] == b["step"]
+        for key in ("mass", "p_heavy", "p_light", "u_max", "kinetic"):
+            assert a[key] == pytest.approx(b[key], rel=1e-6, abs=1e-300), key
+    with pytest.raises(pflb.PflbError):
+        A.diag_wait(prev + 1, rp[0])  # not queued yet
