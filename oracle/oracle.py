@@ -76,6 +76,8 @@ def _load():
         lib.orc_update_ghosts_only.argtypes = [C.c_void_p]
         lib.orc_set_nthreads.argtypes = [C.c_void_p, C.c_int]
         lib.orc_set_force.argtypes = [C.c_void_p, _d]
+        lib.orc_set_x_boundaries.argtypes = [C.c_void_p, C.c_int, _d, C.c_int, _d]
+        lib.orc_set_x_boundaries.restype = C.c_int
         lib.orc_lattice_tables.argtypes = [_P(C.c_int), _P(C.c_int), _P(C.c_int), _d, _P(C.c_int)]
         lib.orc_max_threads.restype = C.c_int
         lib.orc_gamma.argtypes = [_d, _d]
@@ -286,6 +288,23 @@ class OracleLattice:
     def set_force(self, F):
         f = _f64(F)
         self._lib.orc_set_force(self._h, _ptr(f))
+
+    def set_x_boundaries(self, lo=None, hi=None):
+        """Open x boundaries (reading R22): lo / hi are dicts with type
+        ("pressure" or "velocity"), P, u (3) and phi; None for both restores
+        periodic x."""
+        kinds = {None: 0, "pressure": 1, "velocity": 2}
+
+        def pack(b):
+            if b is None:
+                return 0, np.zeros(5)
+            u = b.get("u", (0.0, 0.0, 0.0))
+            return kinds[b["type"]], _f64([b.get("P", 0.0), u[0], u[1], u[2], b.get("phi", 0.0)])
+
+        tl, vl = pack(lo)
+        th, vh = pack(hi)
+        if self._lib.orc_set_x_boundaries(self._h, tl, _ptr(vl), th, _ptr(vh)) != 0:
+            raise ValueError("bad open-boundary request")
 
     def macros(self):
         out = [np.zeros(self.N) for _ in range(6)]

@@ -43,6 +43,21 @@
  *   R16 Initial state: h = h_eq(phi0, u=0, n(grad phi0)), g = g_eq(P0, u=0)
  *       with K from grad phi0, ghosts = phi of the wall node.
  *   R17 Solid cells are never updated; sums run over fluid cells only.
+ *   R22 Open x boundaries (Sec. IV A: Dirichlet pressure with Neumann
+ *       velocity and phi; velocity inlets): the fluid cells of the planes
+ *       x = 0 and x = nx-1 are boundary cells.  At the start of each step a
+ *       boundary state (phi_b, P_b, u_b) is formed: given values, and for the
+ *       Neumann quantities those of the adjacent interior cell (x = 1 or
+ *       nx-2) in their bulk form, phi = sum h, P = T sum g,
+ *       rho u = sum c g + F/2.  Pressure boundary: P_b given, phi_b and u_b
+ *       from the neighbour.  Velocity boundary: u_b and phi_b given, P_b
+ *       from the neighbour.  The boundary cell's phi is phi_b (it enters the
+ *       neighbours' stencils); it is not collided: its post-collision
+ *       populations are the equilibria h_i = phi_b Gamma_i(u_b),
+ *       g_i = w_i P_b / T + rho_b (Gamma_i(u_b) - w_i), streamed as usual
+ *       (bounce-back at solid links, no free-slip band, no ghost update).
+ *       What streams into a boundary cell (including the periodic wrap
+ *       between the two planes) is discarded.
  *
  * Parity unpinned by the paper (pinned only oracle <-> GPU): the sub-step
  * order (R3), the ghost lag (R11), the blend side (R12) and the free-slip
@@ -99,6 +114,9 @@ typedef struct {
     double *phi;      /* [N] order parameter of the current step */
     double *ghost;    /* [N*Q] phi_{s,i} of wall node x for solid link i */
     double *ghost_old;/* [N*Q] scratch: ghosts of the previous step */
+    int bc_type[2];   /* x = 0, x = nx-1: 0 periodic, 1 pressure, 2 velocity (R22) */
+    double bc_val[2][5]; /* given P, ux, uy, uz, phi */
+    double *bstate;   /* [2*ny*nz*5] boundary states phi, P, ux, uy, uz */
     int64_t step;
 } orc_lattice;
 
@@ -381,7 +399,7 @@ void orc_destroy(orc_lattice *L) {
     if (!L) return;
     free(L->solid); free(L->nw); free(L->cth); free(L->sth);
     free(L->h); free(L->g); free(L->h2); free(L->g2);
-    free(L->phi); free(L->ghost); free(L->ghost_old);
+    free(L->phi); free(L->ghost); free(L->ghost_old); free(L->bstate);
     free(L);
 }
 
@@ -430,6 +448,64 @@ void orc_init_phi(orc_lattice *L, const double *phi0, double P0) {
     L->step = 0;
 }
 
+/* --------------------------------------------------- open boundaries (R22) */
+
+static inline int bc_side(const orc_lattice *L, int64_t c) {
+    if (!L->bc_type[0] || L->solid[c]) return -1;
+    int64_t x = c % L->nx;
+    return x == 0 ? 0 : (x == L->nx - 1 ? 1 : -1);
+}
+
+/* Boundary states from the current (post-stream) populations, then phi of
+ * the boundary cells := phi_b.  Needs phi of the interior cells. */
+static void boundary_states(orc_lattice *L) {
+    const orc_params *p = &L->p;
+    int64_t plane = (int64_t)L->ny * L->nz;
+    for (int side = 0; side < 2 && L->bc_type[0]; ++side) {
+        int xb = side ? L->nx - 1 : 0, xa = side ? L->nx - 2 : 1;
+        for (int64_t j = 0; j < plane; ++j) {
+            int64_t yz = j * L->nx;                 /* y + ny z, times nx */
+            int64_t cb = xb + yz, ca = xa + yz;
+            double *st = L->bstate + (side * plane + j) * 5;
+            const double *v = L->bc_val[side];
+            double phia = 0, Pa = 0, ua[3] = {0, 0, 0};
+            if (!L->solid[ca]) {
+                const double *g = L->g + ca * Q;
+                double s0 = 0, m[3] = {0, 0, 0};
+                for (int i = 0; i < Q; ++i) {
+                    s0 += g[i];
+                    m[0] += CX[i] * g[i]; m[1] += CY[i] * g[i]; m[2] += CZ[i] * g[i];
+                }
+                phia = L->phi[ca];
+                double rho = p->rho_L + phia * (p->rho_H - p->rho_L);
+                for (int a = 0; a < 3; ++a) ua[a] = (m[a] + 0.5 * p->Fex[a]) / rho;
+                Pa = TT * s0;
+            }
+            if (L->bc_type[side] == 1) {      /* pressure */
+                st[0] = phia; st[1] = v[0]; st[2] = ua[0]; st[3] = ua[1]; st[4] = ua[2];
+            } else {                          /* velocity */
+                st[0] = v[4]; st[1] = Pa; st[2] = v[1]; st[3] = v[2]; st[4] = v[3];
+            }
+            if (!L->solid[cb]) L->phi[cb] = st[0];
+        }
+    }
+}
+
+/* Post-collision populations of a boundary cell: equilibria at its state. */
+static void boundary_equilibria(const orc_lattice *L, int64_t c, int side, double hs[Q],
+                                double gs[Q]) {
+    const orc_params *p = &L->p;
+    int64_t j = c / L->nx;
+    const double *st = L->bstate + (side * (int64_t)L->ny * L->nz + j) * 5;
+    double u[3] = {st[2], st[3], st[4]}, G[Q];
+    orc_gamma(u, G);
+    double rho = p->rho_L + st[0] * (p->rho_H - p->rho_L);
+    for (int i = 0; i < Q; ++i) {
+        hs[i] = st[0] * G[i];
+        gs[i] = WQ[i] * st[1] / TT + rho * (G[i] - WQ[i]);
+    }
+}
+
 /* phi = sum_i h_i on fluid cells (Sec. II A, after Eq. 3). */
 static void compute_phi(orc_lattice *L) {
     int64_t N = L->N;
@@ -450,7 +526,7 @@ static void update_ghosts(orc_lattice *L, double *ghost_out) {
     const orc_params *p = &L->p;
 #pragma omp parallel for num_threads(L->p.nthreads) schedule(static)
     for (int64_t c = 0; c < N; ++c) {
-        if (L->solid[c]) continue;
+        if (L->solid[c] || bc_side(L, c) >= 0) continue;  /* R22: no ghost update */
         uint32_t m = solid_links(L, c);
         if (!m) continue;
         double val[Q], grad[3], lap, fresh[Q];
@@ -470,6 +546,7 @@ void orc_macros(orc_lattice *L, double *phi, double *rho, double *P, double *ux,
     int64_t N = L->N;
     compute_phi(L);
     double *gs = (double *)malloc(N * Q * sizeof(double));
+    boundary_states(L);
     memcpy(gs, L->ghost, N * Q * sizeof(double));
     update_ghosts(L, gs);
     const orc_params *p = &L->p;
@@ -477,6 +554,15 @@ void orc_macros(orc_lattice *L, double *phi, double *rho, double *P, double *ux,
     for (int64_t c = 0; c < N; ++c) {
         if (L->solid[c]) {
             phi[c] = rho[c] = P[c] = ux[c] = uy[c] = uz[c] = 0.0;
+            continue;
+        }
+        const int side = bc_side(L, c);
+        if (side >= 0) {  /* R22: the boundary state */
+            const double *st = L->bstate + (side * (int64_t)L->ny * L->nz + c / L->nx) * 5;
+            phi[c] = st[0];
+            rho[c] = p->rho_L + st[0] * (p->rho_H - p->rho_L);
+            P[c] = st[1];
+            ux[c] = st[2]; uy[c] = st[3]; uz[c] = st[4];
             continue;
         }
         double val[Q], grad[3], lap, r, pr, u[3], mu;
@@ -496,6 +582,7 @@ static void one_step(orc_lattice *L) {
     const orc_params *p = &L->p;
     int64_t N = L->N;
     compute_phi(L);                 /* step 1 */
+    boundary_states(L);             /* R22 */
     double *gnew = (double *)malloc(N * Q * sizeof(double));
     memcpy(gnew, L->ghost, N * Q * sizeof(double));
     update_ghosts(L, gnew);         /* step 2 */
@@ -507,6 +594,22 @@ static void one_step(orc_lattice *L) {
 #pragma omp parallel for num_threads(L->p.nthreads) schedule(static)
     for (int64_t c = 0; c < N; ++c) {
         if (L->solid[c]) continue;
+        const int side = bc_side(L, c);
+        if (side >= 0) {                                 /* R22 */
+            double hs[Q], gs[Q];
+            boundary_equilibria(L, c, side, hs, gs);
+            for (int i = 0; i < Q; ++i) {
+                int64_t y = nbr(L, c, i);
+                if (!L->solid[y]) {
+                    L->h2[y * Q + i] = hs[i];
+                    L->g2[y * Q + i] = gs[i];
+                } else {
+                    L->h2[c * Q + OPP[i]] = hs[i];
+                    L->g2[c * Q + OPP[i]] = gs[i];
+                }
+            }
+            continue;
+        }
         const double *h = L->h + c * Q, *g = L->g + c * Q;
         double val[Q], grad[3], lap;                     /* step 3 */
         stencil_values(L, c, L->ghost, val);
@@ -569,6 +672,24 @@ void orc_update_ghosts_only(orc_lattice *L) {
     free(gnew);
 }
 void orc_set_nthreads(orc_lattice *L, int n) { L->p.nthreads = n > 0 ? n : 1; }
+
+/* Open x boundaries (R22): types 0 (both: periodic), 1 pressure, 2 velocity;
+ * values P, ux, uy, uz, phi per side.  Returns 0, or -1 for a bad request. */
+int orc_set_x_boundaries(orc_lattice *L, int type_lo, const double *val_lo, int type_hi,
+                         const double *val_hi) {
+    if ((type_lo == 0) != (type_hi == 0) || type_lo < 0 || type_lo > 2 || type_hi < 0 ||
+        type_hi > 2 || (type_lo && (L->nx < 3 || !val_lo || !val_hi)))
+        return -1;
+    L->bc_type[0] = type_lo;
+    L->bc_type[1] = type_hi;
+    for (int k = 0; k < 5; ++k) {
+        L->bc_val[0][k] = type_lo ? val_lo[k] : 0.0;
+        L->bc_val[1][k] = type_hi ? val_hi[k] : 0.0;
+    }
+    if (type_lo && !L->bstate)
+        L->bstate = (double *)calloc((size_t)2 * L->ny * L->nz * 5, sizeof(double));
+    return 0;
+}
 void orc_set_force(orc_lattice *L, const double F[3]) {
     for (int a = 0; a < 3; ++a) L->p.Fex[a] = F[a];
 }

@@ -1,0 +1,80 @@
+"""Open x boundaries of the oracle (reading R22: Dirichlet pressure with
+Neumann velocity and phi, and velocity inlets, Sec. IV A) pinned to
+closed forms of steady channel flow: plane Poiseuille flow under an imposed
+pressure difference, and flux conservation from a velocity inlet to a
+pressure outlet."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+NX, NY = 40, 18                        # plates: solid rows y = 0 and y = 17
+H = NY - 2                             # gap between the halfway walls
+MU = 1.0 / 6.0                         # rho_H nu_H with the liquid filling the channel
+
+
+def _channel(lo, hi, steps):
+    solid = np.zeros((1, NY, NX), np.uint8)
+    solid[:, 0, :] = 1
+    solid[:, -1, :] = 1
+    L = O.OracleLattice(NX, NY, 1, solid=solid.reshape(-1), nthreads=os.cpu_count() or 1,
+                        sigma=0.01, W=4.0, M=0.02, rho_H=1.0, rho_L=1e-3, nu_H=MU, nu_L=0.1)
+    L.init_phi((1 - solid).reshape(-1).astype(float))
+    L.set_x_boundaries(lo, hi)
+    L.step(steps)
+    m = L.macros()
+    return {k: v.reshape(NY, NX) for k, v in m.items()}
+
+
+def test_pressure_driven_poiseuille():
+    """P = dP at x = 0 and 0 at x = nx-1: the interior pressure falls
+    linearly with the imposed gradient dP / (nx - 1) (within 3 %), and the
+    velocity profile is the parabola u = G (y - 1/2)(H + 1/2 - y) / (2 mu)
+    of that gradient (within 2 % of its maximum)."""
+    dP = 2e-3
+    m = _channel(dict(type="pressure", P=dP), dict(type="pressure", P=0.0), 8000)
+    P = m["P"][1:-1, :].mean(axis=0)
+    xs = np.arange(5, NX - 5)
+    G = -np.polyfit(xs, P[xs], 1)[0]
+    assert G == pytest.approx(dP / (NX - 1), rel=0.03)
+    y = np.arange(1, NY - 1)
+    want = G * (y - 0.5) * (H + 0.5 - y) / (2 * MU)
+    got = m["ux"][1:-1, NX // 2]
+    assert np.max(np.abs(got - want)) < 0.02 * want.max(), (got, want)
+    # no transverse flow, and the same flux through every interior section
+    assert np.max(np.abs(m["uy"][1:-1, 2:-2])) < 1e-3 * want.max()
+    flux = m["ux"][1:-1, 2:-2].sum(axis=0)
+    assert np.ptp(flux) < 1e-3 * flux.mean()
+
+
+def test_velocity_inlet_to_pressure_outlet():
+    """A uniform inlet velocity U at x = 0 (phi = 1) and P = 0 at x = nx-1:
+    every interior cross-section carries the same flux (steady mass
+    conservation, to 1e-3), which is the inlet flux U H within 5 % (the
+    equilibrium inlet is first-order: the adjacent node's non-equilibrium
+    part is not reconstructed, and at H = 16 the inflow falls 3.6 % short),
+    the profile develops towards the parabola of that flux, and the pressure
+    falls towards the outlet."""
+    U = 5e-3
+    m = _channel(dict(type="velocity", u=(U, 0.0, 0.0), phi=1.0),
+                 dict(type="pressure", P=0.0), 8000)
+    flux = m["ux"][1:-1, 2:-2].sum(axis=0)
+    assert np.ptp(flux) < 1e-3 * flux.mean()
+    assert flux.mean() == pytest.approx(U * H, rel=0.05)
+    U = flux.mean() / H
+    y = np.arange(1, NY - 1)
+    parab = 1.5 * U * (y - 0.5) * (H + 0.5 - y) / (H * H / 4.0)
+    got = m["ux"][1:-1, NX - 6]
+    assert np.max(np.abs(got - parab)) < 0.1 * parab.max()
+    P = m["P"][1:-1, :].mean(axis=0)
+    assert P[3] > P[NX // 2] > P[NX - 4] > -1e-9
+
+
+def test_boundary_requests_are_checked():
+    L = O.OracleLattice(8, 6, 1, sigma=0.01, W=4.0, M=0.02, rho_H=1.0, rho_L=1e-3, nu_H=0.1,
+                        nu_L=0.1)
+    with pytest.raises(ValueError):
+        L.set_x_boundaries(dict(type="pressure", P=0.0), None)  # one side only
+    L.set_x_boundaries(None, None)  # periodic again
