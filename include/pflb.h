@@ -175,6 +175,33 @@ pflb_status pflb_set_region(pflb_lattice *L, const int box[6]);
  * [2, 32], from the device's SM count and the kernel's occupancy. */
 pflb_status pflb_set_kernel(pflb_lattice *L, int kind, int bx, int by, int lz);
 
+/* Open x boundaries (Sec. IV A: "standard" Dirichlet pressure with Neumann
+ * velocity and phi; velocity inlets).  The fluid cells of the planes x = 0
+ * (lo) and x = nx-1 (hi) become boundary cells; both planes must be given
+ * (NULL for both restores periodic x).  Each step, before the update, a
+ * boundary state (phi_b, P_b, u_b) is formed per boundary cell:
+ *   PFLB_XBC_PRESSURE: P_b = P; phi_b and u_b are those of the adjacent
+ *     interior cell (x = 1 or nx-2) in bulk form (phi = sum h,
+ *     rho u = sum c g + F/2);
+ *   PFLB_XBC_VELOCITY: u_b = u and phi_b = phi; P_b = T sum g of the
+ *     adjacent interior cell.
+ * A boundary cell is not collided: its post-collision populations are the
+ * equilibria h_i = phi_b Gamma_i(u_b), g_i = w_i P_b / T +
+ * rho_b (Gamma_i(u_b) - w_i), streamed as usual (bounce-back at solid
+ * links), and whatever streams into it is discarded.  Boundary cells carry
+ * no diagnostics and read back their boundary state.  First-order accurate
+ * (equilibrium boundary).  Lattices with open boundaries run the fused or
+ * two-pass kernel (not the TMA one) and cannot join a batch. */
+enum { PFLB_XBC_PRESSURE = 1, PFLB_XBC_VELOCITY = 2 };
+typedef struct {
+  int type;        /* PFLB_XBC_PRESSURE or PFLB_XBC_VELOCITY */
+  double P;        /* pressure (pressure boundary) */
+  double u[3];     /* velocity (velocity boundary) */
+  double phi;      /* order parameter (velocity boundary) */
+} pflb_xbc;
+
+pflb_status pflb_set_x_boundaries(pflb_lattice *L, const pflb_xbc *lo, const pflb_xbc *hi);
+
 /* The launch shape in effect: out = {kind, bx, by, lz}. */
 pflb_status pflb_get_kernel(const pflb_lattice *L, int out[4]);
 

@@ -265,7 +265,7 @@ cudaError_t dev_alloc(Lattice *L, T **ptr, size_t count) {
 
 void free_all(Lattice *L) {
   void *ptrs[] = {L->h[0], L->h[1], L->g, L->wp[0], L->wp[1], L->flags, L->widx, L->wmask,
-                  L->wgeo, L->ghost, L->phi, L->diag, L->out, L->phi0, L->err};
+                  L->wgeo, L->ghost, L->phi, L->diag, L->out, L->phi0, L->err, L->bcm};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (L->aux) cudaStreamDestroy(L->aux);
@@ -565,12 +565,54 @@ pflb_status pflb_set_kernel(pflb_lattice *L, int kind, int bx, int by, int lz) {
   return PFLB_OK;
 }
 
+pflb_status pflb_set_x_boundaries(pflb_lattice *L, const pflb_xbc *lo, const pflb_xbc *hi) {
+  pflb_status s = check_lattice(L);
+  if (s != PFLB_OK) return s;
+  const bool on = lo || hi;
+  if (on) {
+    if (!lo || !hi) return fail(PFLB_ERR_ARG, "open x boundaries need both planes");
+    for (const pflb_xbc *b : {lo, hi}) {
+      if (b->type != PFLB_XBC_PRESSURE && b->type != PFLB_XBC_VELOCITY)
+        return fail(PFLB_ERR_ARG, "boundary type must be PFLB_XBC_PRESSURE or PFLB_XBC_VELOCITY");
+      if (!std::isfinite(b->P) || !std::isfinite(b->phi) || !std::isfinite(b->u[0]) ||
+          !std::isfinite(b->u[1]) || !std::isfinite(b->u[2]))
+        return fail(PFLB_ERR_ARG, "non-finite boundary value");
+    }
+    if (L->nx < 3) return fail(PFLB_ERR_ARG, "open x boundaries need nx >= 3");
+    if (!L->bcm) {
+      const size_t bytes = 5 * 2 * (size_t)L->ny * L->nz * compute_bytes(L->p.storage);
+      cudaError_t e = cudaMalloc(&L->bcm, bytes);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        L->bcm = nullptr;
+        return fail(PFLB_ERR_OOM, "device allocation failed (boundary states)");
+      }
+      L->dev_bytes += (int64_t)bytes;
+    }
+    const pflb_xbc *bs[2] = {lo, hi};
+    for (int k = 0; k < 2; ++k) {
+      L->bc_type[k] = bs[k]->type;
+      const double v[5] = {bs[k]->P, bs[k]->u[0], bs[k]->u[1], bs[k]->u[2], bs[k]->phi};
+      for (int q = 0; q < 5; ++q) L->bc_val[k][q] = v[q];
+    }
+  }
+  if (on != L->bc_on) {
+    CK(L, dispatch(L, [&](auto *s_, auto *r_) {
+      PFLB_SR_TYPES
+      return pflb::mark_xbc<S, R>(*L, on);
+    }));
+  }
+  L->bc_on = on;
+  L->lz = resolve_lz(L);  // the TMA kernel is not used with open boundaries
+  return PFLB_OK;
+}
+
 pflb_status pflb_get_kernel(const pflb_lattice *L, int out[4]) {
   pflb_status s = check_lattice(L);
   if (s != PFLB_OK) return s;
   if (!out) return fail(PFLB_ERR_ARG, "null output");
   const bool tma = L->kernel == PFLB_KERNEL_FUSED_TMA && L->p.storage == PFLB_STORAGE_FP32 &&
-                   L->tma_ok;
+                   L->tma_ok && !L->bc_on;
   out[0] = L->kernel;
   out[1] = tma ? 32 : L->bx;
   out[2] = tma ? 8 : L->by;
@@ -884,6 +926,8 @@ extern "C" pflb_status pflb_batch_create(pflb_lattice *const *lattices, int coun
     if (st != PFLB_OK) return st;
     if (lattices[l]->p.storage != lattices[0]->p.storage)
       return fail(PFLB_ERR_ARG, "all lattices of a batch need the same storage");
+    if (lattices[l]->bc_on)
+      return fail(PFLB_ERR_ARG, "lattices with open x boundaries cannot be batched");
     for (int k = 0; k < l; ++k)
       if (lattices[k] == lattices[l]) return fail(PFLB_ERR_ARG, "a lattice appears twice");
   }

@@ -46,6 +46,11 @@ struct Lattice {
   int kernel = PFLB_KERNEL_FUSED;
   int bx = 32, by = 4, lz = 16;   // lz: planes per block in effect
   int lz_req = 0;                  // requested planes per block, 0 = automatic
+  // open x boundaries (reading R22)
+  bool bc_on = false;
+  int bc_type[2] = {0, 0};         // 1 pressure, 2 velocity
+  double bc_val[2][5] = {};        // P, ux, uy, uz, phi
+  void *bcm = nullptr;             // [5][2 ny nz] boundary states, compute type
   int reg[6] = {0, 0, 0, 0, 0, 0};
   bool poisoned = false;
   int64_t dev_bytes = 0;
@@ -74,6 +79,7 @@ template <class S, class R> cudaError_t launch_macro(Lattice &L, bool fields);
 template <class S, class R> cudaError_t set_model(Lattice &L);
 template <class S, class R> int max_block_threads();
 template <class S, class R> int auto_lz(const Lattice &L);
+template <class S, class R> cudaError_t mark_xbc(Lattice &L, bool on);
 // Batch: size of one descriptor, host-side descriptor build (2 per lattice,
 // diagnostics pointers for the next diagnostic launch), one step launch,
 // and the occupancy-limited blocks per SM of the batch kernel.

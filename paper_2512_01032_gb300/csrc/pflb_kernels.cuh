@@ -51,7 +51,15 @@ struct Args {
   double *diag_zero; // [32] accumulator of the next diagnostic launch, zeroed here
   int reg[6];        // diagnostic box [x0,x1) x [y0,y1) x [z0,z1)
   double *out;       // macro outputs [6][N] (phi, rho, P, ux, uy, uz) or null
+  const R *bcm;      // open x boundaries: states [5][nbc] (phi, P, ux, uy, uz), or null
+  int nbc;           // 2 ny nz: plane x = 0, then plane x = nx-1
 };
+
+// Index of the boundary state of a cell in plane x = 0 or x = nx-1.
+template <class S, class R>
+__device__ __forceinline__ int bc_index(const Args<S, R> &a, int x, int yz) {
+  return yz + (x == 0 ? 0 : a.ny * a.nz);
+}
 
 template <class R>
 struct DiagAcc {
@@ -116,6 +124,48 @@ __device__ __forceinline__ void gather_g(const Args<S, R> &a, int c, uint32_t lm
   }
 }
 
+template <class S, class R, bool ODD>
+__device__ __forceinline__ void store_cell(const Args<S, R> &a, int c, uint32_t lm, int rec,
+                                           const Nbr &nb, R h[Q], R g[Q], const R val[Q],
+                                           bool in_band);
+
+// Open x boundary cell (reading R22): not collided; its post-collision
+// populations are the equilibria at the boundary state formed before the
+// step (k_xbc), h_i = phi_b Gamma_i(u_b), g_i = w_i P_b / T +
+// rho_b (Gamma_i - w_i); no diagnostics, no ghost update, no free-slip band.
+template <class S, class R, bool ODD, int MODE>
+__device__ __forceinline__ void boundary_cell(const Args<S, R> &a, int x, int y, int z, int c,
+                                              uint32_t lm, int rec, const Nbr &nb) {
+  const int j = bc_index(a, x, y + a.ny * z), nb5 = a.nbc;
+  const R phib = a.bcm[j], Pb = a.bcm[nb5 + j];
+  const R ux = a.bcm[2 * nb5 + j], uy = a.bcm[3 * nb5 + j], uz = a.bcm[4 * nb5 + j];
+  const R rho = a.m.rho_L + phib * a.m.rho_dif;
+  if (MODE == MODE_MACRO) {
+    if (a.out) {
+      const long long N = a.N;
+      a.out[c] = (double)phib;
+      a.out[N + c] = (double)rho;
+      a.out[2 * N + c] = (double)Pb;
+      a.out[3 * N + c] = (double)ux;
+      a.out[4 * N + c] = (double)uy;
+      a.out[5 * N + c] = (double)uz;
+    }
+    return;
+  }
+  const R uu15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
+  R h[Q], g[Q], val[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const R wi = R(w_of(i));
+    const R cu = R(cx_of(i)) * ux + R(cy_of(i)) * uy + R(cz_of(i)) * uz;
+    const R Gd = wi * (cu * (R(3) + R(4.5) * cu) - uu15);  // Gamma_i - w_i
+    h[i] = phib * (wi + Gd);
+    g[i] = wi * R(3) * Pb + rho * Gd;
+    val[i] = R(0);
+  }
+  store_cell<S, R, ODD>(a, c, lm, rec, nb, h, g, val, false);
+}
+
 // Rest of the update (or macro evaluation) of one fluid cell c at (x, y, z)
 // once its populations are gathered: h[] and g[] hold the streamed
 // populations, phi = sum h, val[1..18] the phi of the 18 neighbours
@@ -125,6 +175,10 @@ __device__ __forceinline__ void finish_cell(const Args<S, R> &a, int x, int y, i
                                             uint8_t f, uint32_t lm, int rec, const Nbr &nb,
                                             R h[Q], R g[Q], R phi, R val[Q], DiagAcc<R> &acc) {
   const Model<R> &m = a.m;
+  if (f & F_BC) {
+    boundary_cell<S, R, ODD, MODE>(a, x, y, z, c, lm, rec, nb);
+    return;
+  }
   val[0] = phi;
   R gx, gy, gz, lap;
   const bool wall = (f & F_WALL) != 0;
@@ -177,6 +231,20 @@ __device__ __forceinline__ void finish_cell(const Args<S, R> &a, int x, int y, i
   }
 
   collide(m, h, g, mc, phi, gx, gy, gz, lap);
+  store_cell<S, R, ODD>(a, c, lm, rec, nb, h, g, val,
+                        m.free_slip && phi >= m.band_lo && phi <= m.band_hi);
+}
+
+// Streaming of one cell's post-collision populations: h pushed into the
+// other buffer (halfway bounce-back at solid links), g written A-A; g on
+// solid links goes to the wall population buffer, to this node
+// (bounce-back) or, when in_band and the neighbour's phi (val) is in the
+// band too, to the tangential neighbour (specular reflection, Sec. III A).
+template <class S, class R, bool ODD>
+__device__ __forceinline__ void store_cell(const Args<S, R> &a, int c, uint32_t lm, int rec,
+                                           const Nbr &nb, R h[Q], R g[Q], const R val[Q],
+                                           bool in_band) {
+  const Model<R> &m = a.m;
   S he[Q], h_lo;
   enc_h_cell<S, R>(h, he, &h_lo);
   if constexpr (Codec<S>::scaled) a.hout[Q][c] = h_lo;  // rest population stays
@@ -201,10 +269,6 @@ __device__ __forceinline__ void finish_cell(const Args<S, R> &a, int x, int y, i
     else
       a.hout[i][c + nb.off(i)] = he[i];
   }
-  // g: A-A write; solid links go to the wall population buffer, either to
-  // this node (bounce-back) or to the tangential neighbour (specular
-  // reflection, free-slip band of Sec. III A).
-  const bool in_band = m.free_slip && phi >= m.band_lo && phi <= m.band_hi;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     if (i != 0 && ((lm >> i) & 1u)) {
@@ -367,7 +431,9 @@ __device__ __forceinline__ void diag_thread_flush(double *diag, const R *tacc,
 // phi of one cell from the h buffer being read (0 for solid cells).
 template <class S, class R>
 __device__ __forceinline__ R cell_phi(const Args<S, R> &a, int c) {
-  if (a.flags[c] & F_SOLID) return R(0);
+  const uint8_t f = a.flags[c];
+  if (f & F_SOLID) return R(0);
+  if (f & F_BC) return a.bcm[bc_index(a, c % a.nx, c / a.nx)];  // phi_b
   R h[Q];
   ld_h_cell<S, R>(a.hin, c, h);
   R s = R(0);
@@ -524,6 +590,86 @@ __global__ void __launch_bounds__(256, PFLB_MIN_BLOCKS)
   march_tile<S, R, ODD, DIAG>(a, blockIdx.x * BX, blockIdx.y * BY, zb, min(zb + a.lz, a.nz), BX,
                               BY, sphi, tacc);
   if (DIAG) diag_thread_flush(a.diag, tacc, wacc);
+}
+
+// ------------------------------------------------------ open boundaries
+// Boundary states of the open x planes (reading R22), formed before each
+// step from the state the step will read: given values, and for the
+// Neumann quantities the adjacent interior cell's bulk moments (phi = sum h,
+// P = T sum g, rho u = sum c g + F/2), its g gathered exactly as that cell
+// will gather it.  One thread per cell of the two planes; no other kernel
+// runs meanwhile, so the reads cannot race the step's writes.
+struct XbcSpec {
+  int type[2];        // 1 pressure (P given), 2 velocity (u and phi given)
+  double val[2][5];   // P, ux, uy, uz, phi
+};
+
+template <class S, class R, bool ODD>
+__global__ void k_xbc(const __grid_constant__ Args<S, R> a, const __grid_constant__ XbcSpec sp,
+                      R *bcm) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int plane = a.ny * a.nz;
+  if (j >= 2 * plane) return;
+  const int side = j >= plane, yz = j - side * plane;
+  const int y = yz % a.ny, z = yz / a.ny;
+  const int xa = side ? a.nx - 2 : 1;
+  const int ca = xa + a.nx * yz;
+  const uint8_t fa = a.flags[ca];
+  R phia = R(0), Pa = R(0), ua[3] = {R(0), R(0), R(0)};
+  if (!(fa & F_SOLID)) {
+    R h[Q], g[Q];
+    ld_h_cell<S, R>(a.hin, ca, h);
+    Nbr nb;
+    nb.init(xa, y, z, a.nx, a.ny, a.nz);
+    uint32_t lm = 0;
+    int rec = 0;
+    if (fa & F_WALL) {
+      rec = a.widx[ca];
+      lm = a.wmask[rec];
+    }
+    gather_g<S, R, ODD>(a, ca, lm, rec, nb, g);
+    R s0 = R(0), m0 = R(0), m1 = R(0), m2 = R(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      phia += h[i];
+      s0 += g[i];
+      m0 += R(cx_of(i)) * g[i];
+      m1 += R(cy_of(i)) * g[i];
+      m2 += R(cz_of(i)) * g[i];
+    }
+    const R rho = a.m.rho_L + phia * a.m.rho_dif;
+    ua[0] = (m0 + R(0.5) * a.m.Fx) / rho;
+    ua[1] = (m1 + R(0.5) * a.m.Fy) / rho;
+    ua[2] = (m2 + R(0.5) * a.m.Fz) / rho;
+    Pa = s0 / R(3);
+  }
+  const double *v = sp.val[side];
+  const int n = 2 * plane;
+  if (sp.type[side] == 1) {
+    bcm[j] = phia;
+    bcm[n + j] = (R)v[0];
+    bcm[2 * n + j] = ua[0];
+    bcm[3 * n + j] = ua[1];
+    bcm[4 * n + j] = ua[2];
+  } else {
+    bcm[j] = (R)v[4];
+    bcm[n + j] = Pa;
+    bcm[2 * n + j] = (R)v[1];
+    bcm[3 * n + j] = (R)v[2];
+    bcm[4 * n + j] = (R)v[3];
+  }
+}
+
+// Sets (on) or clears (off) the boundary flag of the fluid cells of the
+// planes x = 0 and x = nx-1.
+static __global__ void k_mark_xbc(uint8_t *flags, int nx, int plane, int on) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= 2 * plane) return;
+  const int side = j >= plane, yz = j - side * plane;
+  const long long c = (side ? nx - 1 : 0) + (long long)nx * yz;
+  const uint8_t f = flags[c];
+  if (f & F_SOLID) return;
+  flags[c] = on ? (uint8_t)(f | F_BC) : (uint8_t)(f & ~F_BC);
 }
 
 // ------------------------------------------------------------ init

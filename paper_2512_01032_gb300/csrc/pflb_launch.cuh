@@ -72,7 +72,26 @@ static Args<S, R> make_args(Lattice &L) {
   a.diag_zero = nullptr;
   for (int k = 0; k < 6; ++k) a.reg[k] = L.reg[k];
   a.out = nullptr;
+  a.bcm = L.bc_on ? (const R *)L.bcm : nullptr;
+  a.nbc = 2 * L.ny * L.nz;
   return a;
+}
+
+// Boundary states of the open x planes for the state the next launch reads.
+template <class S, class R>
+static cudaError_t launch_xbc(Lattice &L, const Args<S, R> &a) {
+  if (!L.bc_on) return cudaSuccess;
+  XbcSpec sp;
+  for (int s = 0; s < 2; ++s) {
+    sp.type[s] = L.bc_type[s];
+    for (int k = 0; k < 5; ++k) sp.val[s][k] = L.bc_val[s][k];
+  }
+  const int n = 2 * L.ny * L.nz, T = 128;
+  if (L.step & 1)
+    k_xbc<S, R, true><<<(n + T - 1) / T, T, 0, L.stream>>>(a, sp, (R *)L.bcm);
+  else
+    k_xbc<S, R, false><<<(n + T - 1) / T, T, 0, L.stream>>>(a, sp, (R *)L.bcm);
+  return cudaGetLastError();
 }
 
 template <class S, class R>
@@ -97,7 +116,8 @@ cudaError_t launch_init(Lattice &L, const double *d_phi0, double P0) {
 
 // The staged kernel (FP32, x extent a multiple of 4 and at least 64).
 inline bool async_eligible(const Lattice &L) {
-  return L.kernel == PFLB_KERNEL_FUSED_TMA && L.p.storage == PFLB_STORAGE_FP32 && L.tma_ok;
+  return L.kernel == PFLB_KERNEL_FUSED_TMA && L.p.storage == PFLB_STORAGE_FP32 && L.tma_ok &&
+         !L.bc_on;
 }
 
 template <bool ODD, bool DIAG>
@@ -199,7 +219,8 @@ template <class S, class R>
 cudaError_t launch_step(Lattice &L, bool diag) {
   Args<S, R> a = make_args<S, R>(L);
   const bool odd = (L.step & 1) != 0;
-  cudaError_t e;
+  cudaError_t e = launch_xbc<S, R>(L, a);
+  if (e != cudaSuccess) return e;
   if (diag) {
     // Diagnostic launch d accumulates into buffer d&1 and zeroes the other.
     a.diag = L.diag + 32 * (L.ndiag & 1);
@@ -231,9 +252,17 @@ cudaError_t launch_macro(Lattice &L, bool fields) {
   a.diag = L.diag + 64;
   a.diag_zero = nullptr;
   cudaError_t e = cudaMemsetAsync(a.diag, 0, 32 * sizeof(double), L.stream);
+  if (e == cudaSuccess) e = launch_xbc<S, R>(L, a);
   if (e != cudaSuccess) return e;
   if (L.step & 1) return launch_cell_t<S, R, true, MODE_MACRO, true>(L, a);
   return launch_cell_t<S, R, false, MODE_MACRO, true>(L, a);
+}
+
+template <class S, class R>
+cudaError_t mark_xbc(Lattice &L, bool on) {
+  const int plane = L.ny * L.nz, T = 128;
+  k_mark_xbc<<<(2 * plane + T - 1) / T, T, 0, L.stream>>>(L.flags, L.nx, plane, on ? 1 : 0);
+  return cudaGetLastError();
 }
 
 template <class S, class R>
@@ -295,6 +324,7 @@ int batch_max_blocks_per_sm(int bx, int by) {
   template cudaError_t launch_macro<S, R>(Lattice &, bool);                      \
   template cudaError_t set_model<S, R>(Lattice &);                               \
   template int max_block_threads<S, R>();                                        \
-  template int auto_lz<S, R>(const Lattice &);
+  template int auto_lz<S, R>(const Lattice &);                                  \
+  template cudaError_t mark_xbc<S, R>(Lattice &, bool);
 
 }  // namespace pflb

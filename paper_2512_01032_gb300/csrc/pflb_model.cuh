@@ -81,6 +81,7 @@ enum {
 // Cell flags.
 constexpr uint8_t F_SOLID = 1;
 constexpr uint8_t F_WALL = 2;
+constexpr uint8_t F_BC = 4;  // fluid cell of an open x boundary plane (reading R22)
 
 // Model parameters in the compute precision R (derived constants included).
 template <class R>

@@ -27,6 +27,22 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NAN"
                 5: "ERR_TIMEOUT", 6: "ERR_BUDGET", 7: "ERR_STATE"}
 
 
+class XBC(C.Structure):
+    _fields_ = [("type", C.c_int), ("P", C.c_double), ("u", C.c_double * 3),
+                ("phi", C.c_double)]
+
+
+XBC_PRESSURE, XBC_VELOCITY = 1, 2
+
+
+def _xbc(b):
+    if b is None:
+        return None
+    t = {"pressure": XBC_PRESSURE, "velocity": XBC_VELOCITY}.get(b["type"], b["type"])
+    u = b.get("u", (0.0, 0.0, 0.0))
+    return XBC(int(t), float(b.get("P", 0.0)), (C.c_double * 3)(*u), float(b.get("phi", 0.0)))
+
+
 class DiagRaw(C.Structure):
     _fields_ = [("acc", C.c_double * 32), ("step", C.c_int64), ("err", C.c_int32),
                 ("pad", C.c_int32)]
@@ -147,6 +163,8 @@ def load(build_if_missing: bool = True):
     lib.pflb_last_diag_async.restype = st
     lib.pflb_diag_wait.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, _P(Diag)]
     lib.pflb_diag_wait.restype = st
+    lib.pflb_set_x_boundaries.argtypes = [C.c_void_p, _P(XBC), _P(XBC)]
+    lib.pflb_set_x_boundaries.restype = st
     lib.pflb_get_kernel.argtypes = [C.c_void_p, _P(C.c_int)]
     lib.pflb_get_kernel.restype = st
     lib.pflb_step.argtypes = [C.c_void_p, C.c_int64]
@@ -357,6 +375,13 @@ class Lattice:
         if not (allow_nan and s == ERR_NAN):
             _check(s)
         return d.as_dict()
+
+    def set_x_boundaries(self, lo=None, hi=None):
+        """Open x boundaries: lo / hi dicts with type ("pressure" or
+        "velocity"), P, u (3), phi; None for both restores periodic x."""
+        a, b = _xbc(lo), _xbc(hi)
+        _check(self._lib.pflb_set_x_boundaries(self._h, C.byref(a) if a else None,
+                                               C.byref(b) if b else None))
 
     def get_kernel(self) -> dict:
         out = (C.c_int * 4)()

@@ -67,7 +67,7 @@ def test_server_struct_layouts_match_header(tmp_path):
     mirrors."""
     import ctypes as C
     from paper_2512_01032_gb300 import pflb
-    structs = {"pflb_diag_raw_t": pflb.DiagRaw,
+    structs = {"pflb_diag_raw_t": pflb.DiagRaw, "pflb_xbc": pflb.XBC,
                "pflb_server_config": pflb.ServerConfig, "pflb_solve_spec": pflb.SolveSpec,
                "pflb_solve_result": pflb.SolveResult, "pflb_server_stats": pflb.ServerStats}
     lines = []
@@ -152,6 +152,7 @@ def test_create_rejects_bad_geometry():
     lib.pflb_server_destroy(None)
     assert lib.pflb_step_ex(None, 1, 0) == pflb.ERR_ARG
     assert lib.pflb_get_kernel(None, (C.c_int * 4)()) == pflb.ERR_ARG
+    assert lib.pflb_set_x_boundaries(None, None, None) == pflb.ERR_ARG
     raw = pflb.DiagRaw()
     assert lib.pflb_last_diag_async(None, C.byref(raw), C.byref(t)) == pflb.ERR_ARG
     assert lib.pflb_diag_wait(None, 0, C.byref(raw), C.byref(pflb.Diag())) == pflb.ERR_ARG
