@@ -170,14 +170,16 @@ __device__ __forceinline__ void boundary_cell(const Args<S, R> &a, int x, int y,
 // once its populations are gathered: h[] and g[] hold the streamed
 // populations, phi = sum h, val[1..18] the phi of the 18 neighbours
 // (anything for solid ones), lm/rec the wall data (0 for bulk cells).
-template <class S, class R, bool ODD, int MODE, bool DIAG>
+template <class S, class R, bool ODD, int MODE, bool DIAG, bool XBC = false>
 __device__ __forceinline__ void finish_cell(const Args<S, R> &a, int x, int y, int z, int c,
                                             uint8_t f, uint32_t lm, int rec, const Nbr &nb,
                                             R h[Q], R g[Q], R phi, R val[Q], DiagAcc<R> &acc) {
   const Model<R> &m = a.m;
-  if (f & F_BC) {
-    boundary_cell<S, R, ODD, MODE>(a, x, y, z, c, lm, rec, nb);
-    return;
+  if constexpr (XBC) {
+    if (f & F_BC) {
+      boundary_cell<S, R, ODD, MODE>(a, x, y, z, c, lm, rec, nb);
+      return;
+    }
   }
   val[0] = phi;
   R gx, gy, gz, lap;
@@ -299,7 +301,7 @@ __device__ __forceinline__ void store_cell(const Args<S, R> &a, int c, uint32_t 
 
 // Full update (or macro evaluation) of one fluid cell: wall data, g
 // gather, then finish_cell.
-template <class S, class R, bool ODD, int MODE, bool DIAG>
+template <class S, class R, bool ODD, int MODE, bool DIAG, bool XBC = false>
 __device__ __forceinline__ void update_cell(const Args<S, R> &a, int x, int y, int z, int c,
                                             uint8_t f, R h[Q], R phi, R val[Q],
                                             DiagAcc<R> &acc) {
@@ -313,7 +315,7 @@ __device__ __forceinline__ void update_cell(const Args<S, R> &a, int x, int y, i
   }
   R g[Q];
   gather_g<S, R, ODD>(a, c, lm, rec, nb, g);
-  finish_cell<S, R, ODD, MODE, DIAG>(a, x, y, z, c, f, lm, rec, nb, h, g, phi, val, acc);
+  finish_cell<S, R, ODD, MODE, DIAG, XBC>(a, x, y, z, c, f, lm, rec, nb, h, g, phi, val, acc);
 }
 
 // Diagnostics are reduced in three levels: each cell's contributions (a
@@ -429,11 +431,13 @@ __device__ __forceinline__ void diag_thread_flush(double *diag, const R *tacc,
 }
 
 // phi of one cell from the h buffer being read (0 for solid cells).
-template <class S, class R>
+template <class S, class R, bool XBC = false>
 __device__ __forceinline__ R cell_phi(const Args<S, R> &a, int c) {
   const uint8_t f = a.flags[c];
   if (f & F_SOLID) return R(0);
-  if (f & F_BC) return a.bcm[bc_index(a, c % a.nx, c / a.nx)];  // phi_b
+  if constexpr (XBC) {
+    if (f & F_BC) return a.bcm[bc_index(a, c % a.nx, c / a.nx)];  // phi_b
+  }
   R h[Q];
   ld_h_cell<S, R>(a.hin, c, h);
   R s = R(0);
@@ -450,15 +454,15 @@ __device__ __forceinline__ void zero_next_diag(const Args<S, R> &a) {
 
 // --------------------------------------------------------- two-pass path
 // Pass 1: phi field.
-template <class S, class R>
+template <class S, class R, bool XBC = false>
 __global__ void k_phi(const __grid_constant__ Args<S, R> a, R *phi_out) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= a.N) return;
-  phi_out[c] = cell_phi(a, c);
+  phi_out[c] = cell_phi<S, R, XBC>(a, c);
 }
 
 // Pass 2: one thread per cell, neighbour phi from the field.
-template <class S, class R, bool ODD, int MODE, bool DIAG>
+template <class S, class R, bool ODD, int MODE, bool DIAG, bool XBC = false>
 __global__ void __launch_bounds__(256) k_cell(const __grid_constant__ Args<S, R> a) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   zero_next_diag(a);
@@ -489,7 +493,7 @@ __global__ void __launch_bounds__(256) k_cell(const __grid_constant__ Args<S, R>
       for (int i = 0; i < Q; ++i) phi += h[i];
 #pragma unroll
       for (int i = 1; i < Q; ++i) val[i] = a.phi[c + nb.off(i)];
-      update_cell<S, R, ODD, MODE, DIAG>(a, x, y, z, c, f, h, phi, val, acc);
+      update_cell<S, R, ODD, MODE, DIAG, XBC>(a, x, y, z, c, f, h, phi, val, acc);
     }
   }
   if (DIAG) {
@@ -506,7 +510,7 @@ __global__ void __launch_bounds__(256) k_cell(const __grid_constant__ Args<S, R>
 // stored in HBM.  march_tile does one tile column [zb, ze) of lattice a;
 // sphi holds 3 (BX+2)(BY+2) values, tacc the per-thread diagnostic slots
 // (zeroed by the caller, each thread its own).
-template <class S, class R, bool ODD, bool DIAG>
+template <class S, class R, bool ODD, bool DIAG, bool XBC = false>
 __device__ __forceinline__ void march_tile(const Args<S, R> &a, int x0, int y0, int zb, int ze,
                                            int BX, int BY, R *sphi, R *tacc) {
   const int PW = BX + 2, PS = (BX + 2) * (BY + 2);
@@ -531,8 +535,8 @@ __device__ __forceinline__ void march_tile(const Args<S, R> &a, int x0, int y0, 
   auto plane = [&](int zu) {  // fill phi of (unwrapped) plane zu into its ring slot
     const int zw = ((zu % nz) + nz) % nz;
     R *dst = sphi + (((zu % 3) + 3) % 3) * PS;
-    if (active) dst[(ty + 1) * PW + tx + 1] = cell_phi(a, col + sz * zw);
-    if (rx >= 0) dst[ry * PW + rx] = cell_phi(a, rcol + sz * zw);
+    if (active) dst[(ty + 1) * PW + tx + 1] = cell_phi<S, R, XBC>(a, col + sz * zw);
+    if (rx >= 0) dst[ry * PW + rx] = cell_phi<S, R, XBC>(a, rcol + sz * zw);
   };
 
   plane(zb - 1);
@@ -558,7 +562,7 @@ __device__ __forceinline__ void march_tile(const Args<S, R> &a, int x0, int y0, 
           const R *pl = cz_of(i) == 0 ? p0 : (cz_of(i) > 0 ? pp : pm);
           val[i] = pl[o + cy_of(i) * PW + cx_of(i)];
         }
-        update_cell<S, R, ODD, MODE_STEP, DIAG>(a, gx, gy, z, c, f, h, phi, val, acc);
+        update_cell<S, R, ODD, MODE_STEP, DIAG, XBC>(a, gx, gy, z, c, f, h, phi, val, acc);
         if (DIAG) diag_thread_add(tacc, acc);
       }
     }
@@ -577,7 +581,7 @@ __host__ __device__ constexpr size_t fused_smem_bytes(int BX, int BY, bool diag)
   return fused_phi_bytes<R>(BX, BY) + (diag ? diag_thread_bytes<R>(BX * BY) : 0);
 }
 
-template <class S, class R, bool ODD, bool DIAG>
+template <class S, class R, bool ODD, bool DIAG, bool XBC = false>
 __global__ void __launch_bounds__(256, PFLB_MIN_BLOCKS)
     k_fused(const __grid_constant__ Args<S, R> a, int BX, int BY) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -587,7 +591,7 @@ __global__ void __launch_bounds__(256, PFLB_MIN_BLOCKS)
   __shared__ R wacc[DIAG_MAX_WARPS][32];
   if (DIAG) diag_thread_zero(tacc);
   const int zb = blockIdx.z * a.lz;
-  march_tile<S, R, ODD, DIAG>(a, blockIdx.x * BX, blockIdx.y * BY, zb, min(zb + a.lz, a.nz), BX,
+  march_tile<S, R, ODD, DIAG, XBC>(a, blockIdx.x * BX, blockIdx.y * BY, zb, min(zb + a.lz, a.nz), BX,
                               BY, sphi, tacc);
   if (DIAG) diag_thread_flush(a.diag, tacc, wacc);
 }

@@ -152,7 +152,10 @@ static cudaError_t launch_fused_t(Lattice &L, Args<S, R> &a) {
   const int bx = L.bx, by = L.by;
   dim3 grid((L.nx + bx - 1) / bx, (L.ny + by - 1) / by, (L.nz + L.lz - 1) / L.lz);
   const size_t smem = fused_smem_bytes<R>(bx, by, DIAG);
-  k_fused<S, R, ODD, DIAG><<<grid, bx * by, smem, L.stream>>>(a, bx, by);
+  if (L.bc_on)  // open x boundaries: the variant with boundary cells
+    k_fused<S, R, ODD, DIAG, true><<<grid, bx * by, smem, L.stream>>>(a, bx, by);
+  else
+    k_fused<S, R, ODD, DIAG, false><<<grid, bx * by, smem, L.stream>>>(a, bx, by);
   return cudaGetLastError();
 }
 
@@ -160,10 +163,16 @@ template <class S, class R, bool ODD, int MODE, bool DIAG>
 static cudaError_t launch_cell_t(Lattice &L, Args<S, R> &a) {
   const int T = 256;
   const long long B = (L.N + T - 1) / T;
-  k_phi<S, R><<<(unsigned)B, T, 0, L.stream>>>(a, (R *)L.phi);
+  if (L.bc_on)
+    k_phi<S, R, true><<<(unsigned)B, T, 0, L.stream>>>(a, (R *)L.phi);
+  else
+    k_phi<S, R, false><<<(unsigned)B, T, 0, L.stream>>>(a, (R *)L.phi);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_cell<S, R, ODD, MODE, DIAG><<<(unsigned)B, T, 0, L.stream>>>(a);
+  if (L.bc_on)
+    k_cell<S, R, ODD, MODE, DIAG, true><<<(unsigned)B, T, 0, L.stream>>>(a);
+  else
+    k_cell<S, R, ODD, MODE, DIAG, false><<<(unsigned)B, T, 0, L.stream>>>(a);
   return cudaGetLastError();
 }
 
