@@ -173,9 +173,41 @@ def cpu_baseline(g, p, drop, budget_s=15.0):
     L.step(k)
     dt = time.perf_counter() - t0
     fluid = int(g.N - g.solid.sum())
+    # one thread, on the same lattice, about a third of the budget
+    L.set_nthreads(1)
+    t0 = time.perf_counter()
+    L.step(1)
+    k1 = 1
+    while time.perf_counter() - t0 < budget_s / 3.0 and k1 < 50:
+        L.step(1)
+        k1 += 1
+    dt1 = time.perf_counter() - t0
     return {"value": fluid * k / dt / 1e6, "unit": "MLUPS", "cores": nthreads, "kind": "oracle",
+            "single_thread_value": fluid * k1 / dt1 / 1e6, "cpu_model": cpu_model(),
             "sample": f"{k} FP64 oracle steps of the full {g.nx}x{g.ny}x{g.nz} lattice "
-                      f"({dt:.1f} s on {nthreads} threads)"}
+                      f"({dt:.1f} s on {nthreads} threads); {k1} steps on one thread "
+                      f"({dt1:.1f} s)"}
+
+
+ARM_PARTS = {"0xd0c": "Arm Neoverse-N1", "0xd40": "Arm Neoverse-V1", "0xd49": "Arm Neoverse-N2",
+             "0xd4f": "Arm Neoverse-V2"}
+
+
+def cpu_model() -> str:
+    """Host CPU model name from /proc/cpuinfo (Arm: the part number, named
+    where known), or the platform."""
+    try:
+        for line in open("/proc/cpuinfo"):
+            k, _, v = line.partition(":")
+            k, v = k.strip(), v.strip()
+            if k in ("model name", "Model") and v:
+                return v
+            if k == "CPU part" and v:
+                return f"{ARM_PARTS.get(v, 'Arm')} (CPU part {v})"
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def main_reference(args):

@@ -122,3 +122,34 @@ def test_switching_boundaries_off_restores_periodic():
     B.set_x_boundaries(lo, hi)
     with pytest.raises(pflb.PflbError):
         pflb.Batch([B])
+
+
+def test_pressure_driven_channel_flow_on_gpu():
+    """Liquid between plates 32 cells apart, P = dP at x = 0 and 0 at
+    x = nx-1 (FP32, 96 x 34 x 1, 12000 steps, several viscous times): the
+    interior pressure gradient is dP / (nx - 1) within 3 %, the profile is
+    the plane Poiseuille parabola of the measured gradient within 2 %, and
+    every section carries the same flux."""
+    from paper_2512_01032_gb300 import pflb
+    nx, ny = 96, 34
+    H, mu = ny - 2, 1.0 / 6.0
+    solid = np.zeros((1, ny, nx), np.uint8)
+    solid[:, 0, :] = 1
+    solid[:, -1, :] = 1
+    L = pflb.Lattice(nx, ny, 1, solid=solid.reshape(-1), storage="fp32", sigma=0.01, W=4.0,
+                     M=0.02, rho_H=1.0, rho_L=1e-3, nu_H=mu, nu_L=0.1)
+    dP = 2e-3
+    L.set_x_boundaries(dict(type="pressure", P=dP), dict(type="pressure", P=0.0))
+    L.init_phi((1 - solid).reshape(-1).astype(float))
+    L.step(12000)
+    P = L.read("P").reshape(ny, nx)[1:-1].mean(axis=0)
+    ux = L.read("ux").reshape(ny, nx)
+    xs = np.arange(8, nx - 8)
+    G = -np.polyfit(xs, P[xs], 1)[0]
+    assert G == pytest.approx(dP / (nx - 1), rel=0.03)
+    y = np.arange(1, ny - 1)
+    want = G * (y - 0.5) * (H + 0.5 - y) / (2 * mu)
+    got = ux[1:-1, nx // 2]
+    assert np.max(np.abs(got - want)) < 0.02 * want.max()
+    flux = ux[1:-1, 4:-4].sum(axis=0)
+    assert np.ptp(flux) < 2e-3 * flux.mean()
