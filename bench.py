@@ -404,7 +404,7 @@ def main_serve(args):
         # the client's geometry (mask, normals, angles) is ready before the trace starts
         geo = dict(nx=g.nx, ny=g.ny, nz=g.nz, solid=g.solid, normals=g.normals(),
                    theta=g.theta())
-        prepared.append((geo, r["params"], synth.constriction_spec(r)))
+        prepared.append((geo, r["params"], synth.constriction_spec(r, drive=args.drive)))
     out = {}
     modes = [("batched", dict(storage="fp32", batched=True,
                               max_active_cells=args.max_cells)),
@@ -454,7 +454,7 @@ def main_serve(args):
                                    f"w in 48..96, beta ramp 0.7..1.3 every {args.ramp_every} "
                                    f"steps, at most {13 * args.ramp_every} steps",
                        "storage": "fp32", "budget_gb": args.budget_gb,
-                       "max_active_cells": args.max_cells,
+                       "max_active_cells": args.max_cells, "drive": args.drive,
                        "steps_per_tick": args.ramp_every // 2},
             "batched": out["batched"], "plain_sequential_fp32": out["plain"], **extra,
             "same_step_counts": same}
@@ -482,6 +482,9 @@ def main(argv=None):
                     help="lattices of the channels workload / requests of the serve workload")
     ap.add_argument("--ramp-every", type=int, default=500, help="serve: steps per beta level")
     ap.add_argument("--budget-gb", type=float, default=16.0, help="serve: HBM budget")
+    ap.add_argument("--drive", choices=["force", "pressure"], default="force",
+                    help="serve: ramp pressure as a body force (periodic) or as a pressure "
+                         "difference across open x boundaries")
     ap.add_argument("--max-cells", type=int, default=8 << 20,
                     help="serve: cap on resident cells of the batching server (0 = none)")
     args = ap.parse_args(argv)

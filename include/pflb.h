@@ -191,7 +191,8 @@ pflb_status pflb_set_kernel(pflb_lattice *L, int kind, int bx, int by, int lz);
  * links), and whatever streams into it is discarded.  Boundary cells carry
  * no diagnostics and read back their boundary state.  First-order accurate
  * (equilibrium boundary).  Lattices with open boundaries run the fused or
- * two-pass kernel (not the TMA one) and cannot join a batch. */
+ * two-pass kernel (not the TMA one); in a batch their boundary states are
+ * formed by one extra kernel per step (one block per such lattice). */
 enum { PFLB_XBC_PRESSURE = 1, PFLB_XBC_VELOCITY = 2 };
 typedef struct {
   int type;        /* PFLB_XBC_PRESSURE or PFLB_XBC_VELOCITY */
@@ -386,6 +387,10 @@ typedef struct {
   int region[6];           /* breakthrough box x0,x1,y0,y1,z0,z1 */
   double threshold;        /* breakthrough when region_mass > threshold */
   int keep_phi;            /* keep the final phi field for pflb_server_fetch_phi */
+  int drive;               /* 0: the ramp pressure as the body force above;
+                              1: as a pressure difference across open x boundaries,
+                              P = beta(t) p_ref at x = 0 and 0 at x = nx-1 (dir and
+                              length unused) */
 } pflb_solve_spec;
 
 enum { PFLB_REQ_QUEUED = 0, PFLB_REQ_RUNNING = 1, PFLB_REQ_DONE = 2, PFLB_REQ_FAILED = 3,

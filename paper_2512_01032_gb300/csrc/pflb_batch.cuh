@@ -24,7 +24,7 @@ __host__ __device__ constexpr size_t batch_smem(int BX, int BY, bool diag) {
   return fused_smem_bytes<R>(BX, BY, diag) + sizeof(Args<S, R>);
 }
 
-template <class S, class R, bool DIAG>
+template <class S, class R, bool DIAG, bool XBC = false>
 __global__ void __launch_bounds__(256, PFLB_MIN_BLOCKS)
     k_batch(const Args<S, R> *__restrict__ descs, const int *__restrict__ par0,
             const int4 *__restrict__ items, int nitems, int *counter, const int *bstep, int BX,
@@ -54,11 +54,30 @@ __global__ void __launch_bounds__(256, PFLB_MIN_BLOCKS)
       a.diag_zero[tid] = 0.0;
     const int ze = min(it.w + LZ, a.nz);
     if (p)
-      march_tile<S, R, true, DIAG>(a, it.y, it.z, it.w, ze, BX, BY, sphi, tacc);
+      march_tile<S, R, true, DIAG, XBC>(a, it.y, it.z, it.w, ze, BX, BY, sphi, tacc);
     else
-      march_tile<S, R, false, DIAG>(a, it.y, it.z, it.w, ze, BX, BY, sphi, tacc);
+      march_tile<S, R, false, DIAG, XBC>(a, it.y, it.z, it.w, ze, BX, BY, sphi, tacc);
     if (DIAG) diag_thread_flush(a.diag, tacc, wacc);
     __syncthreads();  // shared descriptor and phi ring are reused by the next item
+  }
+}
+
+// Boundary states of the open-boundary lattices of a batch (one block per
+// lattice in xlist), for the parity each lattice has at this batch step.
+template <class S, class R>
+__global__ void k_batch_xbc(const Args<S, R> *__restrict__ descs, const int *__restrict__ par0,
+                            const int *__restrict__ xlist, const XbcSpec *__restrict__ specs,
+                            const int *bstep) {
+  const int l = xlist[blockIdx.x];
+  const int p = (par0[l] + *bstep) & 1;
+  const Args<S, R> &a = descs[2 * l + p];
+  const XbcSpec &sp = specs[l];
+  const int n = 2 * a.ny * a.nz;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    if (p)
+      xbc_cell<S, R, true>(a, sp, a.bcm, j);
+    else
+      xbc_cell<S, R, false>(a, sp, a.bcm, j);
   }
 }
 

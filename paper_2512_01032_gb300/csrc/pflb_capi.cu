@@ -39,6 +39,7 @@ struct pflb_batch {
   bool own_stream = false;
   cudaEvent_t ev = nullptr;
   cudaGraphExec_t graph = nullptr;  // kGraphSteps plain steps
+  int graph_nxbc = -1;               // open-boundary lattice count the graph was captured for
   bool poisoned = false;
 };
 static constexpr int kGraphSteps = 16;
@@ -926,8 +927,6 @@ extern "C" pflb_status pflb_batch_create(pflb_lattice *const *lattices, int coun
     if (st != PFLB_OK) return st;
     if (lattices[l]->p.storage != lattices[0]->p.storage)
       return fail(PFLB_ERR_ARG, "all lattices of a batch need the same storage");
-    if (lattices[l]->bc_on)
-      return fail(PFLB_ERR_ARG, "lattices with open x boundaries cannot be batched");
     for (int k = 0; k < l; ++k)
       if (lattices[k] == lattices[l]) return fail(PFLB_ERR_ARG, "a lattice appears twice");
   }
@@ -955,6 +954,8 @@ extern "C" pflb_status pflb_batch_create(pflb_lattice *const *lattices, int coun
   if (e == cudaSuccess) e = cudaMalloc((void **)&b->dev.par0, count * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc((void **)&b->dev.counter, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc((void **)&b->dev.bstep, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&b->dev.xspecs, count * sizeof(pflb::XbcSpec));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&b->dev.xlist, count * sizeof(int));
   if (e != cudaSuccess) {
     pflb_batch_destroy(b);
     cudaGetLastError();
@@ -1003,6 +1004,25 @@ static pflb_status batch_run(pflb_batch *b, int64_t nsteps, bool diag_last) {
     return 0;
   });
   for (int l = 0; l < n; ++l) par[l] = (int)(b->lats[l]->step & 1);
+  // open x boundaries: specs of every lattice (type 0 = periodic) and the
+  // list of those that have them; the values may change between calls
+  std::vector<pflb::XbcSpec> specs(n);
+  std::vector<int> xlist;
+  for (int l = 0; l < n; ++l) {
+    const Lattice *L = b->lats[l];
+    for (int side = 0; side < 2; ++side) {
+      specs[l].type[side] = L->bc_on ? L->bc_type[side] : 0;
+      for (int k = 0; k < 5; ++k) specs[l].val[side][k] = L->bc_val[side][k];
+    }
+    if (L->bc_on) xlist.push_back(l);
+  }
+  b->dev.nxbc = (int)xlist.size();
+  if (b->dev.nxbc != b->graph_nxbc) batch_drop_graph(b);
+  BCK(b, cudaMemcpyAsync(b->dev.xspecs, specs.data(), n * sizeof(pflb::XbcSpec),
+                         cudaMemcpyHostToDevice, b->dev.stream));
+  if (!xlist.empty())
+    BCK(b, cudaMemcpyAsync(b->dev.xlist, xlist.data(), xlist.size() * sizeof(int),
+                           cudaMemcpyHostToDevice, b->dev.stream));
   BCK(b, cudaMemcpyAsync(b->dev.descs, host.data(), host.size(), cudaMemcpyHostToDevice,
                          b->dev.stream));
   BCK(b, cudaMemcpyAsync(b->dev.par0, par.data(), n * sizeof(int), cudaMemcpyHostToDevice,
@@ -1025,6 +1045,7 @@ static pflb_status batch_run(pflb_batch *b, int64_t nsteps, bool diag_last) {
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
     if (g) cudaGraphDestroy(g);
     if (e != cudaSuccess) return batch_fail(b, e, "graph capture");
+    b->graph_nxbc = b->dev.nxbc;
   }
   while (plain >= kGraphSteps) {
     BCK(b, cudaGraphLaunch(b->graph, b->dev.stream));
@@ -1094,7 +1115,8 @@ extern "C" void pflb_batch_destroy(pflb_batch *b) {
   if (!b) return;
   if (b->dev.stream) cudaStreamSynchronize(b->dev.stream);
   batch_drop_graph(b);
-  void *ptrs[] = {b->dev.descs, b->dev.par0, b->dev.items, b->dev.counter, b->dev.bstep};
+  void *ptrs[] = {b->dev.descs, b->dev.par0, b->dev.items, b->dev.counter, b->dev.bstep,
+                  b->dev.xspecs, b->dev.xlist};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (b->ev) cudaEventDestroy(b->ev);

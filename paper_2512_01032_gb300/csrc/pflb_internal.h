@@ -57,6 +57,12 @@ struct Lattice {
 };
 
 // Device side of a batch of lattices stepped by one persistent kernel.
+// Open x boundaries of one lattice as the boundary-state kernels take them.
+struct XbcSpec {
+  int type[2];        // 1 pressure (P given), 2 velocity (u and phi given); 0 closed
+  double val[2][5];   // P, ux, uy, uz, phi
+};
+
 struct BatchDev {
   void *descs = nullptr;   // [nlat][2] step descriptors (Args), both parities
   int *par0 = nullptr;     // [nlat] parity of each lattice at batch step 0
@@ -66,6 +72,9 @@ struct BatchDev {
   int *bstep = nullptr;    // batch steps since par0 was set
   int bx = 32, by = 4, lz = 16, grid = 0;
   cudaStream_t stream = nullptr;
+  XbcSpec *xspecs = nullptr;  // [nlat] open-boundary specs (type 0: periodic x)
+  int *xlist = nullptr;       // [nxbc] lattices with open boundaries
+  int nxbc = 0;
 };
 
 // Sets the thread-local message returned by pflb_last_error().

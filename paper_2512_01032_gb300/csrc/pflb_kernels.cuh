@@ -19,6 +19,7 @@
 // The 19 per-direction base pointers of each population array travel in the
 // kernel parameters (constant bank), so an access costs one multiply-add.
 #pragma once
+#include "pflb_internal.h"
 #include "pflb_model.cuh"
 
 namespace pflb {
@@ -51,7 +52,7 @@ struct Args {
   double *diag_zero; // [32] accumulator of the next diagnostic launch, zeroed here
   int reg[6];        // diagnostic box [x0,x1) x [y0,y1) x [z0,z1)
   double *out;       // macro outputs [6][N] (phi, rho, P, ux, uy, uz) or null
-  const R *bcm;      // open x boundaries: states [5][nbc] (phi, P, ux, uy, uz), or null
+  R *bcm;            // open x boundaries: states [5][nbc] (phi, P, ux, uy, uz), or null
   int nbc;           // 2 ny nz: plane x = 0, then plane x = nx-1
 };
 
@@ -603,17 +604,11 @@ __global__ void __launch_bounds__(256, PFLB_MIN_BLOCKS)
 // P = T sum g, rho u = sum c g + F/2), its g gathered exactly as that cell
 // will gather it.  One thread per cell of the two planes; no other kernel
 // runs meanwhile, so the reads cannot race the step's writes.
-struct XbcSpec {
-  int type[2];        // 1 pressure (P given), 2 velocity (u and phi given)
-  double val[2][5];   // P, ux, uy, uz, phi
-};
+// XbcSpec (types and given values of the two planes) is in pflb_internal.h.
 
 template <class S, class R, bool ODD>
-__global__ void k_xbc(const __grid_constant__ Args<S, R> a, const __grid_constant__ XbcSpec sp,
-                      R *bcm) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void xbc_cell(const Args<S, R> &a, const XbcSpec &sp, R *bcm, int j) {
   const int plane = a.ny * a.nz;
-  if (j >= 2 * plane) return;
   const int side = j >= plane, yz = j - side * plane;
   const int y = yz % a.ny, z = yz / a.ny;
   const int xa = side ? a.nx - 2 : 1;
@@ -662,6 +657,12 @@ __global__ void k_xbc(const __grid_constant__ Args<S, R> a, const __grid_constan
     bcm[3 * n + j] = (R)v[2];
     bcm[4 * n + j] = (R)v[3];
   }
+}
+
+template <class S, class R, bool ODD>
+__global__ void k_xbc(const __grid_constant__ Args<S, R> a, const __grid_constant__ XbcSpec sp) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < 2 * a.ny * a.nz) xbc_cell<S, R, ODD>(a, sp, a.bcm, j);
 }
 
 // Sets (on) or clears (off) the boundary flag of the fluid cells of the

@@ -72,7 +72,7 @@ static Args<S, R> make_args(Lattice &L) {
   a.diag_zero = nullptr;
   for (int k = 0; k < 6; ++k) a.reg[k] = L.reg[k];
   a.out = nullptr;
-  a.bcm = L.bc_on ? (const R *)L.bcm : nullptr;
+  a.bcm = L.bc_on ? (R *)L.bcm : nullptr;
   a.nbc = 2 * L.ny * L.nz;
   return a;
 }
@@ -82,15 +82,15 @@ template <class S, class R>
 static cudaError_t launch_xbc(Lattice &L, const Args<S, R> &a) {
   if (!L.bc_on) return cudaSuccess;
   XbcSpec sp;
-  for (int s = 0; s < 2; ++s) {
-    sp.type[s] = L.bc_type[s];
-    for (int k = 0; k < 5; ++k) sp.val[s][k] = L.bc_val[s][k];
+  for (int side = 0; side < 2; ++side) {
+    sp.type[side] = L.bc_type[side];
+    for (int k = 0; k < 5; ++k) sp.val[side][k] = L.bc_val[side][k];
   }
   const int n = 2 * L.ny * L.nz, T = 128;
   if (L.step & 1)
-    k_xbc<S, R, true><<<(n + T - 1) / T, T, 0, L.stream>>>(a, sp, (R *)L.bcm);
+    k_xbc<S, R, true><<<(n + T - 1) / T, T, 0, L.stream>>>(a, sp);
   else
-    k_xbc<S, R, false><<<(n + T - 1) / T, T, 0, L.stream>>>(a, sp, (R *)L.bcm);
+    k_xbc<S, R, false><<<(n + T - 1) / T, T, 0, L.stream>>>(a, sp);
   return cudaGetLastError();
 }
 
@@ -298,14 +298,27 @@ cudaError_t batch_launch_step(const BatchDev &b, bool diag) {
   const size_t smem = batch_smem<S, R>(b.bx, b.by, diag);
   const Args<S, R> *d = (const Args<S, R> *)b.descs;
   const int4 *it = (const int4 *)b.items;
-  if (diag)
-    k_batch<S, R, true><<<b.grid, b.bx * b.by, smem, b.stream>>>(d, b.par0, it, b.nitems,
+  if (b.nxbc > 0) {  // boundary states of the open-boundary lattices first
+    k_batch_xbc<S, R><<<b.nxbc, 128, 0, b.stream>>>(d, b.par0, b.xlist, b.xspecs, b.bstep);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  const dim3 grid(b.grid), block(b.bx * b.by);
+  if (diag && b.nxbc > 0)
+    k_batch<S, R, true, true><<<grid, block, smem, b.stream>>>(d, b.par0, it, b.nitems, b.counter,
+                                                               b.bstep, b.bx, b.by, b.lz);
+  else if (diag)
+    k_batch<S, R, true, false><<<grid, block, smem, b.stream>>>(d, b.par0, it, b.nitems,
+                                                                b.counter, b.bstep, b.bx, b.by,
+                                                                b.lz);
+  else if (b.nxbc > 0)
+    k_batch<S, R, false, true><<<grid, block, smem, b.stream>>>(d, b.par0, it, b.nitems,
+                                                                b.counter, b.bstep, b.bx, b.by,
+                                                                b.lz);
+  else
+    k_batch<S, R, false, false><<<grid, block, smem, b.stream>>>(d, b.par0, it, b.nitems,
                                                                  b.counter, b.bstep, b.bx, b.by,
                                                                  b.lz);
-  else
-    k_batch<S, R, false><<<b.grid, b.bx * b.by, smem, b.stream>>>(d, b.par0, it, b.nitems,
-                                                                  b.counter, b.bstep, b.bx,
-                                                                  b.by, b.lz);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_batch_tick<<<1, 1, 0, b.stream>>>(b.bstep);

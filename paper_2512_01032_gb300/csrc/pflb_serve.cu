@@ -131,6 +131,8 @@ extern "C" pflb_status pflb_server_submit(pflb_server *s, const pflb_geometry *g
                                "steps_per_tick");
   if (!(spec->length > 0) || !std::isfinite(spec->p_ref))
     return sfail(PFLB_ERR_ARG, "need length > 0 and a finite p_ref");
+  if (spec->drive != 0 && spec->drive != 1) return sfail(PFLB_ERR_ARG, "drive must be 0 or 1");
+  if (spec->drive == 1 && geom->nx < 3) return sfail(PFLB_ERR_ARG, "pressure drive needs nx >= 3");
   if (params->storage != s->cfg.storage)
     return sfail(PFLB_ERR_ARG, "request storage differs from the server's");
   if (geom->nx < 1 || geom->ny < 1 || geom->nz < 1) return sfail(PFLB_ERR_ARG, "bad dimensions");
@@ -186,6 +188,15 @@ static void retire(pflb_server *s, Request *r, int state) {
   std::vector<double>().swap(r->theta);
 }
 
+// Pressure drive: P = beta p_ref at the inlet plane, 0 at the outlet plane.
+static pflb_status set_drive_boundaries(Request *r, int64_t step) {
+  pflb_xbc in{}, out{};
+  in.type = out.type = PFLB_XBC_PRESSURE;
+  in.P = r->beta_at(step) * r->spec.p_ref;
+  out.P = 0.0;
+  return pflb_set_x_boundaries(r->L, &in, &out);
+}
+
 static pflb_status admit(pflb_server *s) {
   while (!s->queue.empty()) {
     Request *r = s->queue.front();
@@ -202,6 +213,7 @@ static pflb_status admit(pflb_server *s) {
       st = pflb_init_tanh(r->L, r->spec.init_shape, r->spec.center, r->spec.R, r->spec.normal,
                           0.0);
     if (st == PFLB_OK) st = pflb_set_region(r->L, r->spec.region);
+    if (st == PFLB_OK && r->spec.drive == 1) st = set_drive_boundaries(r, 0);
     if (st != PFLB_OK) {
       // the request cannot run (e.g. its parameters are invalid): fail it,
       // keep serving the others
@@ -232,6 +244,11 @@ extern "C" pflb_status pflb_server_tick(pflb_server *s, int *n_active) {
   std::vector<Request *> stepped = s->active;
   if (!stepped.empty()) {
     for (Request *r : stepped) {
+      if (r->spec.drive == 1) {
+        if (set_drive_boundaries(r, r->res.steps) != PFLB_OK)
+          return server_poison(s, std::string("boundaries: ") + pflb_last_error());
+        continue;
+      }
       const double F = r->beta_at(r->res.steps) * r->spec.p_ref / r->spec.length;
       const double f[3] = {F * r->spec.dir[0], F * r->spec.dir[1], F * r->spec.dir[2]};
       if (pflb_set_force(r->L, f) != PFLB_OK) return server_poison(s, "set_force failed");

@@ -59,7 +59,8 @@ class SolveSpec(C.Structure):
                 ("normal", C.c_double * 3), ("p_ref", C.c_double), ("length", C.c_double),
                 ("dir", C.c_double * 3), ("beta0", C.c_double), ("dbeta", C.c_double),
                 ("beta_max", C.c_double), ("ramp_every", C.c_int64), ("max_steps", C.c_int64),
-                ("region", C.c_int * 6), ("threshold", C.c_double), ("keep_phi", C.c_int)]
+                ("region", C.c_int * 6), ("threshold", C.c_double), ("keep_phi", C.c_int),
+                ("drive", C.c_int)]
 
 
 class SolveResult(C.Structure):

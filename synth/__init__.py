@@ -315,14 +315,16 @@ def constriction_request(req: dict, ramp_every=2000, max_steps=26000):
                 max_steps=max_steps, region=region, threshold=0.5 * d * d)
 
 
-def constriction_spec(r: dict, keep_phi=False) -> dict:
-    """The pflb_solve_spec fields of a constriction_request."""
+def constriction_spec(r: dict, keep_phi=False, drive="force") -> dict:
+    """The pflb_solve_spec fields of a constriction_request; drive "force"
+    applies the ramp pressure as a body force over the periodic length,
+    "pressure" as the pressure difference across open x boundaries."""
     i = r["init"]
     return dict(init_shape=i["shape"], center=i["center"], R=i["R"], normal=i["normal"],
                 p_ref=r["p_crit"], length=r["length"], dir=(1.0, 0.0, 0.0), beta0=r["beta0"],
                 dbeta=r["dbeta"], beta_max=r["beta_max"], ramp_every=r["ramp_every"],
                 max_steps=r["max_steps"], region=r["region"], threshold=r["threshold"],
-                keep_phi=1 if keep_phi else 0)
+                keep_phi=1 if keep_phi else 0, drive={"force": 0, "pressure": 1}[drive])
 
 
 def serving_trace(count=200, rate=20.0, seed=2512010321):

@@ -119,9 +119,53 @@ def test_switching_boundaries_off_restores_periodic():
         assert np.array_equal(A.read(k), B.read(k)), k
     with pytest.raises(pflb.PflbError):
         B.set_x_boundaries(lo, None)
-    B.set_x_boundaries(lo, hi)
-    with pytest.raises(pflb.PflbError):
-        pflb.Batch([B])
+
+
+def _gpu(case, storage="fp64"):
+    from paper_2512_01032_gb300 import pflb
+    (nx, ny, nz), solid, nrm, th, p, phi0, lo, hi, _ = case
+    G = pflb.Lattice(nx, ny, nz, solid=solid, wall_normal=nrm, theta_cells=th, storage=storage,
+                     **p)
+    if lo is not None:
+        G.set_x_boundaries(lo, hi)
+    G.init_phi(phi0)
+    return G
+
+
+def _droplet_case():
+    g, p, init = synth.static_droplet(24, 6.0)
+    phi0 = O.tanh_phi(0, (24, 24, 24), init["center"], 6.0, 4.0)
+    return (24, 24, 24), None, None, None, p, phi0, None, None, 1.0
+
+
+def test_batch_with_open_boundaries():
+    """Open-boundary lattices (gas channel, pushed slab) and a periodic one in
+    one batch: each bitwise equal to the same lattice in a batch of its own,
+    and within the FP64 parity bars of the single-lattice kernel, over 37
+    steps (two graph replays of 16 steps, then single launches)."""
+    from paper_2512_01032_gb300 import pflb
+    cases = [_poiseuille(), _slab_pushed(), _droplet_case()]
+    mixed = [_gpu(c) for c in cases]
+    ones = [_gpu(c) for c in cases]
+    alone = [_gpu(c) for c in cases]
+    mixed[1].step(1)  # start one lattice at odd A-A parity
+    ones[1].step(1)
+    alone[1].step(1)
+    B = pflb.Batch(mixed)
+    B.step(37)
+    for L in ones:
+        b1 = pflb.Batch([L])
+        b1.step(37)
+        b1.close()
+    for L in alone:
+        L.step(37)
+    for M, A1, A in zip(mixed, ones, alone):
+        for k in ("phi", "P", "ux", "uy", "uz"):
+            m, o, a = M.read(k), A1.read(k), A.read(k)
+            assert np.array_equal(m, o), k
+            tol = 1e-12 if k.startswith("u") else 1e-11 * max(np.max(np.abs(a)), 1e-3)
+            assert np.max(np.abs(m - a)) <= tol, (k, np.max(np.abs(m - a)))
+    B.close()
 
 
 def test_pressure_driven_channel_flow_on_gpu():

@@ -21,10 +21,10 @@ def _requests(count=4):
     return reqs
 
 
-def _submit(S, r, keep_phi=True, **override):
+def _submit(S, r, keep_phi=True, drive="force", **override):
     g = r["geometry"]
     p = dict(r["params"], **override)
-    return S.submit(g.nx, g.ny, g.nz, synth.constriction_spec(r, keep_phi), solid=g.solid,
+    return S.submit(g.nx, g.ny, g.nz, synth.constriction_spec(r, keep_phi, drive), solid=g.solid,
                     wall_normal=g.normals(), theta_cells=g.theta(), **p)
 
 
@@ -35,10 +35,10 @@ def _drain(S, limit=10000):
     raise AssertionError("server did not drain")
 
 
-def _serve(reqs, **cfg):
+def _serve(reqs, drive="force", **cfg):
     from paper_2512_01032_gb300 import pflb
     S = pflb.Server(steps_per_tick=TICK, **cfg)
-    tickets = [_submit(S, r) for r in reqs]
+    tickets = [_submit(S, r, drive=drive) for r in reqs]
     _drain(S)
     out = [(S.poll(t), S.fetch_phi(t)) for t in tickets]
     st = S.stats()
@@ -129,3 +129,21 @@ def test_plain_sequential_matches_batched():
     for (rp, pp), (rb, pb) in zip(plain, batched):
         assert rp["steps"] == rb["steps"]
         assert np.max(np.abs(pp - pb)) < 1e-4
+
+
+def test_pressure_drive_alone_equals_mixed():
+    """Requests driven by a pressure difference across open x boundaries
+    (inlet P = beta p_ref, outlet 0) give bitwise the same result alone and
+    in a mix, and the same steps as served one at a time by the plain server
+    (whose fields agree to FP32 rounding)."""
+    from paper_2512_01032_gb300 import pflb
+    reqs = _requests(3)
+    alone = [_serve([r], drive="pressure", storage="fp32")[0][0] for r in reqs]
+    mixed, st = _serve(reqs, drive="pressure", storage="fp32")
+    plain, _ = _serve(reqs, drive="pressure", storage="fp32", batched=False, max_active=1)
+    assert st["completed"] == len(reqs)
+    for (ra, pa), (rm, pm), (rp, pp) in zip(alone, mixed, plain):
+        assert rm["state"] == pflb.REQ_DONE
+        assert rm["steps"] == ra["steps"] == rp["steps"] and rm["beta"] == ra["beta"]
+        assert np.array_equal(pa, pm) and np.isfinite(pa).all()
+        assert np.max(np.abs(pp - pm)) < 1e-4
