@@ -62,8 +62,9 @@ __global__ void __launch_bounds__(256, PFLB_MIN_BLOCKS)
   }
 }
 
-// Boundary states of the open-boundary lattices of a batch (one block per
-// lattice in xlist), for the parity each lattice has at this batch step.
+// Boundary states of the open-boundary lattices of a batch (blockIdx.x:
+// lattice in xlist; blockIdx.y: a strided share of its boundary cells), for
+// the parity each lattice has at this batch step.
 template <class S, class R>
 __global__ void k_batch_xbc(const Args<S, R> *__restrict__ descs, const int *__restrict__ par0,
                             const int *__restrict__ xlist, const XbcSpec *__restrict__ specs,
@@ -73,7 +74,8 @@ __global__ void k_batch_xbc(const Args<S, R> *__restrict__ descs, const int *__r
   const Args<S, R> &a = descs[2 * l + p];
   const XbcSpec &sp = specs[l];
   const int n = 2 * a.ny * a.nz;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+  const int stride = blockDim.x * gridDim.y;
+  for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < n; j += stride) {
     if (p)
       xbc_cell<S, R, true>(a, sp, a.bcm, j);
     else

@@ -299,7 +299,8 @@ cudaError_t batch_launch_step(const BatchDev &b, bool diag) {
   const Args<S, R> *d = (const Args<S, R> *)b.descs;
   const int4 *it = (const int4 *)b.items;
   if (b.nxbc > 0) {  // boundary states of the open-boundary lattices first
-    k_batch_xbc<S, R><<<b.nxbc, 128, 0, b.stream>>>(d, b.par0, b.xlist, b.xspecs, b.bstep);
+    k_batch_xbc<S, R><<<dim3(b.nxbc, 32), 128, 0, b.stream>>>(d, b.par0, b.xlist, b.xspecs,
+                                                              b.bstep);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
