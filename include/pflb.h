@@ -199,6 +199,10 @@ typedef struct {
   double P;        /* pressure (pressure boundary) */
   double u[3];     /* velocity (velocity boundary) */
   double phi;      /* order parameter (velocity boundary) */
+  int64_t ramp_steps; /* > 0: the given values are reached linearly over this many
+                         steps from those in effect at the call (the rest state,
+                         P = 0 and u = 0, when the boundaries were off); a function
+                         of the step counter, so reads do not advance it */
 } pflb_xbc;
 
 pflb_status pflb_set_x_boundaries(pflb_lattice *L, const pflb_xbc *lo, const pflb_xbc *hi);
@@ -390,7 +394,8 @@ typedef struct {
   int drive;               /* 0: the ramp pressure as the body force above;
                               1: as a pressure difference across open x boundaries,
                               P = beta(t) p_ref at x = 0 and 0 at x = nx-1 (dir and
-                              length unused) */
+                              length unused), each change ramped over one tick
+                              (from rest at admission) */
 } pflb_solve_spec;
 
 enum { PFLB_REQ_QUEUED = 0, PFLB_REQ_RUNNING = 1, PFLB_REQ_DONE = 2, PFLB_REQ_FAILED = 3,

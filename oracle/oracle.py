@@ -76,7 +76,7 @@ def _load():
         lib.orc_update_ghosts_only.argtypes = [C.c_void_p]
         lib.orc_set_nthreads.argtypes = [C.c_void_p, C.c_int]
         lib.orc_set_force.argtypes = [C.c_void_p, _d]
-        lib.orc_set_x_boundaries.argtypes = [C.c_void_p, C.c_int, _d, C.c_int, _d]
+        lib.orc_set_x_boundaries.argtypes = [C.c_void_p, C.c_int, _d, C.c_int, _d, C.c_int64]
         lib.orc_set_x_boundaries.restype = C.c_int
         lib.orc_lattice_tables.argtypes = [_P(C.c_int), _P(C.c_int), _P(C.c_int), _d, _P(C.c_int)]
         lib.orc_max_threads.restype = C.c_int
@@ -289,10 +289,11 @@ class OracleLattice:
         f = _f64(F)
         self._lib.orc_set_force(self._h, _ptr(f))
 
-    def set_x_boundaries(self, lo=None, hi=None):
+    def set_x_boundaries(self, lo=None, hi=None, ramp_steps=0):
         """Open x boundaries (reading R22): lo / hi are dicts with type
         ("pressure" or "velocity"), P, u (3) and phi; None for both restores
-        periodic x."""
+        periodic x.  ramp_steps > 0 reaches the given values linearly from
+        those in effect (the rest state when the boundaries were off)."""
         kinds = {None: 0, "pressure": 1, "velocity": 2}
 
         def pack(b):
@@ -303,7 +304,8 @@ class OracleLattice:
 
         tl, vl = pack(lo)
         th, vh = pack(hi)
-        if self._lib.orc_set_x_boundaries(self._h, tl, _ptr(vl), th, _ptr(vh)) != 0:
+        if self._lib.orc_set_x_boundaries(self._h, tl, _ptr(vl), th, _ptr(vh),
+                                          int(ramp_steps)) != 0:
             raise ValueError("bad open-boundary request")
 
     def macros(self):

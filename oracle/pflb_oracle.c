@@ -57,7 +57,9 @@
  *       g_i = w_i P_b / T + rho_b (Gamma_i(u_b) - w_i), streamed as usual
  *       (bounce-back at solid links, no free-slip band, no ghost update).
  *       What streams into a boundary cell (including the periodic wrap
- *       between the two planes) is discarded.
+ *       between the two planes) is discarded.  Given values may be ramped
+ *       linearly over a number of steps from those in effect (the rest
+ *       state P = 0, u = 0 when the boundaries were off).
  *
  * Parity unpinned by the paper (pinned only oracle <-> GPU): the sub-step
  * order (R3), the ghost lag (R11), the blend side (R12) and the free-slip
@@ -115,7 +117,9 @@ typedef struct {
     double *ghost;    /* [N*Q] phi_{s,i} of wall node x for solid link i */
     double *ghost_old;/* [N*Q] scratch: ghosts of the previous step */
     int bc_type[2];   /* x = 0, x = nx-1: 0 periodic, 1 pressure, 2 velocity (R22) */
-    double bc_val[2][5]; /* given P, ux, uy, uz, phi */
+    double bc_val[2][5]; /* given P, ux, uy, uz, phi (targets) */
+    double bc_from[2][5];/* values at the start of the ramp */
+    int64_t bc_t0, bc_ramp; /* ramp start step and length (0: targets at once) */
     double *bstate;   /* [2*ny*nz*5] boundary states phi, P, ux, uy, uz */
     int64_t step;
 } orc_lattice;
@@ -450,6 +454,14 @@ void orc_init_phi(orc_lattice *L, const double *phi0, double P0) {
 
 /* --------------------------------------------------- open boundaries (R22) */
 
+/* Given boundary value k (P, ux, uy, uz, phi) of side s at step t: linear
+ * from bc_from at step bc_t0 to bc_val at step bc_t0 + bc_ramp. */
+static double bc_value(const orc_lattice *L, int s, int k, int64_t t) {
+    if (L->bc_ramp <= 0 || t >= L->bc_t0 + L->bc_ramp) return L->bc_val[s][k];
+    double f = t <= L->bc_t0 ? 0.0 : (double)(t - L->bc_t0) / (double)L->bc_ramp;
+    return L->bc_from[s][k] + f * (L->bc_val[s][k] - L->bc_from[s][k]);
+}
+
 static inline int bc_side(const orc_lattice *L, int64_t c) {
     if (!L->bc_type[0] || L->solid[c]) return -1;
     int64_t x = c % L->nx;
@@ -467,7 +479,8 @@ static void boundary_states(orc_lattice *L) {
             int64_t yz = j * L->nx;                 /* y + ny z, times nx */
             int64_t cb = xb + yz, ca = xa + yz;
             double *st = L->bstate + (side * plane + j) * 5;
-            const double *v = L->bc_val[side];
+            double v[5];
+            for (int k = 0; k < 5; ++k) v[k] = bc_value(L, side, k, L->step);
             double phia = 0, Pa = 0, ua[3] = {0, 0, 0};
             if (!L->solid[ca]) {
                 const double *g = L->g + ca * Q;
@@ -676,16 +689,28 @@ void orc_set_nthreads(orc_lattice *L, int n) { L->p.nthreads = n > 0 ? n : 1; }
 /* Open x boundaries (R22): types 0 (both: periodic), 1 pressure, 2 velocity;
  * values P, ux, uy, uz, phi per side.  Returns 0, or -1 for a bad request. */
 int orc_set_x_boundaries(orc_lattice *L, int type_lo, const double *val_lo, int type_hi,
-                         const double *val_hi) {
+                         const double *val_hi, int64_t ramp) {
     if ((type_lo == 0) != (type_hi == 0) || type_lo < 0 || type_lo > 2 || type_hi < 0 ||
-        type_hi > 2 || (type_lo && (L->nx < 3 || !val_lo || !val_hi)))
+        type_hi > 2 || ramp < 0 || (type_lo && (L->nx < 3 || !val_lo || !val_hi)))
         return -1;
-    L->bc_type[0] = type_lo;
-    L->bc_type[1] = type_hi;
-    for (int k = 0; k < 5; ++k) {
-        L->bc_val[0][k] = type_lo ? val_lo[k] : 0.0;
-        L->bc_val[1][k] = type_hi ? val_hi[k] : 0.0;
+    /* ramp start: the values in effect now for an unchanged type, else the
+     * rest state (P = 0, u = 0, phi at its target) */
+    const int type[2] = {type_lo, type_hi};
+    const double *val[2] = {val_lo, val_hi};
+    double from[2][5];
+    for (int s = 0; s < 2; ++s)
+        for (int k = 0; k < 5; ++k)
+            from[s][k] = (L->bc_type[s] && L->bc_type[s] == type[s]) ? bc_value(L, s, k, L->step)
+                         : (k < 4 ? 0.0 : (type[s] ? val[s][4] : 0.0));
+    for (int s = 0; s < 2; ++s) {
+        L->bc_type[s] = type[s];
+        for (int k = 0; k < 5; ++k) {
+            L->bc_val[s][k] = type[s] ? val[s][k] : 0.0;
+            L->bc_from[s][k] = from[s][k];
+        }
     }
+    L->bc_t0 = L->step;
+    L->bc_ramp = ramp;
     if (type_lo && !L->bstate)
         L->bstate = (double *)calloc((size_t)2 * L->ny * L->nz * 5, sizeof(double));
     return 0;

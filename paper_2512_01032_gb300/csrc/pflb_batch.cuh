@@ -77,9 +77,9 @@ __global__ void k_batch_xbc(const Args<S, R> *__restrict__ descs, const int *__r
   const int stride = blockDim.x * gridDim.y;
   for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < n; j += stride) {
     if (p)
-      xbc_cell<S, R, true>(a, sp, a.bcm, j);
+      xbc_cell<S, R, true>(a, sp, a.bcm, j, sp.step0 + *bstep);
     else
-      xbc_cell<S, R, false>(a, sp, a.bcm, j);
+      xbc_cell<S, R, false>(a, sp, a.bcm, j, sp.step0 + *bstep);
   }
 }
 

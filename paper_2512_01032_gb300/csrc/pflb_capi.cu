@@ -590,12 +590,23 @@ pflb_status pflb_set_x_boundaries(pflb_lattice *L, const pflb_xbc *lo, const pfl
       }
       L->dev_bytes += (int64_t)bytes;
     }
+    if (lo->ramp_steps < 0 || hi->ramp_steps < 0 || lo->ramp_steps != hi->ramp_steps)
+      return fail(PFLB_ERR_ARG, "ramp_steps must be >= 0 and the same on both planes");
+    // ramp start values: those in effect now (same boundary type), else the
+    // rest state (P = 0, u = 0; phi at its target)
+    const pflb::XbcSpec cur = pflb::xbc_spec(*L, L->step);
     const pflb_xbc *bs[2] = {lo, hi};
     for (int k = 0; k < 2; ++k) {
-      L->bc_type[k] = bs[k]->type;
       const double v[5] = {bs[k]->P, bs[k]->u[0], bs[k]->u[1], bs[k]->u[2], bs[k]->phi};
-      for (int q = 0; q < 5; ++q) L->bc_val[k][q] = v[q];
+      const bool same = L->bc_on && L->bc_type[k] == bs[k]->type;
+      for (int q = 0; q < 5; ++q) {
+        L->bc_from[k][q] = same ? pflb::xbc_value(cur, k, q, L->step) : (q < 4 ? 0.0 : v[4]);
+        L->bc_val[k][q] = v[q];
+      }
+      L->bc_type[k] = bs[k]->type;
     }
+    L->bc_t0 = L->step;
+    L->bc_ramp = lo->ramp_steps;
   }
   if (on != L->bc_on) {
     CK(L, dispatch(L, [&](auto *s_, auto *r_) {
@@ -1010,10 +1021,7 @@ static pflb_status batch_run(pflb_batch *b, int64_t nsteps, bool diag_last) {
   std::vector<int> xlist;
   for (int l = 0; l < n; ++l) {
     const Lattice *L = b->lats[l];
-    for (int side = 0; side < 2; ++side) {
-      specs[l].type[side] = L->bc_on ? L->bc_type[side] : 0;
-      for (int k = 0; k < 5; ++k) specs[l].val[side][k] = L->bc_val[side][k];
-    }
+    specs[l] = pflb::xbc_spec(*L, L->step);
     if (L->bc_on) xlist.push_back(l);
   }
   b->dev.nxbc = (int)xlist.size();

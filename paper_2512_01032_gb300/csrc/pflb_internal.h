@@ -49,7 +49,9 @@ struct Lattice {
   // open x boundaries (reading R22)
   bool bc_on = false;
   int bc_type[2] = {0, 0};         // 1 pressure, 2 velocity
-  double bc_val[2][5] = {};        // P, ux, uy, uz, phi
+  double bc_val[2][5] = {};        // P, ux, uy, uz, phi (targets)
+  double bc_from[2][5] = {};       // values at the start of the ramp
+  int64_t bc_t0 = 0, bc_ramp = 0;  // ramp start step and length
   void *bcm = nullptr;             // [5][2 ny nz] boundary states, compute type
   int reg[6] = {0, 0, 0, 0, 0, 0};
   bool poisoned = false;
@@ -60,7 +62,11 @@ struct Lattice {
 // Open x boundaries of one lattice as the boundary-state kernels take them.
 struct XbcSpec {
   int type[2];        // 1 pressure (P given), 2 velocity (u and phi given); 0 closed
-  double val[2][5];   // P, ux, uy, uz, phi
+  double val[2][5];   // P, ux, uy, uz, phi (targets)
+  double from[2][5];  // values at the start of the ramp
+  long long t0;       // step at which the ramp started
+  long long ramp;     // ramp length in steps (0: targets at once)
+  long long step0;    // step of the launch (batches add the batch step)
 };
 
 struct BatchDev {
@@ -82,6 +88,30 @@ void set_last_error(const char *msg);
 
 // Per-precision launchers (pflb_launch.cuh, instantiated per storage type).
 // All enqueue work on L.stream; none synchronises.
+// Given boundary value k (P, ux, uy, uz, phi) of side s at step t: linear
+// ramp from `from` (at step t0) to `val` (at step t0 + ramp).
+__host__ __device__ inline double xbc_value(const XbcSpec &sp, int s, int k, long long t) {
+  if (sp.ramp <= 0 || t >= sp.t0 + sp.ramp) return sp.val[s][k];
+  const double f = t <= sp.t0 ? 0.0 : (double)(t - sp.t0) / (double)sp.ramp;
+  return sp.from[s][k] + f * (sp.val[s][k] - sp.from[s][k]);
+}
+
+// The open-boundary spec of a lattice for launches starting at step step0.
+inline XbcSpec xbc_spec(const Lattice &L, long long step0) {
+  XbcSpec sp;
+  for (int side = 0; side < 2; ++side) {
+    sp.type[side] = L.bc_on ? L.bc_type[side] : 0;
+    for (int k = 0; k < 5; ++k) {
+      sp.val[side][k] = L.bc_val[side][k];
+      sp.from[side][k] = L.bc_from[side][k];
+    }
+  }
+  sp.t0 = L.bc_t0;
+  sp.ramp = L.bc_ramp;
+  sp.step0 = step0;
+  return sp;
+}
+
 template <class S, class R> cudaError_t launch_init(Lattice &L, const double *d_phi0, double P0);
 template <class S, class R> cudaError_t launch_step(Lattice &L, bool diag);
 template <class S, class R> cudaError_t launch_macro(Lattice &L, bool fields);

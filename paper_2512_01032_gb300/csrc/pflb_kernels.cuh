@@ -607,7 +607,8 @@ __global__ void __launch_bounds__(256, PFLB_MIN_BLOCKS)
 // XbcSpec (types and given values of the two planes) is in pflb_internal.h.
 
 template <class S, class R, bool ODD>
-__device__ __forceinline__ void xbc_cell(const Args<S, R> &a, const XbcSpec &sp, R *bcm, int j) {
+__device__ __forceinline__ void xbc_cell(const Args<S, R> &a, const XbcSpec &sp, R *bcm, int j,
+                                         long long t) {
   const int plane = a.ny * a.nz;
   const int side = j >= plane, yz = j - side * plane;
   const int y = yz % a.ny, z = yz / a.ny;
@@ -642,27 +643,26 @@ __device__ __forceinline__ void xbc_cell(const Args<S, R> &a, const XbcSpec &sp,
     ua[2] = (m2 + R(0.5) * a.m.Fz) / rho;
     Pa = s0 / R(3);
   }
-  const double *v = sp.val[side];
   const int n = 2 * plane;
   if (sp.type[side] == 1) {
     bcm[j] = phia;
-    bcm[n + j] = (R)v[0];
+    bcm[n + j] = (R)xbc_value(sp, side, 0, t);
     bcm[2 * n + j] = ua[0];
     bcm[3 * n + j] = ua[1];
     bcm[4 * n + j] = ua[2];
   } else {
-    bcm[j] = (R)v[4];
+    bcm[j] = (R)xbc_value(sp, side, 4, t);
     bcm[n + j] = Pa;
-    bcm[2 * n + j] = (R)v[1];
-    bcm[3 * n + j] = (R)v[2];
-    bcm[4 * n + j] = (R)v[3];
+    bcm[2 * n + j] = (R)xbc_value(sp, side, 1, t);
+    bcm[3 * n + j] = (R)xbc_value(sp, side, 2, t);
+    bcm[4 * n + j] = (R)xbc_value(sp, side, 3, t);
   }
 }
 
 template <class S, class R, bool ODD>
 __global__ void k_xbc(const __grid_constant__ Args<S, R> a, const __grid_constant__ XbcSpec sp) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < 2 * a.ny * a.nz) xbc_cell<S, R, ODD>(a, sp, a.bcm, j);
+  if (j < 2 * a.ny * a.nz) xbc_cell<S, R, ODD>(a, sp, a.bcm, j, sp.step0);
 }
 
 // Sets (on) or clears (off) the boundary flag of the fluid cells of the

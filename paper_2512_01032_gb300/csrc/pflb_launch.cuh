@@ -81,11 +81,7 @@ static Args<S, R> make_args(Lattice &L) {
 template <class S, class R>
 static cudaError_t launch_xbc(Lattice &L, const Args<S, R> &a) {
   if (!L.bc_on) return cudaSuccess;
-  XbcSpec sp;
-  for (int side = 0; side < 2; ++side) {
-    sp.type[side] = L.bc_type[side];
-    for (int k = 0; k < 5; ++k) sp.val[side][k] = L.bc_val[side][k];
-  }
+  const XbcSpec sp = xbc_spec(L, L.step);
   const int n = 2 * L.ny * L.nz, T = 128;
   if (L.step & 1)
     k_xbc<S, R, true><<<(n + T - 1) / T, T, 0, L.stream>>>(a, sp);

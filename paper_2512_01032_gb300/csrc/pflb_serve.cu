@@ -188,12 +188,15 @@ static void retire(pflb_server *s, Request *r, int state) {
   std::vector<double>().swap(r->theta);
 }
 
-// Pressure drive: P = beta p_ref at the inlet plane, 0 at the outlet plane.
-static pflb_status set_drive_boundaries(Request *r, int64_t step) {
+// Pressure drive: P = beta p_ref at the inlet plane, 0 at the outlet plane,
+// each change reached linearly over `ramp` steps (from rest at admission):
+// a sudden inlet jump sends a pressure wave through the light phase.
+static pflb_status set_drive_boundaries(Request *r, int64_t step, int64_t ramp) {
   pflb_xbc in{}, out{};
   in.type = out.type = PFLB_XBC_PRESSURE;
   in.P = r->beta_at(step) * r->spec.p_ref;
   out.P = 0.0;
+  in.ramp_steps = out.ramp_steps = ramp;
   return pflb_set_x_boundaries(r->L, &in, &out);
 }
 
@@ -213,7 +216,8 @@ static pflb_status admit(pflb_server *s) {
       st = pflb_init_tanh(r->L, r->spec.init_shape, r->spec.center, r->spec.R, r->spec.normal,
                           0.0);
     if (st == PFLB_OK) st = pflb_set_region(r->L, r->spec.region);
-    if (st == PFLB_OK && r->spec.drive == 1) st = set_drive_boundaries(r, 0);
+    if (st == PFLB_OK && r->spec.drive == 1)
+      st = set_drive_boundaries(r, 0, s->cfg.steps_per_tick);
     if (st != PFLB_OK) {
       // the request cannot run (e.g. its parameters are invalid): fail it,
       // keep serving the others
@@ -245,7 +249,7 @@ extern "C" pflb_status pflb_server_tick(pflb_server *s, int *n_active) {
   if (!stepped.empty()) {
     for (Request *r : stepped) {
       if (r->spec.drive == 1) {
-        if (set_drive_boundaries(r, r->res.steps) != PFLB_OK)
+        if (set_drive_boundaries(r, r->res.steps, s->cfg.steps_per_tick) != PFLB_OK)
           return server_poison(s, std::string("boundaries: ") + pflb_last_error());
         continue;
       }

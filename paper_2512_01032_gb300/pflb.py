@@ -29,18 +29,19 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NAN"
 
 class XBC(C.Structure):
     _fields_ = [("type", C.c_int), ("P", C.c_double), ("u", C.c_double * 3),
-                ("phi", C.c_double)]
+                ("phi", C.c_double), ("ramp_steps", C.c_int64)]
 
 
 XBC_PRESSURE, XBC_VELOCITY = 1, 2
 
 
-def _xbc(b):
+def _xbc(b, ramp_steps=0):
     if b is None:
         return None
     t = {"pressure": XBC_PRESSURE, "velocity": XBC_VELOCITY}.get(b["type"], b["type"])
     u = b.get("u", (0.0, 0.0, 0.0))
-    return XBC(int(t), float(b.get("P", 0.0)), (C.c_double * 3)(*u), float(b.get("phi", 0.0)))
+    return XBC(int(t), float(b.get("P", 0.0)), (C.c_double * 3)(*u), float(b.get("phi", 0.0)),
+               int(ramp_steps))
 
 
 class DiagRaw(C.Structure):
@@ -377,10 +378,11 @@ class Lattice:
             _check(s)
         return d.as_dict()
 
-    def set_x_boundaries(self, lo=None, hi=None):
+    def set_x_boundaries(self, lo=None, hi=None, ramp_steps=0):
         """Open x boundaries: lo / hi dicts with type ("pressure" or
-        "velocity"), P, u (3), phi; None for both restores periodic x."""
-        a, b = _xbc(lo), _xbc(hi)
+        "velocity"), P, u (3), phi; None for both restores periodic x.
+        ramp_steps > 0 reaches the values linearly over that many steps."""
+        a, b = _xbc(lo, ramp_steps), _xbc(hi, ramp_steps)
         _check(self._lib.pflb_set_x_boundaries(self._h, C.byref(a) if a else None,
                                                C.byref(b) if b else None))
 

@@ -51,18 +51,26 @@ def _slab_pushed():
     return (nx, ny, nz), g.solid, g.normals(), g.theta(), p, phi0, lo, hi, 2 * p["sigma"] / 8.0
 
 
+def _slab_ramped():
+    """The pushed slab with the inlet ramped up over 50 steps from rest."""
+    c = list(_slab_pushed())
+    c.append(50)
+    return tuple(c)
+
+
 def _pair(case, storage, kernel=0, tile=None):
     from paper_2512_01032_gb300 import pflb
-    (nx, ny, nz), solid, nrm, th, p, phi0, lo, hi, _ = case
+    (nx, ny, nz), solid, nrm, th, p, phi0, lo, hi, _ = case[:9]
+    ramp = case[9] if len(case) > 9 else 0
     G = pflb.Lattice(nx, ny, nz, solid=solid, wall_normal=nrm, theta_cells=th, storage=storage,
                      **p)
     G.set_kernel(kernel, *(tile or (0, 0, 0)))
-    G.set_x_boundaries(lo, hi)
+    G.set_x_boundaries(lo, hi, ramp)
     G.init_phi(phi0)
     Orc = O.OracleLattice(nx, ny, nz, solid=solid, wall_normal=nrm, theta_cells=th,
                           nthreads=os.cpu_count() or 1, **{k: v for k, v in p.items() if k in OKEYS})
     Orc.init_phi(phi0)
-    Orc.set_x_boundaries(lo, hi)
+    Orc.set_x_boundaries(lo, hi, ramp)
     return G, Orc
 
 
@@ -78,16 +86,16 @@ def _errors(G, Orc, p_scale):
 
 
 @pytest.mark.parametrize("storage", ["fp64", "fp32"])
-@pytest.mark.parametrize("case", ["poiseuille", "slab"])
+@pytest.mark.parametrize("case", ["poiseuille", "slab", "slab_ramped"])
 def test_open_boundaries_match_oracle(case, storage):
-    c = _poiseuille() if case == "poiseuille" else _slab_pushed()
+    c = {"poiseuille": _poiseuille, "slab": _slab_pushed, "slab_ramped": _slab_ramped}[case]()
     G, Orc = _pair(c, storage)
     t = 0
     for s in (1, 7, 60, 200):
         G.step(s - t)
         Orc.step(s - t)
         t = s
-        e = _errors(G, Orc, c[-1])
+        e = _errors(G, Orc, c[8])
         assert e["phi"] <= TOL[storage] and e["P"] <= TOL[storage], (case, s, e)
         assert e["u_abs"] <= TOL_U[storage], (case, s, e)
 

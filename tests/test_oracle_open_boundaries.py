@@ -78,3 +78,31 @@ def test_boundary_requests_are_checked():
     with pytest.raises(ValueError):
         L.set_x_boundaries(dict(type="pressure", P=0.0), None)  # one side only
     L.set_x_boundaries(None, None)  # periodic again
+
+
+def test_boundary_ramp_is_linear_in_steps():
+    """ramp_steps: the boundary pressure goes linearly from the rest state
+    (boundaries off before) to its value over the ramp, read back at the
+    boundary cells; a new value mid-ramp starts from the value in effect."""
+    solid = np.zeros((1, NY, NX), np.uint8)
+    solid[:, 0, :] = 1
+    solid[:, -1, :] = 1
+    L = O.OracleLattice(NX, NY, 1, solid=solid.reshape(-1), nthreads=2, sigma=0.01, W=4.0,
+                        M=0.02, rho_H=1.0, rho_L=1e-3, nu_H=MU, nu_L=0.1)
+    L.init_phi((1 - solid).reshape(-1).astype(float))
+    P1 = 1e-3
+    L.set_x_boundaries(dict(type="pressure", P=P1), dict(type="pressure", P=0.0), ramp_steps=40)
+
+    def p_in():
+        return L.macros()["P"].reshape(NY, NX)[NY // 2, 0]
+
+    assert p_in() == 0.0
+    L.step(10)
+    assert p_in() == pytest.approx(0.25 * P1, rel=1e-12)
+    L.step(30)
+    assert p_in() == pytest.approx(P1, rel=1e-12)
+    L.step(5)
+    assert p_in() == pytest.approx(P1, rel=1e-12)
+    L.set_x_boundaries(dict(type="pressure", P=0.0), dict(type="pressure", P=0.0), ramp_steps=10)
+    L.step(5)
+    assert p_in() == pytest.approx(0.5 * P1, rel=1e-12)
