@@ -243,6 +243,27 @@ def static_slug(theta_deg, H=32, length=64, nx=192, nz=4):
     return g, p, init
 
 
+def dynamic_slug(U=2e-3, H=32, nx=384, length=64, theta_deg=133.0, nz=4):
+    """Liquid slug driven along a slit (plates H cells apart, periodic in z)
+    by a gas velocity inlet U at x = 0 against a pressure outlet at x = nx-1:
+    the 2-D analogue of the paper's Sec. IV B channel (hydrophobic walls,
+    theta 133 degrees).  Density ratio 1000, dynamic viscosity ratio 50
+    (nu_H = 1/60, nu_L = 1/3), sigma = 0.01, W = 4, M = 0.1666, optimised
+    model.  The slug starts at rest with flat menisci for 64 <= x < 64 +
+    length."""
+    ny = H + 2
+    shapes = [Plane((0, 0.5, 0), (0, 1, 0)), Plane((0, ny - 1.5, 0), (0, -1, 0))]
+    g = Geometry(nx, ny, nz, shapes, theta_deg=theta_deg)
+    p = dict(sigma=0.01, W=4.0, M=0.1666, rho_H=1.0, rho_L=1e-3, nu_H=1.0 / 60.0,
+             nu_L=1.0 / 3.0, theta_deg=theta_deg, F_mode=1, mobility_corr=1, free_slip=1,
+             blend=0.95)
+    init = dict(shape=2, center=(64 + length / 2.0 - 0.5, 0.0, 0.0), R=length / 2.0,
+                normal=(1.0, 0.0, 0.0))
+    inlet = dict(type="velocity", u=(U, 0.0, 0.0), phi=0.0)
+    outlet = dict(type="pressure", P=0.0)
+    return g, p, init, inlet, outlet
+
+
 def channel_lattice(spec: dict):
     """(geometry, params, init) of one channel_batch_specs entry: square duct
     along x, droplet at x = Nx/4 on the axis, carrier driven by a uniform body
