@@ -57,6 +57,30 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+BATCH_SOURCES = ("pflb_batch.cuh", "pflb_kernels.cuh", "pflb_model.cuh", "pflb_launch.cuh",
+                 "pflb_bf16.cu")
+
+
+def batch_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in BATCH_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2512_01032_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_batch_traffic(storage, fluid):
+    """DRAM bytes per launch of the batch kernel, from the committed ncu
+    summary of a smaller case scaled by fluid cells, if it was taken on the
+    current sources at this storage."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "k_batch_channels8_bf16_traffic.json")))
+    except Exception:
+        return None
+    if d.get("batch_source_hash") != batch_source_hash() or d.get("storage") != storage:
+        return None
+    return d["dram_bytes_per_fluid_cell"] * fluid
+
+
 def hbm_peak():
     try:
         d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -346,7 +370,9 @@ def main_channels(args):
                                         "blocks_per_sm": best[3]},
                        "l2": "inputs larger than L2 (no flush)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": recorded_batch_traffic(storage, fluid),
+                         "traffic_note": "ncu capture of 8 of the lattices, scaled by fluid cells",
                          "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS hbm_gbs)",
                          "algorithmic_bytes_per_cell": ALGO_BYTES[storage],
                          "kernel": "k_batch"},
