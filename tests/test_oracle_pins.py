@@ -367,3 +367,28 @@ def test_contact_angle_flat_wall_2d(theta):
     cx, cz, rr = synth.fit_circle(pts)
     got = math.degrees(math.acos(max(-1, min(1, (0.5 - cz) / rr))))
     assert abs(got - theta) < 3.0, got
+
+
+def test_free_slip_band_conserves_tangential_momentum():
+    """Free-slip band (R14, Sec. III A): specular reflection at flat walls
+    removes no tangential momentum, so a body-forced fluid whose phi stays
+    inside the band gains exactly F per cell per step (total x-momentum
+    F N t to rounding); halfway bounce-back (band off) loses most of it to
+    the walls."""
+    nx, ny, nz, F, t = 6, 10, 1, 1e-6, 300
+    solid = np.zeros((nz, ny, nx), np.uint8)
+    solid[:, 0, :] = 1
+    solid[:, -1, :] = 1
+    fluid = solid.reshape(-1) == 0
+    ratio = {}
+    for fs in (1, 0):
+        L = O.OracleLattice(nx, ny, nz, solid=solid.reshape(-1), nthreads=1, sigma=0.01, W=4.0,
+                            M=0.02, rho_H=1.0, rho_L=1e-3, nu_H=0.1, nu_L=0.1, theta_deg=90.0,
+                            free_slip=fs, Fex=(F, 0.0, 0.0))
+        L.init_phi(0.7 * fluid.astype(float))
+        L.step(t)
+        m = L.macros()
+        assert 0.5 < m["phi"][fluid].min() and m["phi"][fluid].max() < 0.95  # inside the band
+        ratio[fs] = (m["rho"] * m["ux"])[fluid].sum() / (F * fluid.sum() * t)
+    assert ratio[1] == pytest.approx(1.0, abs=1e-10)
+    assert ratio[0] < 0.5
