@@ -450,6 +450,17 @@ pflb_status pflb_server_stats_get(pflb_server *s, pflb_server_stats *out);
 /* Free the server and every resident lattice; NULL is ignored. */
 void pflb_server_destroy(pflb_server *s);
 
+/* Self-test of the failure-detection path (no counterpart in the paper).
+ * Queues on the lattice's stream a kernel that waits, through the same
+ * bounded-wait helper the staged step kernel uses for its TMA copies, on an
+ * mbarrier that nothing completes; after `polls` polls (1 .. 2^20) the wait
+ * gives up, raises the lattice's device error flag and the kernel returns,
+ * so no fault occurs and the GPU context stays usable.  The lattice's next
+ * synchronising call (pflb_read, pflb_last_diag, pflb_diag) then returns
+ * PFLB_ERR_TIMEOUT and the lattice is poisoned (PFLB_ERR_STATE afterwards),
+ * as after a real stalled copy.  Other lattices are unaffected. */
+pflb_status pflb_selftest_wait_timeout(pflb_lattice *L, int64_t polls);
+
 /* Free the lattice (synchronises its stream first).  NULL is ignored. */
 void pflb_destroy(pflb_lattice *L);
 

@@ -23,7 +23,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]
 SOURCES = ["pflb_capi.cu", "pflb_f32.cu", "pflb_f64.cu", "pflb_f16.cu", "pflb_bf16.cu",
-           "pflb_noalloc.cu", "pflb_serve.cu"]
+           "pflb_noalloc.cu", "pflb_serve.cu", "pflb_selftest.cu"]
 
 
 def _nvcc() -> str:

@@ -70,17 +70,23 @@ __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// Wait for a stage; on running out of the spin limit, raise the error flag
-// and return false (the caller stops using the stage).
-__device__ __forceinline__ bool stage_wait(uint64_t *bar, unsigned parity, int *err) {
+// Bounded wait on an mbarrier phase: on running out of `limit` polls, raise
+// the error flag and return false (the caller stops using what it waited for).
+__device__ __forceinline__ bool bounded_wait(uint64_t *bar, unsigned parity, int *err,
+                                             unsigned long long limit) {
   unsigned long long it = 0;
   while (!mbar_try_wait(bar, parity)) {
-    if (++it > AB_WAIT_LIMIT) {
+    if (++it > limit) {
       if (err) atomicExch(err, 1);
       return false;
     }
   }
   return true;
+}
+
+// Wait for a stage of the staged step kernel.
+__device__ __forceinline__ bool stage_wait(uint64_t *bar, unsigned parity, int *err) {
+  return bounded_wait(bar, parity, err, AB_WAIT_LIMIT);
 }
 
 // One TMA load of plane zw of the h buffer (tile + halo, 19 directions)

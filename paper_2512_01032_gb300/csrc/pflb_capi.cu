@@ -25,7 +25,6 @@
 
 using pflb::Lattice;
 
-struct pflb_lattice : public Lattice {};
 
 struct pflb_batch {
   std::vector<Lattice *> lats;

@@ -128,3 +128,6 @@ template <class S, class R> cudaError_t batch_launch_step(const BatchDev &b, boo
 template <class S, class R> int batch_max_blocks_per_sm(int bx, int by);
 
 }  // namespace pflb
+
+// The opaque handle of the C ABI is the lattice state itself.
+struct pflb_lattice : public pflb::Lattice {};

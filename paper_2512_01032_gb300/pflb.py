@@ -167,6 +167,8 @@ def load(build_if_missing: bool = True):
     lib.pflb_diag_wait.restype = st
     lib.pflb_set_x_boundaries.argtypes = [C.c_void_p, _P(XBC), _P(XBC)]
     lib.pflb_set_x_boundaries.restype = st
+    lib.pflb_selftest_wait_timeout.argtypes = [C.c_void_p, C.c_int64]
+    lib.pflb_selftest_wait_timeout.restype = st
     lib.pflb_get_kernel.argtypes = [C.c_void_p, _P(C.c_int)]
     lib.pflb_get_kernel.restype = st
     lib.pflb_step.argtypes = [C.c_void_p, C.c_int64]
@@ -385,6 +387,11 @@ class Lattice:
         a, b = _xbc(lo, ramp_steps), _xbc(hi, ramp_steps)
         _check(self._lib.pflb_set_x_boundaries(self._h, C.byref(a) if a else None,
                                                C.byref(b) if b else None))
+
+    def selftest_wait_timeout(self, polls=1000):
+        """Queue the bounded-wait self-test (the next synchronising call
+        reports ERR_TIMEOUT and poisons this lattice)."""
+        _check(self._lib.pflb_selftest_wait_timeout(self._h, int(polls)))
 
     def get_kernel(self) -> dict:
         out = (C.c_int * 4)()

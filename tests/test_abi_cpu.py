@@ -153,6 +153,7 @@ def test_create_rejects_bad_geometry():
     assert lib.pflb_step_ex(None, 1, 0) == pflb.ERR_ARG
     assert lib.pflb_get_kernel(None, (C.c_int * 4)()) == pflb.ERR_ARG
     assert lib.pflb_set_x_boundaries(None, None, None) == pflb.ERR_ARG
+    assert lib.pflb_selftest_wait_timeout(None, 100) == pflb.ERR_ARG
     raw = pflb.DiagRaw()
     assert lib.pflb_last_diag_async(None, C.byref(raw), C.byref(t)) == pflb.ERR_ARG
     assert lib.pflb_diag_wait(None, 0, C.byref(raw), C.byref(pflb.Diag())) == pflb.ERR_ARG
