@@ -37,7 +37,8 @@ def test_save_load_resumes_bitwise(storage, tmp_path):
         L.step(20)
     for k in FIELDS:
         assert np.array_equal(A.read(k), B.read(k)), k
-    assert A.diag()["mass"] == B.diag()["mass"]
+    # the diagnostics add block sums with FP64 atomics in no fixed order
+    assert A.diag()["mass"] == pytest.approx(B.diag()["mass"], rel=1e-13)
 
 
 def test_load_refuses_a_different_lattice(tmp_path):
