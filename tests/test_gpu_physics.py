@@ -50,7 +50,7 @@ def _axis_top(phi3, c):
     return k + (col[k] - 0.5) / (col[k] - col[k + 1])
 
 
-@pytest.mark.parametrize("theta", [60.0, 90.0, 120.0])
+@pytest.mark.parametrize("theta", [30.0, 60.0, 90.0, 120.0, 150.0])
 def test_drop_height_on_sphere(theta):
     """64^3: solid sphere of radius 15 centred on the floor, drop of radius
     10 set on its top; after 15000 steps the drop's top lies where a ball of
