@@ -413,7 +413,6 @@ def main_serve(args):
     batching (one persistent batch kernel per step over all resident
     requests, admission by HBM budget) against the plain server (one request
     at a time, FP32, one fused launch per step) on the same trace."""
-    import math
     import torch
     from paper_2512_01032_gb300 import pflb, shard
     world, rank = init_ranks()
@@ -449,17 +448,15 @@ def main_serve(args):
         res = [S.poll(t) for t in tickets]
         S.close()
         # over ranks: latencies and step counts gathered, makespan max, counters summed
-        lat = sorted(x for r in shard.gather([q["latency_s"] for q in res
-                                              if q["state"] == pflb.REQ_DONE]) for x in r)
+        lat = shard.merged_sorted(q["latency_s"] for q in res if q["state"] == pflb.REQ_DONE)
         steps = [x for r in shard.gather([q["steps"] for q in res]) for x in r]
         makespan, = shard.reduce_max([st["makespan_s"]], device=dev)
         tot = shard.reduce_sum([st["completed"], st["failed"], st["rejected"],
                                 st["cell_updates"],
                                 sum(q["broke_through"] for q in res)], device=dev)
-        pct = (lambda q: lat[min(len(lat), max(1, math.ceil(q * len(lat)))) - 1]
-               if lat else 0.0)
-        out[name] = dict(solves_per_s=tot[0] / max(makespan, 1e-9), p50_s=pct(0.5),
-                         p99_s=pct(0.99), mean_s=sum(lat) / max(len(lat), 1),
+        out[name] = dict(solves_per_s=tot[0] / max(makespan, 1e-9),
+                         p50_s=shard.nearest_rank(lat, 0.5), p99_s=shard.nearest_rank(lat, 0.99),
+                         mean_s=sum(lat) / max(len(lat), 1),
                          makespan_s=makespan, completed=int(tot[0]), failed=int(tot[1]),
                          rejected=int(tot[2]), peak_gb=st["peak_bytes"] / 2 ** 30,
                          mlups=tot[3] / max(makespan, 1e-9) / 1e6,

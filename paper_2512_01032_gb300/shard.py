@@ -76,3 +76,20 @@ def gather(obj) -> list:
     out = [None] * dist.get_world_size()
     dist.all_gather_object(out, obj)
     return out
+
+
+def nearest_rank(sorted_values, q: float) -> float:
+    """Nearest-rank percentile (q in (0, 1]) of an ascending list; 0 when
+    empty (the definition the request server uses for its p50/p99)."""
+    import math
+    n = len(sorted_values)
+    if n == 0:
+        return 0.0
+    k = min(n, max(1, math.ceil(q * n)))
+    return float(sorted_values[k - 1])
+
+
+def merged_sorted(values) -> list:
+    """Every rank's values (e.g. per-request latencies), merged and sorted,
+    on every rank."""
+    return sorted(float(v) for part in gather(list(values)) for v in part)

@@ -42,6 +42,11 @@ def rank_main(rank, world, port, out_path):
         n_sum, cells_sum = shard.reduce_sum([len(mine), sum(cells[i] for i in mine)])
         probe_max, = shard.reduce_max([rank + 1.0])
         allres = shard.gather(res)
+        # serving statistics over ranks: each rank holds its requests' latencies
+        lat_all = [0.5 + 0.37 * k for k in range(23)]
+        mine_lat = [v for k, v in enumerate(lat_all) if k % world == rank]
+        lat_merged = shard.merged_sorted(mine_lat)
+        p50, p99 = shard.nearest_rank(lat_merged, 0.5), shard.nearest_rank(lat_merged, 0.99)
         if rank == 0:
             merged = {}
             for r in allres:
@@ -52,7 +57,8 @@ def rank_main(rank, world, port, out_path):
                 json.dump({"results": {str(k): v for k, v in merged.items()},
                            "t_max": t_max, "t_rank0": dt, "n_sum": n_sum,
                            "cells_sum": cells_sum, "probe_max": probe_max,
-                           "owned": [shard.my_items(cells, r, world) for r in range(world)]},
+                           "owned": [shard.my_items(cells, r, world) for r in range(world)],
+                           "merged": lat_merged, "p50": p50, "p99": p99},
                           f)
         dist.barrier()
     finally:

@@ -53,3 +53,16 @@ def test_two_gloo_ranks_match_one_process(tmp_path):
     for i, spec in enumerate(specs):
         want = W.run_item(spec)
         assert got["results"][str(i)] == want  # same oracle, one thread: bitwise
+    lat_all = sorted(0.5 + 0.37 * k for k in range(23))
+    assert got["merged"] == lat_all
+    assert got["p50"] == shard.nearest_rank(lat_all, 0.5) == lat_all[11]
+    assert got["p99"] == shard.nearest_rank(lat_all, 0.99) == lat_all[22]
+
+
+def test_nearest_rank_percentiles():
+    v = [1.0, 2.0, 3.0, 4.0]
+    assert shard.nearest_rank(v, 0.5) == 2.0
+    assert shard.nearest_rank(v, 0.99) == 4.0
+    assert shard.nearest_rank(v, 0.01) == 1.0
+    assert shard.nearest_rank([], 0.5) == 0.0
+    assert shard.merged_sorted([3, 1, 2]) == [1.0, 2.0, 3.0]  # no process group: local
