@@ -10,6 +10,7 @@ tensors, ``nccl`` on CUDA tensors).
 from __future__ import annotations
 
 import heapq
+import math
 
 
 def assign(cells, world: int) -> list[list[int]]:
@@ -81,7 +82,6 @@ def gather(obj) -> list:
 def nearest_rank(sorted_values, q: float) -> float:
     """Nearest-rank percentile (q in (0, 1]) of an ascending list; 0 when
     empty (the definition the request server uses for its p50/p99)."""
-    import math
     n = len(sorted_values)
     if n == 0:
         return 0.0
