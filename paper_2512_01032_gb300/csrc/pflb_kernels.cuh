@@ -26,9 +26,18 @@ namespace pflb {
 
 enum { MODE_STEP = 0, MODE_MACRO = 1 };
 
-// Blocks per SM the fused kernels are compiled for (sets the register cap).
+// Blocks of 256 threads per SM the batch kernel is compiled for (sets its
+// register cap: 128).
 #ifndef PFLB_MIN_BLOCKS
 #define PFLB_MIN_BLOCKS 2
+#endif
+
+// Register cap of the plain fused kernel.  At 96 registers five 128-thread
+// blocks fit on an SM (20 warps instead of the 16 that 128 registers allow);
+// the FP32 and 16-bit instantiations then spill 36-52 bytes per thread, and
+// the extra warps hide more of the DRAM latency that bounds the kernel.
+#ifndef PFLB_FUSED_MAXNREG
+#define PFLB_FUSED_MAXNREG 96
 #endif
 
 template <class S, class R>
@@ -583,7 +592,7 @@ __host__ __device__ constexpr size_t fused_smem_bytes(int BX, int BY, bool diag)
 }
 
 template <class S, class R, bool ODD, bool DIAG, bool XBC = false>
-__global__ void __launch_bounds__(256, PFLB_MIN_BLOCKS)
+__global__ void __maxnreg__(PFLB_FUSED_MAXNREG)
     k_fused(const __grid_constant__ Args<S, R> a, int BX, int BY) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R *sphi = reinterpret_cast<R *>(smem_raw);
