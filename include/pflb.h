@@ -192,7 +192,7 @@ pflb_status pflb_set_kernel(pflb_lattice *L, int kind, int bx, int by, int lz);
  * no diagnostics and read back their boundary state.  First-order accurate
  * (equilibrium boundary).  Lattices with open boundaries run the fused or
  * two-pass kernel (not the TMA one); in a batch their boundary states are
- * formed by one extra kernel per step (one block per such lattice). */
+ * formed by one extra kernel per step over all such lattices. */
 enum { PFLB_XBC_PRESSURE = 1, PFLB_XBC_VELOCITY = 2 };
 typedef struct {
   int type;        /* PFLB_XBC_PRESSURE or PFLB_XBC_VELOCITY */
@@ -317,8 +317,11 @@ pflb_status pflb_fields_noalloc(int nx, int ny, int nz, const float *h_dev, cons
  * persistent kernel: a grid of (SMs x blocks per SM) blocks pulls work
  * items -- one per (lattice, tile column, chunk of z planes) -- from a device
  * work list, so small lattices that could not fill the GPU on their own
- * share it.  Every cell gets exactly the arithmetic of its lattice stepped
- * alone (results are bit-identical).  Plain steps are replayed from a
+ * share it.  No work item reads another lattice, so a lattice's result does
+ * not depend on what it is batched with: it is bit-identical to the same
+ * lattice in a batch of its own.  Against pflb_step on that lattice it
+ * agrees to rounding (the two kernels are compiled separately and may
+ * contract different multiply-adds).  Plain steps are replayed from a
  * captured CUDA graph of 16 steps.  The batch does not own the lattices;
  * they must outlive it, share one storage type, and appear once.  Work is
  * ordered on the batch stream (cuda_stream, or a stream the batch creates
