@@ -17,8 +17,8 @@
  * Notation follows the paper: h_i are the phase-field populations (Eq. 1),
  * g_i (the paper's g-bar) the hydrodynamic populations (Eq. 5).  T = 1/3.
  *
- * Readings of passages the paper leaves open (each is listed in the design
- * notes with its justification):
+ * Readings of passages the paper leaves open, the same on both sides of the
+ * parity tests:
  *   R1  rho = rho_L + phi*(rho_H - rho_L), rho_dif = rho_H - rho_L, phi=1 heavy.
  *   R2  Filtered collision (Eqs. 9-11): G_eq = E + K/2 with
  *       E_i = rho*Gamma_i + w_i*(P/T - rho); non-equilibrium = g - g_eq
