@@ -564,3 +564,56 @@ def test_flow_along_the_interface_leaves_it_in_place(u_along, rho_L):
     else:
         heavy = m["phi"] > 0.99
         assert np.abs(m[k][heavy] - u0).max() < 0.02 * u0
+
+
+
+@pytest.mark.parametrize("base", [0.9, 0.1])
+def test_mobility_correction_enters_h_equilibrium_with_its_weight(base):
+    """Eq. 4's delta-theta is added to theta in the h equilibrium (Eqs. 2-3),
+    and nowhere else: from one common state, a step with the correction and
+    a step without it differ only in h, by w_i delta-theta(x) (c_i . n(x)) /
+    tau_phi on the population that leaves x in direction i, with
+    n = grad phi / (|grad phi| + eps) and tau_phi = M/T + 1/2; g is bitwise
+    the same.  The field is a smooth periodic ripple inside one correction
+    window (phi in (0.8, 1) or (0, 0.2)), so both signs of the Laplacian
+    occur and the correction acts on about half of the cells (on an exact
+    tanh profile it is off: there the Laplacian has the other sign in both
+    windows).  delta-theta itself is pinned by the hand-evaluated cases."""
+    from oracle.oracle import make_params
+    n = 14
+    kw = dict(sigma=0.01, W=4.0, M=0.02, rho_H=1.0, rho_L=1e-3, nu_H=0.1, nu_L=0.1)
+    Z, Y, X = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    k = 2 * np.pi / n
+    phi0 = base + 0.06 * np.cos(k * X) * np.cos(k * Y) + 0.03 * np.sin(k * Z + 0.4)
+    A = O.OracleLattice(n, n, n, mobility_corr=1, **kw)
+    B = O.OracleLattice(n, n, n, mobility_corr=0, **kw)
+    B.init_phi(phi0.reshape(-1))
+    h0, g0 = B.populations()
+    A.init_phi(phi0.reshape(-1))
+    A.set_populations(h0, g0)
+    A.step(1)
+    B.step(1)
+    hA, gA = A.populations()
+    hB, gB = B.populations()
+    assert np.array_equal(gA, gB)
+    c, w, _ = O.lattice_tables()
+    p = make_params(mobility_corr=1, **kw)
+    tau_phi = kw["M"] * 3.0 + 0.5
+    phi = h0.sum(axis=1).reshape(n, n, n)
+    want = np.zeros_like(hA)
+    active = 0
+    for z in range(n):
+        for y in range(n):
+            for x in range(n):
+                nb = [phi[(z + c[i, 2]) % n, (y + c[i, 1]) % n, (x + c[i, 0]) % n]
+                      for i in range(19)]
+                grad, lap = O.cd_stencil(nb)
+                dth = O.delta_theta(p, phi[z, y, x], grad, lap)
+                active += abs(dth) > 1e-6
+                nrm = grad / (np.linalg.norm(grad) + p.eps)
+                for i in range(19):
+                    to = (((z + c[i, 2]) % n) * n + (y + c[i, 1]) % n) * n + (x + c[i, 0]) % n
+                    want[to, i] = w[i] * dth * (c[i] @ nrm) / tau_phi
+    assert 0.3 * n ** 3 < active < 0.7 * n ** 3
+    assert np.abs(want).max() > 1e-4
+    assert np.abs((hA - hB) - want).max() < 1e-15
