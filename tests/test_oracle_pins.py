@@ -619,55 +619,49 @@ def test_mobility_correction_enters_h_equilibrium_with_its_weight(base):
     assert np.abs((hA - hB) - want).max() < 1e-15
 
 
-def test_one_step_moment_identities_per_cell():
-    """Every cell of a whole step, against the moments Eqs. 1-7 fix.
-    Periodic push streaming is undone exactly (the population that arrives
-    at x + c_i in direction i left x), which recovers each cell's
-    post-collision populations h*, g*.  With phi = sum h, grad phi and its
-    Laplacian from Eq. 13, mu from Eq. 7 and u = (sum c g + (mu grad phi +
-    F)/2) / rho from the pre-step state:
-      sum h* = phi;
-      sum c h* = sum c h + (phi u + theta T n - sum c h) / tau_phi, with
-        theta = (M/T)(1 - 4 (phi - 1/2)^2)/W + delta-theta (Eq. 3) and
-        n = grad phi / (|grad phi| + eps);
-      sum c c h* = sum c c h + (phi (T I + u u) - sum c c h) / tau_phi;
-      sum c g* - sum c g = mu grad phi + F (the force of Eq. 6);
-      sum g* - sum g = rho_dif u . grad phi (its zeroth moment).
-    The state is a rippled, non-equilibrium field after three steps, so
-    u, mu and the force are non-zero everywhere."""
+
+def _one_step_identity_errors(dims, kw, phi0, solid3=None, pre_steps=3):
+    """Largest deviations of every fluid cell's post-collision moments from
+    those Eqs. 1-7 fix, over one step after ``pre_steps`` steps.  The
+    post-collision populations are recovered by undoing push streaming: the
+    population that left x in direction i arrived at x + c_i in slot i, or,
+    when x + c_i is solid, came back to x in slot opp(i) (halfway
+    bounce-back, R13; no free-slip band).  The stencil reads, for a solid
+    neighbour, the wetting ghost of that link used by the step."""
     from oracle.oracle import make_params
-    n = 12
-    kw = dict(sigma=0.01, W=4.0, M=0.02, rho_H=1.0, rho_L=1e-3, nu_H=0.1, nu_L=0.05,
-              Fex=(1e-6, -2e-6, 3e-6))
-    Z, Y, X = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
-    k = 2 * np.pi / n
-    phi0 = (0.5 + 0.25 * np.sin(k * X + 0.3) * np.cos(k * Y) + 0.12 * np.cos(k * Z + 1.1)
-            + 0.05 * np.sin(k * (X + Y) + 0.2))
-    L = O.OracleLattice(n, n, n, nthreads=2, **kw)
-    L.init_phi(phi0.reshape(-1))
-    L.step(3)
+    nx, ny, nz = dims
+    solid3 = np.zeros((nz, ny, nx), bool) if solid3 is None else solid3.astype(bool)
+    L = O.OracleLattice(nx, ny, nz, solid=solid3.astype(np.uint8).reshape(-1), nthreads=2, **kw)
+    L.init_phi((phi0 * ~solid3).reshape(-1))
+    L.step(pre_steps)
     h, g = L.populations()
     L.step(1)
     h1, g1 = L.populations()
-    c, w, _ = O.lattice_tables()
+    ghost = L.ghosts()
+    c, w, opp = O.lattice_tables()
     p = make_params(**kw)
     T = 1.0 / 3.0
     tau_phi = kw["M"] / T + 0.5
-    F = np.array(kw["Fex"])
+    F = np.array(kw.get("Fex", (0.0, 0.0, 0.0)))
     rho_dif = kw["rho_H"] - kw["rho_L"]
-    phi = h.sum(axis=1).reshape(n, n, n)
+    phi = (h.sum(axis=1) * ~solid3.reshape(-1)).reshape(nz, ny, nx)
     err = dict(h0=0.0, h1=0.0, h2=0.0, g1=0.0, g0=0.0)
     scale = dict(h1=0.0, g1=0.0, g0=0.0)
-    for z in range(n):
-        for y in range(n):
-            for x in range(n):
-                cell = (z * n + y) * n + x
-                to = [(((z + c[i, 2]) % n) * n + (y + c[i, 1]) % n) * n + (x + c[i, 0]) % n
-                      for i in range(19)]
-                hs = np.array([h1[to[i], i] for i in range(19)])
-                gs = np.array([g1[to[i], i] for i in range(19)])
-                nb = [phi[(z + c[i, 2]) % n, (y + c[i, 1]) % n, (x + c[i, 0]) % n]
-                      for i in range(19)]
+    walls = 0
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                if solid3[z, y, x]:
+                    continue
+                cell = (z * ny + y) * nx + x
+                nbr = [(((z + c[i, 2]) % nz) * ny + (y + c[i, 1]) % ny) * nx + (x + c[i, 0]) % nx
+                       for i in range(19)]
+                sol = [bool(solid3.reshape(-1)[nbr[i]]) for i in range(19)]
+                walls += any(sol)
+                hs = np.array([h1[cell, opp[i]] if sol[i] else h1[nbr[i], i] for i in range(19)])
+                gs = np.array([g1[cell, opp[i]] if sol[i] else g1[nbr[i], i] for i in range(19)])
+                nb = [ghost[cell, i] if sol[i] else phi.reshape(-1)[nbr[i]] for i in range(19)]
+                nb[0] = phi[z, y, x]
                 grad, lap = O.cd_stencil(nb)
                 f = phi[z, y, x]
                 mu = O.chem_pot(p, f, lap)
@@ -691,7 +685,57 @@ def test_one_step_moment_identities_per_cell():
                 scale["h1"] = max(scale["h1"], np.abs(f * u + theta * T * nrm).max())
                 scale["g1"] = max(scale["g1"], np.abs(mu * grad).max())
                 scale["g0"] = max(scale["g0"], abs(rho_dif * (u @ grad)))
+    return err, scale, walls
+
+
+def _ripple(dims, k_phase=0.0):
+    nx, ny, nz = dims
+    Z, Y, X = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    k = 2 * np.pi / np.array([nx, ny, nz], float)
+    return (0.5 + 0.25 * np.sin(k[0] * X + 0.3 + k_phase) * np.cos(k[1] * Y)
+            + 0.12 * np.cos(k[2] * Z + 1.1) + 0.05 * np.sin(k[0] * X + k[1] * Y + 0.2))
+
+
+def test_one_step_moment_identities_per_cell():
+    """Every cell of a whole step, against the moments Eqs. 1-7 fix (helper
+    above), on a periodic box:
+      sum h* = phi;
+      sum c h* = sum c h + (phi u + theta T n - sum c h) / tau_phi, with
+        theta = (M/T)(1 - 4 (phi - 1/2)^2)/W + delta-theta (Eq. 3) and
+        n = grad phi / (|grad phi| + eps);
+      sum c c h* = sum c c h + (phi (T I + u u) - sum c c h) / tau_phi;
+      sum c g* - sum c g = mu grad phi + F (the force of Eq. 6);
+      sum g* - sum g = rho_dif u . grad phi (its zeroth moment);
+    with phi = sum h, the Eq. 13 stencil, mu of Eq. 7 and u = (sum c g +
+    (mu grad phi + F)/2) / rho from the pre-step state.  The state is a
+    rippled, non-equilibrium field after three steps, so u, mu and the
+    force are non-zero everywhere."""
+    kw = dict(sigma=0.01, W=4.0, M=0.02, rho_H=1.0, rho_L=1e-3, nu_H=0.1, nu_L=0.05,
+              Fex=(1e-6, -2e-6, 3e-6))
+    dims = (12, 12, 12)
+    err, scale, _ = _one_step_identity_errors(dims, kw, _ripple(dims))
     assert scale["h1"] > 1e-4 and scale["g1"] > 1e-6 and scale["g0"] > 1e-8
     # rounding only (measured 7e-16, 9e-17, 3e-16, 4e-17, 1e-16)
+    assert err["h0"] < 4e-15 and err["h1"] < 1e-15 and err["h2"] < 4e-15, err
+    assert err["g1"] < 1e-15 and err["g0"] < 1e-15, err
+
+
+def test_one_step_moment_identities_at_walls():
+    """The same identities at every wall node of a slit with a box obstacle
+    (face, edge and corner links; theta = 60 on the walls): undoing the step
+    with halfway bounce-back at the solid links (R13, both sets) and the
+    step's wetting ghosts in the stencil recovers post-collision populations
+    with the moments of Eqs. 1-7, so each population that meets a wall comes
+    back to its own cell in the opposite direction."""
+    kw = dict(sigma=0.01, W=4.0, M=0.02, rho_H=1.0, rho_L=1e-3, nu_H=0.1, nu_L=0.05,
+              Fex=(1e-6, 0.0, -2e-6), theta_deg=60.0, blend=0.95)
+    dims = (14, 10, 8)
+    nx, ny, nz = dims
+    solid = np.zeros((nz, ny, nx), bool)
+    solid[:, 0, :] = solid[:, -1, :] = True
+    solid[2:5, 3:6, 5:8] = True
+    err, scale, walls = _one_step_identity_errors(dims, kw, _ripple(dims, 0.7), solid)
+    assert walls > 200
+    assert scale["h1"] > 1e-4 and scale["g1"] > 1e-6 and scale["g0"] > 1e-8
     assert err["h0"] < 4e-15 and err["h1"] < 1e-15 and err["h2"] < 4e-15, err
     assert err["g1"] < 1e-15 and err["g0"] < 1e-15, err
