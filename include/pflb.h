@@ -40,8 +40,9 @@ typedef struct pflb_lattice pflb_lattice;
 typedef enum {
   PFLB_OK = 0,
   PFLB_ERR_ARG = 1,     /* invalid argument or parameter */
-  PFLB_ERR_OOM = 2,     /* device or host allocation failed */
-  PFLB_ERR_CUDA = 3,    /* a CUDA call failed (lattice is poisoned) */
+  PFLB_ERR_OOM = 2,     /* out of device memory, or a host allocation failed */
+  PFLB_ERR_CUDA = 3,    /* a CUDA call failed, including no usable device (a lattice
+                           that exists is poisoned) */
   PFLB_ERR_NAN = 4,     /* a diagnostic found non-finite fields */
   PFLB_ERR_TIMEOUT = 5, /* a bounded wait ran out */
   PFLB_ERR_BUDGET = 6,  /* request exceeds the memory budget */

@@ -52,6 +52,13 @@ pflb_status fail(pflb_status s, const std::string &msg) {
   return s;
 }
 
+// A failed device allocation: out of memory only when the allocator says so;
+// any other error (no usable device, a driver too old) is a CUDA error.
+pflb_status alloc_fail(cudaError_t e, const char *what) {
+  return fail(e == cudaErrorMemoryAllocation ? PFLB_ERR_OOM : PFLB_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
 pflb_status cuda_fail(Lattice *L, cudaError_t e, const char *what) {
   if (L) L->poisoned = true;
   return fail(PFLB_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
@@ -415,7 +422,7 @@ pflb_status pflb_create(const pflb_geometry *geom, const pflb_params *params, vo
     free_all(L);
     delete L;
     cudaGetLastError();
-    return fail(PFLB_ERR_OOM, std::string("device allocation failed: ") + cudaGetErrorString(e));
+    return alloc_fail(e, "device allocation failed");
   }
   // Upload geometry.
   std::vector<float> wgeo_f;
@@ -472,7 +479,7 @@ pflb_status pflb_init_phi(pflb_lattice *L, const double *phi_host, double P0) {
     if (e != cudaSuccess) {
       cudaGetLastError();
       L->phi0 = nullptr;
-      return fail(PFLB_ERR_OOM, "device allocation failed (init scratch)");
+      return alloc_fail(e, "device allocation failed (init scratch)");
     }
     L->dev_bytes += L->N * 8;
   }
@@ -585,7 +592,7 @@ pflb_status pflb_set_x_boundaries(pflb_lattice *L, const pflb_xbc *lo, const pfl
       if (e != cudaSuccess) {
         cudaGetLastError();
         L->bcm = nullptr;
-        return fail(PFLB_ERR_OOM, "device allocation failed (boundary states)");
+        return alloc_fail(e, "device allocation failed (boundary states)");
       }
       L->dev_bytes += (int64_t)bytes;
     }
@@ -774,7 +781,7 @@ pflb_status pflb_read(pflb_lattice *L, int field, double *host_out) {
     if (e != cudaSuccess) {
       cudaGetLastError();
       L->out = nullptr;
-      return fail(PFLB_ERR_OOM, "device allocation failed (field output)");
+      return alloc_fail(e, "device allocation failed (field output)");
     }
     L->dev_bytes += 6 * L->N * 8;
   }
@@ -969,7 +976,7 @@ extern "C" pflb_status pflb_batch_create(pflb_lattice *const *lattices, int coun
   if (e != cudaSuccess) {
     pflb_batch_destroy(b);
     cudaGetLastError();
-    return fail(PFLB_ERR_OOM, std::string("batch allocation failed: ") + cudaGetErrorString(e));
+    return alloc_fail(e, "batch allocation failed");
   }
   pflb_status st = batch_build_items(b);
   if (st != PFLB_OK) {

@@ -171,3 +171,17 @@ def test_estimate_bytes_counts_wall_nodes():
     assert empty == 3 * 19 * N * 4 + N * 5 + N * 4 + 96 * 8 + 4
     nw = 2 * n * n  # planes z = 1 and z = n-1 (periodic) touch the solid layer
     assert walled - empty == nw * (2 * 18 * 4 + 4 + 5 * 4 + 18 * 4)
+
+
+def test_no_cpu_fallback_without_a_gpu():
+    """With the library built but no GPU, a valid lattice is refused with a
+    CUDA error; nothing falls back to host computation.  (Skipped where a
+    GPU is present: there the lattice is simply created.)"""
+    from paper_2512_01032_gb300 import pflb
+    try:
+        L = pflb.Lattice(8, 8, 8)
+    except pflb.PflbError as e:
+        assert e.status == pflb.ERR_CUDA, e
+        return
+    L.close() if hasattr(L, "close") else None
+    pytest.skip("a GPU is present")
