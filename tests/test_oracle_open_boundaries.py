@@ -106,3 +106,58 @@ def test_boundary_ramp_is_linear_in_steps():
     L.set_x_boundaries(dict(type="pressure", P=0.0), dict(type="pressure", P=0.0), ramp_steps=10)
     L.step(5)
     assert p_in() == pytest.approx(0.5 * P1, rel=1e-12)
+
+
+def test_boundary_cells_emit_the_equilibria_of_their_boundary_state():
+    """Per cell, one whole step (reading R22): undoing push streaming (and
+    halfway bounce-back at the plates) recovers what each boundary cell
+    emitted, which is the equilibrium h_i = phi_b Gamma_i(u_b),
+    g_i = w_i P_b / T + rho_b (Gamma_i(u_b) - w_i) of its boundary state.
+    Velocity inlet (x = 0): u_b and phi_b as given, P_b = T sum g of the
+    adjacent cell x = 1.  Pressure outlet (x = nx-1): P_b as given, phi_b =
+    sum h and u_b = (sum c g + F/2) / rho(phi_b) of the adjacent cell
+    x = nx-2 (bulk form).  All from the pre-step populations, to rounding."""
+    nx, ny, nz = 24, 10, 2
+    solid = np.zeros((nz, ny, nx), bool)
+    solid[:, 0, :] = solid[:, -1, :] = True
+    Z, Y, X = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    phi0 = 0.5 + 0.3 * np.sin(2 * np.pi * X / nx + 0.4) * np.cos(np.pi * Y / ny)
+    F = np.array([2e-6, -1e-6, 0.0])
+    L = O.OracleLattice(nx, ny, nz, solid=solid.astype(np.uint8).reshape(-1), nthreads=2,
+                        sigma=0.01, W=4.0, M=0.02, rho_H=1.0, rho_L=1e-3, nu_H=MU, nu_L=0.1,
+                        Fex=tuple(F))
+    L.init_phi((phi0 * ~solid).reshape(-1))
+    u_in, phi_in, P_out = np.array([3e-3, 1e-3, 0.0]), 0.7, 1e-3
+    L.set_x_boundaries(dict(type="velocity", u=tuple(u_in), phi=phi_in),
+                       dict(type="pressure", P=P_out))
+    L.step(5)
+    h, g = L.populations()
+    L.step(1)
+    h1, g1 = L.populations()
+    c, w, opp = O.lattice_tables()
+    T = 1.0 / 3.0
+    flat = solid.reshape(-1)
+    worst, count = 0.0, 0
+    for z in range(nz):
+        for y in range(1, ny - 1):
+            for x, adj in ((0, 1), (nx - 1, nx - 2)):
+                cell = (z * ny + y) * nx + x
+                a = (z * ny + y) * nx + adj
+                if x == 0:
+                    phi_b, u_b, P_b = phi_in, u_in, T * g[a].sum()
+                else:
+                    phi_b = h[a].sum()
+                    rho_a = 1e-3 + phi_b * (1.0 - 1e-3)
+                    u_b, P_b = (c.T @ g[a] + 0.5 * F) / rho_a, P_out
+                rho_b = 1e-3 + phi_b * (1.0 - 1e-3)
+                G = O.gamma_vec(u_b)
+                want_h = phi_b * G
+                want_g = w * P_b / T + rho_b * (G - w)
+                for i in range(19):
+                    to = (((z + c[i, 2]) % nz) * ny + (y + c[i, 1]) % ny) * nx + (x + c[i, 0]) % nx
+                    got_h, got_g = (h1[cell, opp[i]], g1[cell, opp[i]]) if flat[to] else \
+                        (h1[to, i], g1[to, i])
+                    worst = max(worst, abs(got_h - want_h[i]), abs(got_g - want_g[i]))
+                count += 1
+    assert count == 2 * nz * (ny - 2)
+    assert worst < 1e-15  # rounding (measured 0: the same operations)
