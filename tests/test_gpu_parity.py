@@ -116,6 +116,37 @@ def test_ragged_and_tiny_lattices(dims):
         _compare(G, Orc, [1, 9], storage, 2 * p["sigma"] / init["R"], f"ragged{dims}")
 
 
+def test_zero_steps_and_a_lattice_without_fluid():
+    """Degenerate inputs: pflb_step with zero steps changes nothing (fields,
+    step counter); a lattice whose every cell is solid has no fluid cells and
+    no wall nodes, steps without error (every cell skips its update), reads
+    back zeros and reports zero mass with no non-finite value."""
+    from paper_2512_01032_gb300 import pflb
+    import synth
+    g, p, drop = synth.sessile_sphere(24, 70.0)
+    L = pflb.Lattice(g.nx, g.ny, g.nz, solid=g.solid, wall_normal=g.normals(),
+                     theta_cells=g.theta(), storage="fp32", **p)
+    L.init_tanh(0, drop["center"], drop["R"])
+    L.step(3)
+    before = {k: L.read(k) for k in ("phi", "P", "ux")}
+    L.step(0)
+    assert L.t == 3
+    for k, v in before.items():
+        assert np.array_equal(L.read(k), v), k
+    L.close()
+    S = pflb.Lattice(8, 6, 5, solid=np.ones(8 * 6 * 5, np.uint8), storage="fp32",
+                     **synth.static_droplet_params())
+    S.init_tanh(0, (4.0, 3.0, 2.0), 2.0)
+    S.set_diag_every(1)
+    S.step(4)
+    assert S.t == 4
+    for k in ("phi", "rho", "P", "ux", "uy", "uz"):
+        assert not S.read(k).any(), k
+    d = S.diag()
+    assert d["mass"] == 0.0 and d["nonfinite"] == 0 and d["u_max"] == 0.0
+    S.close()
+
+
 @pytest.mark.parametrize("tile", [(32, 8, 16), (64, 4, 7), (16, 16, 3), (32, 4, 32), (8, 8, 5), (16, 8, 4)])
 def test_tile_shapes_bitwise_identical(tile):
     """Every launch shape of the fused kernel gives the same bits as the
