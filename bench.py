@@ -113,15 +113,17 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
+        self.out = None
         self.path = os.path.join(os.environ.get("PFLB_CLOCKS_DIR", tempfile.gettempdir()),
                                  f"pflb_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.out = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv",
-                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "100"], stdout=self.out, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
@@ -133,6 +135,7 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
+        self.out.close()
         sm, smax, reasons = [], [], set()
         try:
             for ln in open(self.path).read().strip().splitlines()[1:]:
