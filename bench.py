@@ -126,6 +126,8 @@ class ClockSampler:
                  "-lms", "100"], stdout=self.out, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            if self.out is not None:
+                self.out.close()
 
     def stop(self):
         if self.proc is None:
