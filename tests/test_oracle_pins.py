@@ -739,3 +739,51 @@ def test_one_step_moment_identities_at_walls():
     assert scale["h1"] > 1e-4 and scale["g1"] > 1e-6 and scale["g0"] > 1e-8
     assert err["h0"] < 4e-15 and err["h1"] < 1e-15 and err["h2"] < 4e-15, err
     assert err["g1"] < 1e-15 and err["g0"] < 1e-15, err
+
+
+def test_ghost_update_lags_one_step_and_blends():
+    """Readings R11-R12 per wall node, over one whole step on a curved wall:
+    the ghosts a step uses are b * (the previous step's ghosts) + (1 - b) *
+    (the fresh ghosts of Eqs. 12-15).  The fresh ghosts take phi of the wall
+    node and grad phi from the Eq. 13 stencil, in which each solid neighbour
+    reads the previous step's ghost of that link.  (The fresh-ghost function
+    itself is pinned by the planar-wall closed form.)"""
+    import synth
+    from oracle.oracle import make_params
+    g, p, drop = synth.sessile_sphere(24, 60.0)
+    p = dict(p, blend=0.95)
+    L = O.OracleLattice(g.nx, g.ny, g.nz, solid=g.solid, wall_normal=g.normals(),
+                        theta_cells=g.theta(), nthreads=2, **p)
+    L.init_phi(O.tanh_phi(0, (g.nx, g.ny, g.nz), drop["center"], drop["R"], p["W"])
+               * (1 - g.solid))
+    L.step(4)
+    G0 = L.ghosts()
+    h, _ = L.populations()
+    L.step(1)
+    G1 = L.ghosts()
+    c, _, _ = O.lattice_tables()
+    prm = make_params(**p)
+    nx, ny, nz = g.nx, g.ny, g.nz
+    solid = g.solid.astype(bool)
+    phi = h.sum(axis=1) * ~solid
+    nrm = L.normals()
+    theta = g.theta()
+    worst, nodes, moved = 0.0, 0, 0.0
+    for cell in np.nonzero(~solid)[0]:
+        x, y, z = cell % nx, (cell // nx) % ny, cell // (nx * ny)
+        nbr = [(((z + c[i, 2]) % nz) * ny + (y + c[i, 1]) % ny) * nx + (x + c[i, 0]) % nx
+               for i in range(19)]
+        links = [i for i in range(1, 19) if solid[nbr[i]]]
+        if not links:
+            continue
+        nodes += 1
+        val = [phi[cell]] + [G0[cell, i] if solid[nbr[i]] else phi[nbr[i]] for i in range(1, 19)]
+        grad, _ = O.cd_stencil(val)
+        mask = sum(1 << i for i in links)
+        fresh = O.ghost_values(prm, phi[cell], nrm[cell], theta[cell], grad, mask)
+        for i in links:
+            want = 0.95 * G0[cell, i] + 0.05 * fresh[i]
+            worst = max(worst, abs(G1[cell, i] - want))
+            moved = max(moved, abs(G1[cell, i] - G0[cell, i]))
+    assert nodes > 500 and moved > 1e-4
+    assert worst < 1e-14
