@@ -185,3 +185,15 @@ def test_no_cpu_fallback_without_a_gpu():
         return
     L.close() if hasattr(L, "close") else None
     pytest.skip("a GPU is present")
+
+
+@pytest.mark.parametrize("kw,exc", [(dict(sigmaa=0.1), KeyError), (dict(storage="fp8"), KeyError),
+                                    (dict(solid=[1, 0]), ValueError),
+                                    (dict(theta_cells=[1.0, 0.0]), ValueError),
+                                    (dict(wall_normal=[1.0, 0.0]), ValueError)])
+def test_binding_rejects_malformed_arguments(kw, exc):
+    """The binding refuses misspelt parameters, unknown storage names and
+    geometry arrays of the wrong size before any library call."""
+    from paper_2512_01032_gb300 import pflb
+    with pytest.raises(exc):
+        pflb.Lattice(4, 4, 4, **kw)
