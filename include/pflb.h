@@ -29,6 +29,7 @@
 #ifndef PFLB_H
 #define PFLB_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus

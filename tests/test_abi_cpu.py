@@ -197,3 +197,16 @@ def test_binding_rejects_malformed_arguments(kw, exc):
     from paper_2512_01032_gb300 import pflb
     with pytest.raises(exc):
         pflb.Lattice(4, 4, 4, **kw)
+
+
+@pytest.mark.parametrize("lang,std", [("c", "c99"), ("c++", "c++11")])
+def test_header_is_self_contained(tmp_path, lang, std):
+    """include/pflb.h compiles on its own, warning-free, as strict C99 and
+    C++11 (a C ABI must not rely on what the caller included before it)."""
+    src = tmp_path / "only.c"
+    src.write_text('#include "pflb.h"\nint main(void) { return 0; }\n')
+    cc = "gcc" if lang == "c" else "g++"
+    r = subprocess.run([cc, f"-std={std}", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                        "-fsyntax-only", "-x", lang, "-I", os.path.join(ROOT, "include"),
+                        str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
