@@ -210,3 +210,49 @@ def test_header_is_self_contained(tmp_path, lang, std):
                         "-fsyntax-only", "-x", lang, "-I", os.path.join(ROOT, "include"),
                         str(src)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_c_program_links_and_calls_the_library(tmp_path):
+    """A plain C99 program includes pflb.h, links libpflb.so and calls the
+    entry points that need no GPU: default parameters, argument checks with
+    their error messages, the footprint estimate and the null-tolerant
+    destructors."""
+    from paper_2512_01032_gb300 import pflb
+    lib = pflb.lib_path()
+    src = tmp_path / "use.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "pflb.h"
+int main(void) {
+  pflb_params p;
+  pflb_default_params(&p);
+  if (p.gamma != -22.5 || p.blend != 0.95 || p.storage != PFLB_STORAGE_FP32) return 1;
+  pflb_lattice *L = NULL;
+  if (pflb_create(NULL, &p, NULL, &L) != PFLB_ERR_ARG || L != NULL) return 2;
+  if (strlen(pflb_last_error()) == 0) return 3;
+  uint8_t solid[8 * 8 * 8];
+  memset(solid, 0, sizeof solid);
+  memset(solid, 1, 8 * 8);  /* the plane z = 0 */
+  pflb_geometry g = {8, 8, 8, solid, NULL, NULL};
+  int64_t bytes = pflb_estimate_bytes(&g, PFLB_STORAGE_FP32);
+  if (bytes <= 0) return 4;
+  p.nu_H = 0.0;  /* tau = 1/2 */
+  if (pflb_create(&g, &p, NULL, &L) != PFLB_ERR_ARG) return 5;
+  if (pflb_step(NULL, 1) != PFLB_ERR_ARG) return 6;
+  pflb_destroy(NULL);
+  pflb_batch_destroy(NULL);
+  pflb_server_destroy(NULL);
+  printf("%lld\n", (long long)bytes);
+  return 0;
+}
+''')
+    exe = tmp_path / "use"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(src), lib, f"-Wl,-rpath,{os.path.dirname(lib)}", "-o", str(exe)],
+                   check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stderr)
+    solid = np.zeros((8, 8, 8), np.uint8)
+    solid[0] = 1
+    assert int(r.stdout) == pflb.estimate_bytes(8, 8, 8, solid)
