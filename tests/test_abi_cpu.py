@@ -256,3 +256,21 @@ int main(void) {
     solid = np.zeros((8, 8, 8), np.uint8)
     solid[0] = 1
     assert int(r.stdout) == pflb.estimate_bytes(8, 8, 8, solid)
+
+
+def test_binding_declares_every_entry_point():
+    """Every function of include/pflb.h has ctypes argument types and the
+    return type of its C declaration (an undeclared int64_t return would be
+    truncated to int)."""
+    import ctypes as C
+    from paper_2512_01032_gb300 import pflb
+    lib = pflb.load()
+    txt = open(os.path.join(ROOT, "include", "pflb.h")).read()
+    want = {"pflb_status": C.c_int, "void": None, "int64_t": C.c_int64,
+            "const char *": C.c_char_p}
+    decls = re.findall(r"^\s*([a-z_0-9 ]+?\**)\s*\b(pflb_[a-z_0-9]+)\s*\(", txt, re.M)
+    assert len(decls) == len(_declared())
+    for rt, name in decls:
+        f = getattr(lib, name)
+        assert f.argtypes is not None, name
+        assert f.restype == want[rt.strip()], (name, rt, f.restype)
