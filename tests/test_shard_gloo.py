@@ -29,6 +29,12 @@ def test_assign_partitions_and_balances():
         assert max(loads) <= sum(cells) / world + max(cells)
         assert parts == shard.assign(cells, world)  # deterministic
     assert shard.assign([5, 5], 4)[2:] == [[], []]
+    assert shard.assign([], 3) == [[], [], []]
+    # equal sizes: lowest index to the least-loaded rank, ties to the lowest rank
+    assert shard.assign([4, 4, 4], 2) == [[0, 2], [1]]
+    assert shard.my_items([4, 4, 4], 1, 2) == [1]
+    with pytest.raises(ValueError):
+        shard.my_items([4], 2, 2)
     with pytest.raises(ValueError):
         shard.assign(cells, 0)
 
