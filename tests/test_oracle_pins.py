@@ -92,13 +92,33 @@ def test_cd_stencil_exact_for_quadratics():
 
 def test_chem_pot_vanishes_on_exact_profile():
     """Eq. 7 with the exact second derivative of the tanh profile of Eq. 12
-    is zero: this fixes both coefficients (48 sigma/W and 3 sigma W/2)."""
+    is zero: this fixes the ratio of its two coefficients (48 sigma/W and
+    3 sigma W/2) to the width W; their common scale is pinned below."""
     for W, sigma in ((4.0, 0.01), (2.5, 0.005)):
         p = _params(W=W, sigma=sigma)
         for x in np.linspace(-3 * W, 3 * W, 41):
             phi = 0.5 * (1 + math.tanh(2 * x / W))
             d2 = (16.0 / W ** 2) * phi * (1 - phi) * (1 - 2 * phi)
             assert abs(O.chem_pot(p, phi, d2)) < 1e-16
+
+
+def test_chem_pot_scale_gives_the_surface_tension():
+    """The absolute scale of Eq. 7: with the double-well coefficient beta and
+    the gradient coefficient kappa read off the oracle's chemical potential
+    (mu = 4 beta phi (phi - 1)(phi - 1/2) - kappa lap phi), the interface
+    tension of the free energy is sigma: sqrt(2 kappa beta) / 6 = sigma, and
+    the excess energy kappa * integral (phi')^2 dx of the Eq. 12 profile
+    (trapezoid rule over +-8 W) equals sigma."""
+    for W, sigma in ((4.0, 0.01), (2.5, 0.005)):
+        p = _params(W=W, sigma=sigma)
+        kappa = O.chem_pot(p, 0.3, 0.0) - O.chem_pot(p, 0.3, 1.0)
+        beta = O.chem_pot(p, 0.25, 0.0) / (4 * 0.25 * (0.25 - 1) * (0.25 - 0.5))
+        assert math.sqrt(2 * kappa * beta) / 6 == pytest.approx(sigma, rel=1e-14)
+        x = np.linspace(-8 * W, 8 * W, 20001)
+        phi = 0.5 * (1 + np.tanh(2 * x / W))
+        dphi = (4.0 / W) * phi * (1 - phi)
+        energy = kappa * np.sum(0.5 * (dphi[1:] ** 2 + dphi[:-1] ** 2) * np.diff(x))
+        assert energy == pytest.approx(sigma, rel=1e-6)
 
 
 def test_delta_theta_hand_values():
