@@ -17,8 +17,13 @@ What crosses a slab face each step, and nothing else:
     5 directions per population set (those with c_z = -1 or +1), nx * ny
     values each per face.
 So each face cell costs 1 + 2 * 5 = 11 values per step (44 B at FP32).
-No free-slip band or open boundaries here (they are slab-local rules that
-add nothing to the exchange).
+The free-slip band (R14) can send a population across a face too: an edge
+link into a wall whose tangent has a z component is reflected onto the
+neighbour x + (0, 0, c_z), possibly in the next slab.  It lands in a slot
+(that cell, a direction with c_z = +-1) whose ordinary source is the solid
+cell, so it travels in the same 5-direction message, in a place ordinary
+streaming leaves empty: the exchange does not grow.  Open boundaries are not
+covered here.
 """
 from __future__ import annotations
 
@@ -51,6 +56,7 @@ class Slab:
         self.phi = np.zeros((z1 - z0, self.ny, self.nx))
         self.halo_lo = self.halo_hi = None
         self.values_sent = 0
+        self.reflected_across = 0
 
     # -- indexing
     def owns(self, z):
@@ -145,7 +151,11 @@ class Slab:
                 t = self.nbr(z, y, x, i)
                 if self.solid3[t]:
                     self.h2[c, OPP[i]] = hs[i]
-                    self.g2[c, OPP[i]] = gs[i]
+                    sp = self.specular(z, y, x, i, f) if self.kw.get("free_slip") else None
+                    if sp is None:
+                        self.g2[c, OPP[i]] = gs[i]
+                    else:
+                        self.put_g(sp[0], sp[1], gs[i], out)
                 elif self.owns(t[0]):
                     self.h2[self.idx(*t), i] = hs[i]
                     self.g2[self.idx(*t), i] = gs[i]
@@ -160,6 +170,48 @@ class Slab:
         self.values_sent += 4 * 5 * nx * ny
         return out
 
+    def specular(self, z, y, x, i, f):
+        """Reading R14: the edge link i of wall node (z, y, x) into a solid
+        cell, whose step along one of its two axes is solid and along the
+        other fluid, is reflected across the solid axis onto the tangential
+        neighbour when phi at both cells lies in the band; returns (that
+        cell, reflected direction) or None."""
+        axes = [k for k in range(3) if CV[i, k] != 0]
+        if len(axes) != 2:
+            return None
+        pos = (x, y, z)
+        n = (self.nx, self.ny, self.nz)
+
+        def step(k):
+            q = list(pos)
+            q[k] = (q[k] + CV[i, k]) % n[k]
+            return q[2], q[1], q[0]
+
+        sa, sb = (bool(self.solid3[step(k)]) for k in axes)
+        if sa == sb:
+            return None
+        wall, tang = (axes[0], axes[1]) if sa else (axes[1], axes[0])
+        yt = step(tang)
+        lo, hi = self.kw["band_lo"], self.kw["band_hi"]
+        if not (lo <= f <= hi and lo <= self.phi_at(*yt) <= hi):
+            return None
+        cr = CV[i].copy()
+        cr[wall] = -cr[wall]
+        return yt, int(np.nonzero((CV == cr).all(axis=1))[0][0])
+
+    def put_g(self, t, r, v, out):
+        """Write g population r arriving at cell t, here or in a face message."""
+        if self.owns(t[0]):
+            self.g2[self.idx(*t), r] = v
+        elif t[0] == (self.z0 - 1) % self.nz:
+            assert np.isnan(out["lo_g"][DOWN.index(r), t[1], t[2]])
+            out["lo_g"][DOWN.index(r), t[1], t[2]] = v
+            self.reflected_across += 1
+        else:
+            assert np.isnan(out["hi_g"][UP.index(r), t[1], t[2]])
+            out["hi_g"][UP.index(r), t[1], t[2]] = v
+            self.reflected_across += 1
+
     def receive(self, from_below, from_above):
         """Populations streamed in by the slab below (its upward ones, into
         this slab's first plane) and the slab above (its downward ones, into
@@ -170,6 +222,7 @@ class Slab:
                     for x in range(self.nx):
                         if not np.isnan(hh[j, y, x]):
                             self.h2[self.idx(z, y, x), i] = hh[j, y, x]
+                        if not np.isnan(gg[j, y, x]):
                             self.g2[self.idx(z, y, x), i] = gg[j, y, x]
 
     def swap(self):
@@ -203,14 +256,15 @@ def run(dims, solid3, normals, theta, kw, h, g, ghost, bounds, steps):
             s.receive((below["hi_h"], below["hi_g"]), (above["lo_h"], above["lo_g"]))
             s.swap()
     cat = lambda a: np.concatenate([getattr(s, a) for s in slabs])
+    run.reflected_across = sum(s.reflected_across for s in slabs)
     return cat("h"), cat("g"), cat("ghost"), [s.values_sent / steps for s in slabs]
 
 
 # ------------------------------------------------------------ a test case
 DIMS = (10, 8, 9)
 KW = dict(sigma=0.01, W=4.0, M=0.02, rho_H=1.0, rho_L=1e-3, nu_H=0.1, nu_L=0.05,
-          theta_deg=60.0, blend=0.95, F_mode=1, mobility_corr=1, free_slip=0,
-          Fex=(1e-6, 0.0, -2e-6))
+          theta_deg=60.0, blend=0.95, F_mode=1, mobility_corr=1, free_slip=1,
+          band_lo=0.5, band_hi=0.95, Fex=(1e-6, 0.0, -2e-6))
 
 
 def case():
