@@ -22,8 +22,11 @@ link into a wall whose tangent has a z component is reflected onto the
 neighbour x + (0, 0, c_z), possibly in the next slab.  It lands in a slot
 (that cell, a direction with c_z = +-1) whose ordinary source is the solid
 cell, so it travels in the same 5-direction message, in a place ordinary
-streaming leaves empty: the exchange does not grow.  Open boundaries are not
-covered here.
+streaming leaves empty: the exchange does not grow.  Open x boundaries
+(R22) are slab-local as well: a boundary cell's state comes from the
+adjacent cell in x, in the same z plane, and its phi_b reaches the
+neighbouring slab's stencils through the phi plane, which is formed after
+the boundary states.
 """
 from __future__ import annotations
 
@@ -39,7 +42,7 @@ UP = [i for i in range(Q) if CV[i, 2] == 1]
 
 
 class Slab:
-    def __init__(self, dims, z0, z1, solid3, normals, theta, kw, h, g, ghost):
+    def __init__(self, dims, z0, z1, solid3, normals, theta, kw, h, g, ghost, xbc=None):
         self.nx, self.ny, self.nz = dims
         self.z0, self.z1 = z0, z1
         self.kw = kw
@@ -57,6 +60,8 @@ class Slab:
         self.halo_lo = self.halo_hi = None
         self.values_sent = 0
         self.reflected_across = 0
+        self.xbc = xbc  # None, or the (x = 0, x = nx - 1) boundary specs
+        self.bstate = {}
 
     # -- indexing
     def owns(self, z):
@@ -93,6 +98,43 @@ class Slab:
                 s += float(v)
             self.phi[z - self.z0, y, x] = s
 
+    def boundary_side(self, z, y, x):
+        if self.xbc is None or self.solid3[z, y, x]:
+            return -1
+        return 0 if x == 0 else (1 if x == self.nx - 1 else -1)
+
+    def boundary_states(self):
+        """Reading R22 for the owned planes: each boundary cell's (phi_b, P_b,
+        u_b) from the given values and the adjacent interior cell's pre-step
+        bulk moments; phi of the boundary cell becomes phi_b."""
+        if self.xbc is None:
+            return
+        kw, T = self.kw, 1.0 / 3.0
+        F = kw.get("Fex", (0.0, 0.0, 0.0))
+        for z in range(self.z0, self.z1):
+            for y in range(self.ny):
+                for side, xb, xa in ((0, 0, 1), (1, self.nx - 1, self.nx - 2)):
+                    spec = self.xbc[side]
+                    phia, Pa, ua = 0.0, 0.0, [0.0, 0.0, 0.0]
+                    if not self.solid3[z, y, xa]:
+                        g = self.g[self.idx(z, y, xa)]
+                        s0, m = 0.0, [0.0, 0.0, 0.0]
+                        for i in range(Q):
+                            s0 += g[i]
+                            for a in range(3):
+                                m[a] += CV[i, a] * g[i]
+                        phia = self.phi[z - self.z0, y, xa]
+                        rho = kw["rho_L"] + phia * (kw["rho_H"] - kw["rho_L"])
+                        ua = [(m[a] + 0.5 * F[a]) / rho for a in range(3)]
+                        Pa = T * s0
+                    if spec["type"] == "pressure":
+                        st = (phia, spec["P"], ua)
+                    else:
+                        st = (spec["phi"], Pa, list(spec["u"]))
+                    if not self.solid3[z, y, xb]:
+                        self.phi[z - self.z0, y, xb] = st[0]
+                    self.bstate[(z, y, side)] = st
+
     def face_planes(self):
         """(first plane, last plane) of phi: sent to the slab below / above."""
         self.values_sent += 2 * self.nx * self.ny
@@ -116,7 +158,7 @@ class Slab:
         old = self.ghost.copy()
         b = self.kw.get("blend", 0.95)
         for z, y, x in self.cells():
-            if self.solid3[z, y, x]:
+            if self.solid3[z, y, x] or self.boundary_side(z, y, x) >= 0:
                 continue
             c = self.idx(z, y, x)
             grad, _, mask = self.stencil(z, y, x, old)
@@ -141,17 +183,26 @@ class Slab:
                 continue
             c = self.idx(z, y, x)
             f = self.phi[z - self.z0, y, x]
-            grad, lap, _ = self.stencil(z, y, x, self.ghost)
-            rho, P, u, mu = O.macros_cell(self.p, self.g[c], f, grad, lap)
-            heq = O.h_eq(self.p, f, u, grad, lap)
-            hs = self.h[c] - (self.h[c] - heq) / self.tau_phi
-            K, E = O.force_and_eq(self.p, rho, P, u, mu, grad)
-            gs, _ = O.filtered_collide(self.g[c], K, E, O.tau_mix(self.p, f))
+            side = self.boundary_side(z, y, x)
+            if side >= 0:
+                phi_b, P_b, u_b = self.bstate[(z, y, side)]
+                G = O.gamma_vec(u_b)
+                rho_b = self.kw["rho_L"] + phi_b * (self.kw["rho_H"] - self.kw["rho_L"])
+                hs = phi_b * G
+                gs = _W * P_b / (1.0 / 3.0) + rho_b * (G - _W)
+            else:
+                grad, lap, _ = self.stencil(z, y, x, self.ghost)
+                rho, P, u, mu = O.macros_cell(self.p, self.g[c], f, grad, lap)
+                heq = O.h_eq(self.p, f, u, grad, lap)
+                hs = self.h[c] - (self.h[c] - heq) / self.tau_phi
+                K, E = O.force_and_eq(self.p, rho, P, u, mu, grad)
+                gs, _ = O.filtered_collide(self.g[c], K, E, O.tau_mix(self.p, f))
             for i in range(Q):
                 t = self.nbr(z, y, x, i)
                 if self.solid3[t]:
                     self.h2[c, OPP[i]] = hs[i]
-                    sp = self.specular(z, y, x, i, f) if self.kw.get("free_slip") else None
+                    sp = (self.specular(z, y, x, i, f)
+                          if self.kw.get("free_slip") and side < 0 else None)
                     if sp is None:
                         self.g2[c, OPP[i]] = gs[i]
                     else:
@@ -235,15 +286,17 @@ def split(nz, parts):
     return [(edges[k], edges[k + 1]) for k in range(parts)]
 
 
-def run(dims, solid3, normals, theta, kw, h, g, ghost, bounds, steps):
+def run(dims, solid3, normals, theta, kw, h, g, ghost, bounds, steps, xbc=None):
     """Advance the slabs of ``bounds`` together for ``steps`` steps in one
     process; returns the reassembled h, g, ghosts and the values each slab
     sent per step."""
-    slabs = [Slab(dims, z0, z1, solid3, normals, theta, kw, h, g, ghost) for z0, z1 in bounds]
+    slabs = [Slab(dims, z0, z1, solid3, normals, theta, kw, h, g, ghost, xbc)
+             for z0, z1 in bounds]
     n = len(slabs)
     for _ in range(steps):
         for s in slabs:
             s.compute_phi()
+            s.boundary_states()
         faces = [s.face_planes() for s in slabs]
         for k, s in enumerate(slabs):
             s.halo_lo = faces[(k - 1) % n][1]
@@ -321,6 +374,7 @@ def rank_main(rank, world, port, steps, out_path):
 
         for _ in range(steps):
             s.compute_phi()
+            s.boundary_states()
             first, last = s.face_planes()
             (s.halo_lo,), (s.halo_hi,) = swap_msgs([last], [first], 10)
             s.update_ghosts()

@@ -86,3 +86,21 @@ def test_two_gloo_ranks_exchange_the_faces(reference, tmp_path):
     assert np.array_equal(got["h"], h1) and np.array_equal(got["g"], g1)
     assert np.array_equal(got["ghost"], gh1)
     assert list(got["sent"]) == [2 * 11 * DIMS[0] * DIMS[1]] * 2
+
+
+def test_slabs_with_open_x_boundaries():
+    """Open x boundaries (a velocity inlet at x = 0, a pressure outlet at
+    x = nx - 1) do not change the exchange: 2 and 3 slabs still equal one
+    slab bit for bit, and one slab is the oracle's step."""
+    L, (solid3, nrm, theta, h, g, gh) = S.case()
+    xbc = (dict(type="velocity", u=(3e-3, 1e-3, 0.0), phi=0.2), dict(type="pressure", P=1e-3))
+    L.set_x_boundaries(*xbc)
+    one = S.run(DIMS, solid3, nrm, theta, KW, h, g, gh, [(0, DIMS[2])], STEPS, xbc)
+    L.step(STEPS)
+    hc, gc = L.populations()
+    assert np.abs(one[0] - hc).max() < 1e-14 and np.abs(one[1] - gc).max() < 1e-14
+    assert np.abs(one[2] - L.ghosts()).max() < 1e-14
+    for parts in (2, 3):
+        got = S.run(DIMS, solid3, nrm, theta, KW, h, g, gh, S.split(DIMS[2], parts), STEPS, xbc)
+        for a, b in zip(got[:3], one[:3]):
+            assert np.array_equal(a, b)
