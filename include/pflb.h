@@ -51,9 +51,12 @@ typedef enum {
 } pflb_status;
 
 /* Population storage.  The collision computes in FP64 for FP64 storage and
- * in FP32 otherwise.  The 16-bit formats store weight-scaled deviations:
- * h_i / w_i - 1/2 and g_i / w_i (bytes per cell and step: 305 at FP32,
- * 153 at FP16/BF16, 609 at FP64). */
+ * in FP32 otherwise.  The 16-bit formats store each population divided by
+ * its lattice weight, h_i / w_i and g_i / w_i (at rest these are phi and
+ * P/T, so every stored value has the scale of a macroscopic field), with
+ * the rounding of a cell's moving h compensated in its rest population so
+ * that total phi does not drift (bytes per cell and step: 305 at FP32, 157
+ * at FP16/BF16, 609 at FP64). */
 enum { PFLB_STORAGE_FP64 = 0, PFLB_STORAGE_FP32 = 1, PFLB_STORAGE_FP16 = 2,
        PFLB_STORAGE_BF16 = 3 };
 
@@ -61,11 +64,20 @@ enum { PFLB_STORAGE_FP64 = 0, PFLB_STORAGE_FP32 = 1, PFLB_STORAGE_FP16 = 2,
 enum { PFLB_FIELD_PHI = 0, PFLB_FIELD_RHO = 1, PFLB_FIELD_P = 2,
        PFLB_FIELD_UX = 3, PFLB_FIELD_UY = 4, PFLB_FIELD_UZ = 5 };
 
-/* Step kernels: one fused z-marching pass per step (default), a phi pass
- * followed by a per-cell pass, or the fused pass with h staged through
- * shared memory by TMA (FP32 storage, nx a multiple of 4 and nx >= 64;
- * otherwise it falls back to the default). */
-enum { PFLB_KERNEL_FUSED = 0, PFLB_KERNEL_TWOPASS = 1, PFLB_KERNEL_FUSED_TMA = 2 };
+/* Step kernels.  Every kind computes the same step; they differ in how the
+ * populations reach the arithmetic:
+ *   PFLB_KERNEL_PIPE (default): the fused z-marching pass with each thread's
+ *     populations of the next planes copied into shared memory one plane
+ *     ahead (cp.async in 16-byte chunks), 32 x 4 tiles, pair form of the
+ *     collision; periodic x and nx a multiple of 4 (of 8 at FP16/BF16
+ *     storage), otherwise PFLB_KERNEL_FUSED runs;
+ *   PFLB_KERNEL_FUSED: one fused z-marching pass with direct loads;
+ *   PFLB_KERNEL_TWOPASS: a phi pass followed by a per-cell pass;
+ *   PFLB_KERNEL_FUSED_TMA: the fused pass with h staged through shared
+ *     memory by TMA (FP32 storage, nx a multiple of 4 and nx >= 64;
+ *     otherwise PFLB_KERNEL_FUSED runs). */
+enum { PFLB_KERNEL_FUSED = 0, PFLB_KERNEL_TWOPASS = 1, PFLB_KERNEL_FUSED_TMA = 2,
+       PFLB_KERNEL_PIPE = 3 };
 
 /* Geometry, read during pflb_create only.
  *   solid       : host, nx*ny*nz bytes, nonzero = solid voxel.
@@ -117,7 +129,15 @@ typedef struct {
  *   cl_count, cl_mean[3], cl_m2[3] : wall nodes with 0.25 <= phi <= 0.75
  *                 (contact-line band): count, mean and mean square position
  *   kinetic     : sum of rho |u|^2 / 2
- *   nonfinite   : number of fluid cells with a non-finite phi, P or u */
+ *   nonfinite   : number of fluid cells with a non-finite phi, P or u
+ *   front_x, rear_x : interface position along x (Sec. III C: the phi = 0.5
+ *                 contour), over fluid cells of the region box whose +x
+ *                 neighbour is fluid, linearly interpolated between the two:
+ *                 front_x = the largest x at which phi falls through 0.5
+ *                 going +x (the advancing front of liquid entering from low
+ *                 x), rear_x = the smallest x at which phi rises through 0.5;
+ *                 -1 where there is no such crossing.  On a periodic x axis a
+ *                 crossing between x = nx-1 and x = 0 lies in [nx-1, nx). */
 typedef struct {
   int64_t step;
   double mass, n_heavy, p_heavy, p_light, n_p_heavy, n_p_light, dp, u_max;
@@ -125,6 +145,7 @@ typedef struct {
   double cl_count, cl_mean[3], cl_m2[3];
   double kinetic;
   double nonfinite;
+  double front_x, rear_x;
 } pflb_diag_t;
 
 /* Fill p with the paper's defaults: gamma = -22.5, phi_M = 0.8,
@@ -299,17 +320,23 @@ pflb_status pflb_load(pflb_lattice *L, const char *path);
  *   h_dev, g_dev : device, FP32, [19][N] each (direction-major, x fastest),
  *                slot i holding the population arriving in direction i (the
  *                layout pflb_save writes after an even number of steps).
- *   params     : model parameters (host, read during the call).
+ *   params     : model parameters (host, read during the call); storage
+ *                must be PFLB_STORAGE_FP32, else PFLB_ERR_ARG.
  *   fields_dev : device, 6*N doubles (phi, rho, P, ux, uy, uz), or NULL.
  *   diag_out   : host, or NULL (at least one output); region_mass is the
- *                whole box, the contact-line fields are zero, step is -1.
+ *                whole box, the contact-line fields are zero, front_x and
+ *                rear_x are -1, step is -1.
  *   cuda_stream: stream to order the work on (NULL = legacy default); the
- *                call synchronises it when diag_out is given.
- * The first call on a device looks up the scratch addresses for that device
- * (cudaGetSymbolAddress with the device current); make that first call
- * before any stream capture.  Every call shares the same scratch, cleared at
- * the start of each call: calls that overlap on the GPU (different streams
- * or threads) race and must be serialised by the caller. */
+ *                call synchronises it when diag_out is given, and with
+ *                diag_out given on a stream that is being captured it
+ *                returns PFLB_ERR_ARG without enqueuing anything.
+ * The first call on a device loads this entry point's device code on that
+ * device (which is when the scratch is reserved) and looks up the scratch
+ * addresses for it (cudaGetSymbolAddress with the device current); make that
+ * first call before any stream capture.  Later calls allocate nothing.
+ * Every call shares the same scratch, cleared at the start of each call:
+ * calls that overlap on the GPU (different streams or threads) race and must
+ * be serialised by the caller. */
 pflb_status pflb_fields_noalloc(int nx, int ny, int nz, const float *h_dev, const float *g_dev,
                                 const pflb_params *params, double *fields_dev,
                                 pflb_diag_t *diag_out, void *cuda_stream);

@@ -286,8 +286,9 @@ void free_all(Lattice *L) {
 int64_t bytes_for(long long N, long long nw, int storage) {
   const int64_t e = (int64_t)storage_bytes(storage);
   const int64_t r = (int64_t)compute_bytes(storage);
-  return (2 * (int64_t)h_slots_of(storage) + 19) * N * e + 2 * 18 * nw * e + N * (1 + 4) +
-         nw * 4 + 5 * nw * r + 18 * nw * r + N * r + 96 * 8 + 4;
+  const int64_t flag_bytes = (N + 3) & ~(int64_t)3;  // whole 4-byte words
+  return (2 * (int64_t)h_slots_of(storage) + 19) * N * e + 2 * 18 * nw * e + flag_bytes +
+         N * 4 + nw * 4 + 5 * nw * r + 18 * nw * r + N * r + 96 * 8 + 4;
 }
 
 // TMA descriptors of the two h buffers (4-D: x, y, z, direction; box
@@ -410,7 +411,7 @@ pflb_status pflb_create(const pflb_geometry *geom, const pflb_params *params, vo
   A(&L->g, 19 * N * E);
   A(&L->wp[0], 18 * nw * E);
   A(&L->wp[1], 18 * nw * E);
-  A((void **)&L->flags, N);
+  A((void **)&L->flags, (N + 3) & ~(size_t)3);  // whole 4-byte words (staged copies)
   A((void **)&L->widx, N * sizeof(int));
   A((void **)&L->wmask, nw * sizeof(uint32_t));
   A(&L->wgeo, 5 * nw * Rb);
@@ -437,6 +438,8 @@ pflb_status pflb_create(const pflb_geometry *geom, const pflb_params *params, vo
   e = cudaStreamCreateWithFlags(&L->aux, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L->ev_init, cudaEventDisableTiming);
   cudaStream_t st = L->aux;
+  if (e == cudaSuccess && (N & 3))
+    e = cudaMemsetAsync(L->flags + N, 0, ((N + 3) & ~(size_t)3) - N, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(L->flags, hg.flags.data(), N, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
@@ -555,7 +558,8 @@ pflb_status pflb_set_region(pflb_lattice *L, const int box[6]) {
 pflb_status pflb_set_kernel(pflb_lattice *L, int kind, int bx, int by, int lz) {
   pflb_status s = check_lattice(L);
   if (s != PFLB_OK) return s;
-  if (kind != PFLB_KERNEL_FUSED && kind != PFLB_KERNEL_TWOPASS && kind != PFLB_KERNEL_FUSED_TMA)
+  if (kind != PFLB_KERNEL_FUSED && kind != PFLB_KERNEL_TWOPASS && kind != PFLB_KERNEL_FUSED_TMA &&
+      kind != PFLB_KERNEL_PIPE)
     return fail(PFLB_ERR_ARG, "unknown kernel");
   if (lz < -1) return fail(PFLB_ERR_ARG, "lz must be > 0, 0 (keep) or -1 (automatic)");
   const int nbx = bx > 0 ? bx : L->bx, nby = by > 0 ? by : L->by;
@@ -631,9 +635,12 @@ pflb_status pflb_get_kernel(const pflb_lattice *L, int out[4]) {
   if (!out) return fail(PFLB_ERR_ARG, "null output");
   const bool tma = L->kernel == PFLB_KERNEL_FUSED_TMA && L->p.storage == PFLB_STORAGE_FP32 &&
                    L->tma_ok && !L->bc_on;
-  out[0] = L->kernel;
-  out[1] = tma ? 32 : L->bx;
-  out[2] = tma ? 8 : L->by;
+  const bool pipe = pflb::pipe_kernel_runs(*L);
+  // the kind that runs: the pipelined and TMA kernels fall back to the
+  // fused one where they do not apply
+  out[0] = pipe || tma || L->kernel == PFLB_KERNEL_TWOPASS ? L->kernel : PFLB_KERNEL_FUSED;
+  out[1] = tma ? 32 : (pipe ? 32 : L->bx);
+  out[2] = tma ? 8 : (pipe ? 4 : L->by);
   out[3] = L->lz;
   return PFLB_OK;
 }
@@ -671,7 +678,7 @@ static pflb_status check_device_flag(pflb_lattice *L) {
 }
 
 // Raw accumulators (32 doubles, see pflb_model.cuh D_*) to the public struct.
-static pflb_status decode_diag(const double *d, int64_t step, pflb_diag_t *out) {
+static pflb_status decode_diag(const double *d, int64_t step, int nx, pflb_diag_t *out) {
   std::memset(out, 0, sizeof *out);
   out->step = step;
   out->mass = d[pflb::D_MASS];
@@ -694,6 +701,8 @@ static pflb_status decode_diag(const double *d, int64_t step, pflb_diag_t *out) 
   }
   out->kinetic = d[pflb::D_KIN];
   out->nonfinite = d[pflb::D_NONFINITE];
+  out->front_x = d[pflb::D_FRONT] > 0 ? d[pflb::D_FRONT] - 1.0 : -1.0;
+  out->rear_x = d[pflb::D_REAR] > 0 ? (double)nx - d[pflb::D_REAR] : -1.0;
   if (out->nonfinite > 0 || !std::isfinite(out->mass))
     return fail(PFLB_ERR_NAN, "non-finite values in the fields");
   return PFLB_OK;
@@ -704,7 +713,7 @@ static pflb_status fetch_diag(pflb_lattice *L, const double *dev, pflb_diag_t *o
   CK(L, cudaMemcpyAsync(d, dev, sizeof d, cudaMemcpyDeviceToHost, L->stream));
   pflb_status fs = check_device_flag(L);
   if (fs != PFLB_OK) return fs;
-  return decode_diag(d, L->step, out);
+  return decode_diag(d, L->step, L->nx, out);
 }
 
 pflb_status pflb_last_diag_async(pflb_lattice *L, pflb_diag_raw_t *raw, int64_t *ticket) {
@@ -735,7 +744,7 @@ pflb_status pflb_diag_wait(pflb_lattice *L, int64_t ticket, const pflb_diag_raw_
     L->poisoned = true;
     return fail(PFLB_ERR_TIMEOUT, "a bounded wait in the step kernel ran out; state is invalid");
   }
-  return decode_diag(raw->acc, raw->step, out);
+  return decode_diag(raw->acc, raw->step, L->nx, out);
 }
 
 pflb_status pflb_step_ex(pflb_lattice *L, int64_t nsteps, int diag_last) {
@@ -857,33 +866,44 @@ pflb_status pflb_load(pflb_lattice *L, const char *path) {
     std::fclose(f);
     return fail(PFLB_ERR_ARG, "checkpoint geometry or storage differs");
   }
-  L->step = hdr[5];
-  const int rd = (int)(L->step & 1);
+  if (hdr[5] < 0) {
+    std::fclose(f);
+    return fail(PFLB_ERR_ARG, "checkpoint step is negative");
+  }
+  // Everything is read and checked on the host before any device buffer or
+  // the step counter changes: a short or oversized file leaves the lattice
+  // as it was.
+  const int64_t step = hdr[5];
+  const int rd = (int)(step & 1);
   const size_t N = (size_t)L->N, nw = (size_t)L->nw, E = L->elem;
   const size_t Rb = compute_bytes(L->p.storage);
   const size_t sizes[4] = {h_slots_of(L->p.storage) * N * E, 19 * N * E, 18 * nw * E,
                            18 * nw * Rb};
   void *dst[4] = {L->h[rd], L->g, L->wp[rd], L->ghost};
-  std::vector<char> buf;
+  std::vector<char> buf[4];
   for (int k = 0; k < 4; ++k) {
     try {
-      buf.resize(sizes[k] ? sizes[k] : 1);
+      buf[k].resize(sizes[k] ? sizes[k] : 1);
     } catch (...) {
       std::fclose(f);
       return fail(PFLB_ERR_OOM, "host allocation failed");
     }
-    if (std::fread(buf.data(), 1, sizes[k], f) != sizes[k]) {
+    if (std::fread(buf[k].data(), 1, sizes[k], f) != sizes[k]) {
       std::fclose(f);
       return fail(PFLB_ERR_ARG, "truncated checkpoint");
     }
-    cudaError_t e = cudaMemcpyAsync(dst[k], buf.data(), sizes[k], cudaMemcpyHostToDevice, L->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(L->stream);
-    if (e != cudaSuccess) {
-      std::fclose(f);
-      return cuda_fail(L, e, "checkpoint upload");
-    }
   }
+  char extra;
+  const bool trailing = std::fread(&extra, 1, 1, f) == 1;
   std::fclose(f);
+  if (trailing) return fail(PFLB_ERR_ARG, "checkpoint longer than its header states");
+  for (int k = 0; k < 4; ++k) {
+    cudaError_t e = cudaMemcpyAsync(dst[k], buf[k].data(), sizes[k], cudaMemcpyHostToDevice,
+                                    L->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(L->stream);
+    if (e != cudaSuccess) return cuda_fail(L, e, "checkpoint upload");  // poisons L
+  }
+  L->step = step;
   return PFLB_OK;
 }
 

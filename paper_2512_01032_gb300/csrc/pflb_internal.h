@@ -43,7 +43,7 @@ struct Lattice {
   int64_t ndiag = 0;          // diagnostic launches since init (ping-pong index)
   int64_t last_diag_step = -1;
   int diag_every = 0;         // pflb_step accumulates diagnostics every k-th step
-  int kernel = PFLB_KERNEL_FUSED;
+  int kernel = PFLB_KERNEL_PIPE;
   int bx = 32, by = 4, lz = 16;   // lz: planes per block in effect
   int lz_req = 0;                  // requested planes per block, 0 = automatic
   // open x boundaries (reading R22)
@@ -82,6 +82,15 @@ struct BatchDev {
   int *xlist = nullptr;       // [nxbc] lattices with open boundaries
   int nxbc = 0;
 };
+
+// The pipelined step kernel runs with periodic x and nx a multiple of the
+// values per 16-byte chunk (4 at FP32, 8 at 16-bit storage) and of 4 (its
+// 4-byte flag words), so that its row chunks and flag words are aligned;
+// elsewhere PFLB_KERNEL_PIPE falls back to the fused kernel.
+inline bool pipe_kernel_runs(const Lattice &L) {
+  const int v = 16 / (int)L.elem;
+  return L.kernel == PFLB_KERNEL_PIPE && !L.bc_on && L.nx % (v > 4 ? v : 4) == 0;
+}
 
 // Sets the thread-local message returned by pflb_last_error().
 void set_last_error(const char *msg);

@@ -74,11 +74,14 @@ __device__ __forceinline__ int bc_index(const Args<S, R> &a, int x, int yz) {
 template <class R>
 struct DiagAcc {
   R v[D_UMAX];
-  R umax;
+  R umax;          // max |u|^2
+  R front, rear;   // D_FRONT, D_REAR (maxima, 0 = no crossing)
   __device__ void zero() {
 #pragma unroll
     for (int k = 0; k < D_UMAX; ++k) v[k] = R(0);
     umax = R(0);
+    front = R(0);
+    rear = R(0);
   }
 };
 
@@ -180,7 +183,7 @@ __device__ __forceinline__ void boundary_cell(const Args<S, R> &a, int x, int y,
 // once its populations are gathered: h[] and g[] hold the streamed
 // populations, phi = sum h, val[1..18] the phi of the 18 neighbours
 // (anything for solid ones), lm/rec the wall data (0 for bulk cells).
-template <class S, class R, bool ODD, int MODE, bool DIAG, bool XBC = false>
+template <class S, class R, bool ODD, int MODE, bool DIAG, bool XBC = false, bool PAIRS = false>
 __device__ __forceinline__ void finish_cell(const Args<S, R> &a, int x, int y, int z, int c,
                                             uint8_t f, uint32_t lm, int rec, const Nbr &nb,
                                             R h[Q], R g[Q], R phi, R val[Q], DiagAcc<R> &acc) {
@@ -217,8 +220,22 @@ __device__ __forceinline__ void finish_cell(const Args<S, R> &a, int x, int y, i
     if (phi > R(0.95)) { acc.v[D_PH] += mc.P; acc.v[D_NPH] += R(1); }
     if (phi < R(0.05)) { acc.v[D_PL] += mc.P; acc.v[D_NPL] += R(1); }
     if (z >= a.reg[4] && z < a.reg[5] && x >= a.reg[0] && x < a.reg[1] && y >= a.reg[2] &&
-        y < a.reg[3])
+        y < a.reg[3]) {
       acc.v[D_REGION] += phi;
+      // phi = 0.5 crossings towards the +x neighbour (a fluid cell): the
+      // interface position of Sec. III C (front: phi falls through 0.5 along
+      // +x; rear: phi rises through it), linearly interpolated
+      if (!((lm >> 1) & 1u)) {
+        const R pn = val[1];
+        if (phi >= R(0.5) && pn < R(0.5)) {
+          const R xc = R(x) + div_(phi - R(0.5), phi - pn);
+          acc.front = xc + R(1) > acc.front ? xc + R(1) : acc.front;
+        } else if (phi < R(0.5) && pn >= R(0.5)) {
+          const R xc = R(x) + div_(R(0.5) - phi, pn - phi);
+          acc.rear = R(a.nx) - xc > acc.rear ? R(a.nx) - xc : acc.rear;
+        }
+      }
+    }
     if (wall && phi >= R(0.25) && phi <= R(0.75)) {
       acc.v[D_CLN] += R(1);
       acc.v[D_CLX] += R(x); acc.v[D_CLY] += R(y); acc.v[D_CLZ] += R(z);
@@ -242,7 +259,10 @@ __device__ __forceinline__ void finish_cell(const Args<S, R> &a, int x, int y, i
     return;
   }
 
-  collide(m, h, g, mc, phi, gx, gy, gz, lap);
+  if constexpr (PAIRS)
+    collide_pairs(m, h, g, mc, phi, gx, gy, gz, lap);
+  else
+    collide(m, h, g, mc, phi, gx, gy, gz, lap);
   store_cell<S, R, ODD>(a, c, lm, rec, nb, h, g, val,
                         m.free_slip && phi >= m.band_lo && phi <= m.band_hi);
 }
@@ -363,10 +383,18 @@ __device__ __forceinline__ void diag_warp_add(R *slot, const DiagAcc<R> &d) {
     const R t = warp_sum(d.v[k]);
     if (lane == 0) slot[k] += t;
   }
-  R um = d.umax;
+  R um = d.umax, fr = d.front, re = d.rear;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) um = fmax(um, __shfl_xor_sync(0xffffffffu, um, o));
-  if (lane == 0) slot[D_UMAX] = slot[D_UMAX] > um ? slot[D_UMAX] : um;
+  for (int o = 16; o > 0; o >>= 1) {
+    um = fmax(um, __shfl_xor_sync(0xffffffffu, um, o));
+    fr = fmax(fr, __shfl_xor_sync(0xffffffffu, fr, o));
+    re = fmax(re, __shfl_xor_sync(0xffffffffu, re, o));
+  }
+  if (lane == 0) {
+    slot[D_UMAX] = slot[D_UMAX] > um ? slot[D_UMAX] : um;
+    slot[D_FRONT] = slot[D_FRONT] > fr ? slot[D_FRONT] : fr;
+    slot[D_REAR] = slot[D_REAR] > re ? slot[D_REAR] : re;
+  }
 }
 
 template <class R>
@@ -380,13 +408,16 @@ __device__ __forceinline__ void diag_block_flush(double *diag, R (*wacc)[32]) {
   const int nwarps = (blockDim.x + 31) >> 5;
   const int k = threadIdx.x;
   if (k < D_COUNT) {
+    const bool is_max = k >= D_UMAX;
     double t = 0.0;
     for (int w = 0; w < nwarps; ++w)
-      t = (k == D_UMAX) ? fmax(t, (double)wacc[w][k]) : t + (double)wacc[w][k];
-    if (k == D_UMAX) {
-      // squared speed; non-negative doubles order like their bit patterns
-      atomicMax((unsigned long long *)(diag + k),
-                (unsigned long long)__double_as_longlong(sqrt(t)));
+      t = is_max ? fmax(t, (double)wacc[w][k]) : t + (double)wacc[w][k];
+    if (is_max) {
+      // non-negative doubles order like their bit patterns; D_UMAX holds
+      // the squared speed until here
+      if (k == D_UMAX) t = sqrt(t);
+      if (t > 0.0)
+        atomicMax((unsigned long long *)(diag + k), (unsigned long long)__double_as_longlong(t));
     } else if (t != 0.0) {
       atomicAdd(diag + k, t);
     }
@@ -422,6 +453,10 @@ __device__ __forceinline__ void diag_thread_add(R *tacc, const DiagAcc<R> &d) {
   for (int k = D_KIN; k < D_UMAX; ++k) tacc[k * nt + t] += d.v[k];
   R &um = tacc[D_UMAX * nt + t];
   um = um > d.umax ? um : d.umax;
+  R &fr = tacc[D_FRONT * nt + t];
+  fr = fr > d.front ? fr : d.front;
+  R &re = tacc[D_REAR * nt + t];
+  re = re > d.rear ? re : d.rear;
 }
 
 // Block reduction of the per-thread slots into the device accumulator
@@ -436,6 +471,8 @@ __device__ __forceinline__ void diag_thread_flush(double *diag, const R *tacc,
 #pragma unroll
   for (int k = 0; k < D_UMAX; ++k) d.v[k] = tacc[k * nt + t];
   d.umax = tacc[D_UMAX * nt + t];
+  d.front = tacc[D_FRONT * nt + t];
+  d.rear = tacc[D_REAR * nt + t];
   diag_warp_add(wacc[t >> 5], d);
   diag_block_flush(diag, wacc);
 }

@@ -8,6 +8,7 @@
 #include "pflb_batch.cuh"
 #include "pflb_internal.h"
 #include "pflb_kernels.cuh"
+#include "pflb_pipe.cuh"
 
 namespace pflb {
 
@@ -140,8 +141,47 @@ static cudaError_t launch_async_t(Lattice &L, Args<float, float> &a) {
   return cudaGetLastError();
 }
 
+// The pipelined kernel (periodic x; nx a multiple of 4, of 8 at 16-bit).
+template <class S>
+constexpr bool pipe_storage() {
+  return true;
+}
+inline bool pipe_eligible(const Lattice &L) { return pipe_kernel_runs(L); }
+
+// Dynamic shared memory above 48 KB is opted into once per device.
+template <class S, class R, bool ODD, bool DIAG>
+static cudaError_t pipe_attrs() {
+  static unsigned long long done = 0;  // bit d: set on device d
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+  if (bit && (done & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(k_pipe<S, R, ODD, DIAG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(PipeSmem<S, R>));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_pipe<S, R, ODD, DIAG>,
+                           cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e != cudaSuccess) return e;
+  done |= bit;
+  return cudaSuccess;
+}
+
+template <class S, class R, bool ODD, bool DIAG>
+static cudaError_t launch_pipe_t(Lattice &L, Args<S, R> &a) {
+  cudaError_t e = pipe_attrs<S, R, ODD, DIAG>();
+  if (e != cudaSuccess) return e;
+  const dim3 grid((L.nx + PP_BX - 1) / PP_BX, (L.ny + PP_BY - 1) / PP_BY,
+                  (L.nz + L.lz - 1) / L.lz);
+  k_pipe<S, R, ODD, DIAG><<<grid, PP_NT, sizeof(PipeSmem<S, R>), L.stream>>>(a);
+  return cudaGetLastError();
+}
+
 template <class S, class R, bool ODD, bool DIAG>
 static cudaError_t launch_fused_t(Lattice &L, Args<S, R> &a) {
+  if constexpr (pipe_storage<S>()) {
+    if (pipe_eligible(L)) return launch_pipe_t<S, R, ODD, DIAG>(L, a);
+  }
   if constexpr (std::is_same<S, float>::value && std::is_same<R, float>::value) {
     if (async_eligible(L)) return launch_async_t<ODD, DIAG>(L, a);
   }
@@ -181,14 +221,22 @@ static cudaError_t launch_cell_t(Lattice &L, Args<S, R> &a) {
 template <class S, class R>
 int auto_lz(const Lattice &L) {
   int dev = 0, nsm = 0, per = 0;
-  bool tma = false;
+  bool tma = false, pipe = false;
   if constexpr (std::is_same<S, float>::value && std::is_same<R, float>::value)
     tma = async_eligible(L);
-  const int bx = tma ? AB_X : L.bx, by = tma ? AB_Y : L.by;
+  if constexpr (pipe_storage<S>()) pipe = pipe_eligible(L);
+  const int bx = pipe ? PP_BX : (tma ? AB_X : L.bx), by = pipe ? PP_BY : (tma ? AB_Y : L.by);
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) {
-    if (tma) {
+    if (pipe) {
+      if constexpr (pipe_storage<S>()) {
+        e = pipe_attrs<S, R, false, true>();
+        if (e == cudaSuccess)
+          e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pipe<S, R, false, true>, PP_NT,
+                                                            sizeof(PipeSmem<S, R>));
+      }
+    } else if (tma) {
       if constexpr (std::is_same<S, float>::value && std::is_same<R, float>::value) {
         e = async_attrs<false, true>();
         if (e == cudaSuccess)
@@ -231,7 +279,7 @@ cudaError_t launch_step(Lattice &L, bool diag) {
     a.diag = L.diag + 32 * (L.ndiag & 1);
     a.diag_zero = L.diag + 32 * ((L.ndiag + 1) & 1);
   }
-  if (L.kernel == PFLB_KERNEL_FUSED || L.kernel == PFLB_KERNEL_FUSED_TMA) {
+  if (L.kernel != PFLB_KERNEL_TWOPASS) {  // fused, its TMA-staged and pipelined forms
     if (odd) e = diag ? launch_fused_t<S, R, true, true>(L, a) : launch_fused_t<S, R, true, false>(L, a);
     else e = diag ? launch_fused_t<S, R, false, true>(L, a) : launch_fused_t<S, R, false, false>(L, a);
   } else {

@@ -73,9 +73,12 @@ __host__ __device__ constexpr EdgeInfo edge_info(int i) {
 }
 
 // Diagnostic accumulator slots (double, device).
+// Slots before D_UMAX are sums; D_UMAX, D_FRONT and D_REAR are maxima of
+// non-negative values (the interface crossings are stored shifted so that
+// 0 means "none": x + 1 for the front, nx - x for the rear).
 enum {
   D_MASS = 0, D_NHEAVY, D_PH, D_NPH, D_PL, D_NPL, D_REGION, D_CLN, D_CLX, D_CLY, D_CLZ,
-  D_CLXX, D_CLYY, D_CLZZ, D_KIN, D_NONFINITE, D_UMAX, D_COUNT
+  D_CLXX, D_CLYY, D_CLZZ, D_KIN, D_NONFINITE, D_UMAX, D_FRONT, D_REAR, D_COUNT
 };
 
 // Cell flags.
@@ -394,6 +397,104 @@ __device__ __forceinline__ void collide(const Model<R> &m, R h[Q], R g[Q], const
     if (c0 * c2) cc += R(2 * c0 * c2) * pxz;
     if (c1 * c2) cc += R(2 * c1 * c2) * pyz;
     g[i] = g[i] + (f * R(w_of(i))) * cc;
+  }
+}
+
+// collide() in pair form (same results up to rounding).  Directions i and
+// opp(i) have c_opp = -c_i and equal weights, so with a = c_i . u and
+// s = 1 + m, m = 9a^2/2 - 3u^2/2 (Gamma_i = w_i (s + 3a), Gamma_opp =
+// w_i (s - 3a)) every per-direction term of Eqs. 2, 5 and 6 splits into a
+// part even in c_i and a part odd in c_i, each evaluated once per pair:
+//   h_eq   = w_i phi s               +- w_i (3 phi a + theta n . c_i)
+//   K_i    = w_i (C c.grad - B u.grad - 3 s u.F + 9 a c.F)
+//         +- w_i (B c.grad - C u.grad + 3 s c.F - 9 a u.F)
+//            with B = m (rho_dif + mu/T) + mu/T, C = 3 a (rho_dif + mu/T)
+//   E_i    = w_i (P/T + rho m)        +- 3 w_i rho a
+// and the pair's non-equilibrium sum (g_i - g_eq,i) + (g_opp - g_eq,opp)
+// feeds Pi with the pair's common c_i c_i.  The filtered correction of
+// Eqs. 9-11 is even.  m is carried instead of s so that, as in collide(),
+// the heavy phase (rho = 1) does not cancel the pressure part of E_i.
+// About two thirds of collide()'s arithmetic.
+template <class R>
+__device__ __forceinline__ void collide_pairs(const Model<R> &m, R h[Q], R g[Q],
+                                              const Macro<R> &mc, R phi, R gx, R gy, R gz,
+                                              R lap) {
+  const R ux = mc.ux, uy = mc.uy, uz = mc.uz;
+  const R gn2 = gx * gx + gy * gy + gz * gz;
+  const R gnorm = sqrt_(gn2);
+  const R inv = div_(R(1), gnorm + m.eps);
+  R th = m.theta_coef * (R(1) - R(4) * (phi - R(0.5)) * (phi - R(0.5)));
+  if (m.mobility_corr) th += delta_theta(m, phi, gnorm, lap);
+  const R thn = th * inv;  // theta n = thn grad phi
+  const R om = m.inv_tau_phi;
+  const R m0 = R(-1.5) * (ux * ux + uy * uy + uz * uz);  // s - 1 of the rest direction
+  const R ug = ux * gx + uy * gy + uz * gz;
+  const R uF = ux * m.Fx + uy * m.Fy + uz * m.Fz;
+  const R rho = mc.rho;
+  const R muT = R(3) * mc.mu;             // mu / T
+  const R al = m.rho_dif + muT;           // rho_dif + mu / T
+  const R P3 = R(3) * mc.P;               // P / T
+  const R phi3 = R(3) * phi, rho3 = R(3) * rho, uF3 = R(3) * uF;
+  R pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
+  R rest = phi;
+#pragma unroll
+  for (int i = 1; i < Q; i += 2) {
+    const int j = i + 1;  // opp(i)
+    const int c0 = cx_of(i), c1 = cy_of(i), c2 = cz_of(i);
+    const R wi = R(w_of(i));
+    const R a = R(c0) * ux + R(c1) * uy + R(c2) * uz;
+    const R cgr = R(c0) * gx + R(c1) * gy + R(c2) * gz;
+    const R cF = R(c0) * m.Fx + R(c1) * m.Fy + R(c2) * m.Fz;
+    const R mm = m0 + R(4.5) * a * a;  // s - 1
+    const R s = R(1) + mm;
+    // h (Eqs. 1-2)
+    const R HS = wi * (phi + phi * mm), HA = wi * (phi3 * a + thn * cgr);
+    h[i] = h[i] + om * ((HS + HA) - h[i]);
+    h[j] = h[j] + om * ((HS - HA) - h[j]);
+    rest -= h[i] + h[j];
+    // g (Eqs. 5-6 and reading R2 of Eqs. 9-11)
+    const R B = mm * al + muT, C = R(3) * a * al;
+    const R KS = wi * (C * cgr - B * ug - s * uF3 + R(9) * a * cF);
+    const R KA = wi * (B * cgr - C * ug + R(3) * s * cF - R(9) * a * uF);
+    const R ES = wi * (P3 + rho * mm), EA = wi * rho3 * a;
+    const R BS = ES + R(0.5) * KS, BA = EA + R(0.5) * KA;
+    const R nsum = (g[i] + g[j]) - (R(2) * ES - KS);
+    g[i] = BS + BA;
+    g[j] = BS - BA;
+    if (c0) pxx += nsum;
+    if (c1) pyy += nsum;
+    if (c2) pzz += nsum;
+    if (c0 * c1 > 0) pxy += nsum;
+    if (c0 * c1 < 0) pxy -= nsum;
+    if (c0 * c2 > 0) pxz += nsum;
+    if (c0 * c2 < 0) pxz -= nsum;
+    if (c1 * c2 > 0) pyz += nsum;
+    if (c1 * c2 < 0) pyz -= nsum;
+  }
+  h[0] = rest;
+  {  // rest direction: a = c . grad = c . F = 0
+    const R w0 = R(w_of(0));
+    const R B = m0 * al + muT;
+    const R K0 = w0 * (-B * ug - (R(1) + m0) * uF3);
+    g[0] = w0 * (P3 + rho * m0) + R(0.5) * K0;
+  }
+  const R tau = tau_mix(m, phi);
+  const R f = (R(1) - div_(R(1), tau)) * R(4.5);
+  const R tr3 = (pxx + pyy + pzz) * R(1.0 / 3.0);
+  g[0] = g[0] - (f * R(w_of(0))) * tr3;
+#pragma unroll
+  for (int i = 1; i < Q; i += 2) {
+    const int c0 = cx_of(i), c1 = cy_of(i), c2 = cz_of(i);
+    R cc = -tr3;
+    if (c0) cc += pxx;
+    if (c1) cc += pyy;
+    if (c2) cc += pzz;
+    if (c0 * c1) cc += R(2 * c0 * c1) * pxy;
+    if (c0 * c2) cc += R(2 * c0 * c2) * pxz;
+    if (c1 * c2) cc += R(2 * c1 * c2) * pyz;
+    const R d = (f * R(w_of(i))) * cc;
+    g[i] += d;
+    g[i + 1] += d;
   }
 }
 

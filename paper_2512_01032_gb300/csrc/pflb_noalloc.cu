@@ -152,11 +152,25 @@ extern "C" pflb_status pflb_fields_noalloc(int nx, int ny, int nz, const float *
   if (!fields_dev && !diag_out) return na_fail(PFLB_ERR_ARG, "nothing to compute: no output");
   if (!(params->W > 0) || !(params->rho_L > 0) || !(params->rho_H > 0))
     return na_fail(PFLB_ERR_ARG, "need W, rho_L, rho_H > 0");
+  if (params->storage != PFLB_STORAGE_FP32)
+    return na_fail(PFLB_ERR_ARG, "pflb_fields_noalloc reads FP32 populations only "
+                                 "(params->storage must be PFLB_STORAGE_FP32)");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (diag_out) {
+    // The diagnostic form copies to pageable host memory and waits for the
+    // stream; on a stream under capture that would invalidate the capture,
+    // so it is refused before anything is enqueued.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t ce = cudaStreamIsCapturing(st, &cs);
+    if (ce != cudaSuccess)
+      return na_fail(PFLB_ERR_CUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(ce));
+    if (cs != cudaStreamCaptureStatusNone)
+      return na_fail(PFLB_ERR_ARG, "diag_out needs a stream that is not being captured");
+  }
   DevScratch *sc = nullptr;
   std::string err;
   pflb_status s = scratch_for_current_device(sc, err);
   if (s != PFLB_OK) return na_fail(s, err);
-  cudaStream_t st = (cudaStream_t)cuda_stream;
   // The accumulators keep the previous call's contents: clear them.
   cudaError_t e = cudaMemsetAsync(sc->diag, 0, 32 * sizeof(double), st);
   const pflb::Model<float> m = pflb::make_model<float>(*params);
@@ -190,6 +204,8 @@ extern "C" pflb_status pflb_fields_noalloc(int nx, int ny, int nz, const float *
   diag_out->region_mass = d[D_REGION];
   diag_out->kinetic = d[D_KIN];
   diag_out->nonfinite = d[D_NONFINITE];
+  diag_out->front_x = -1.0;  // not computed by this pass
+  diag_out->rear_x = -1.0;
   if (diag_out->nonfinite > 0 || !std::isfinite(diag_out->mass))
     return na_fail(PFLB_ERR_NAN, "non-finite values in the fields");
   return PFLB_OK;

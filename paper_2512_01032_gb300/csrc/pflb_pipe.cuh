@@ -1,0 +1,353 @@
+// pflb_pipe.cuh -- fused step kernel with asynchronous staging of the next
+// planes' populations in 16-byte chunks (any storage type, periodic x, nx a
+// multiple of 4, of 8 at 16-bit storage).
+//
+// The step is k_fused's (arXiv 2512.01032, Sec. II and Sec. III A): one
+// thread per (x, y) column of a 32 x 4 tile marching a chunk of z planes,
+// phi recomputed from h for the tile plus a one-cell ring, so no phi field
+// goes to HBM.  What differs is how the populations reach the threads.
+// k_fused loads each value when it needs it and waits for DRAM on every
+// plane.  Here the block copies whole rows into shared memory with
+// cp.async.cg (16 bytes per copy, through L2 only) one iteration before they
+// are used:
+//
+//   iteration z:  wait for the copies issued in iteration z - 1; barrier;
+//                 phi of plane z + 1 from its staged h into the phi ring;
+//                 each thread takes its cell's h and g of plane z from
+//                 shared memory into registers; barrier;
+//                 issue the copies of h of plane z + 2, g of plane z + 1 and
+//                 the flags of plane z + 3 into the buffers just read;
+//                 update of plane z (collision, streaming stores).
+//
+// Staged rows span x0 - V .. x0 + 32 + V (V values per 16-byte chunk), so
+// the ring cells' h and the A-A gather sources of odd steps (shifted by one
+// cell in x) come from the same aligned chunks; because chunks are aligned
+// and nx is a multiple of V, a chunk never straddles the periodic seam and
+// wraps as a whole.  Rows and planes wrap individually.  Chunks whose cells
+// are all solid are not copied, using flag words staged one iteration
+// earlier still.  Wall cells read their wall records and wall populations
+// with ordinary loads; they are few.  16-bit storage stages the stored
+// (weight-scaled) values and decodes them when they are read.
+//
+// Shared memory per block (FP32): h 2 planes x 19 x 6 rows x 40, g 19 x 4
+// rows x 40, flags 4 planes x 6 x 10 words, phi 4 planes x 34 x 6: 54 KB,
+// four blocks per SM.
+//
+// The collision is collide_pairs (the even/odd split of each opposite
+// pair); the per-cell arithmetic is otherwise finish_cell's.
+#pragma once
+#include "pflb_async.cuh"
+#include "pflb_kernels.cuh"
+
+namespace pflb {
+
+constexpr int PP_BX = 32, PP_BY = 4, PP_NT = PP_BX * PP_BY;
+constexpr int PP_PW = PP_BX + 2, PP_PS = (PP_BX + 2) * (PP_BY + 2);
+constexpr int PP_NR = 2 * PP_PW + 2 * PP_BY;  // ring cells around the tile
+constexpr int PP_ROWS = PP_BY + 2;            // staged h rows: y0 - 1 .. y0 + BY
+constexpr int PP_FW = (PP_BX + 8) / 4;        // flag words per staged row (x0 - 4 .. x0 + 36)
+#ifndef PFLB_PIPE_MIN_BLOCKS
+#define PFLB_PIPE_MIN_BLOCKS 4
+#endif
+
+template <class S, class R>
+struct PipeSmem {
+  static constexpr int V = 16 / (int)sizeof(S);  // values per 16-byte chunk
+  static constexpr int W = PP_BX + 2 * V;        // staged row: x0 - V .. x0 + 32 + V
+  static constexpr int NCH = W / V;              // chunks per staged row
+  static constexpr int HS = h_slots<S>();        // 19, or 20 with the rest remainder
+  S h[2][HS][PP_ROWS][W];   // h of planes z + 1 (phi) and z + 2 (in flight), slot = plane & 1
+  S g[Q][PP_BY][W];         // g arriving at the cells of the next plane to update
+  R phi[4][PP_PS];          // phi ring, slot = unwrapped plane & 3
+  uint32_t fl[4][PP_ROWS][PP_FW];  // flag words, x0 - 4 .. x0 + 36, slot = plane & 3
+};
+
+__device__ __forceinline__ void cp_async_16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+__device__ __forceinline__ uint8_t flag_byte(const uint32_t (*fl)[PP_FW], int row, int dx) {
+  // dx: x offset from x0, in [-4, 36)
+  return (uint8_t)(fl[row][(dx + 4) >> 2] >> (8 * ((dx + 4) & 3)));
+}
+__device__ __forceinline__ bool all_solid(uint32_t w) {
+  return (w & 0x01010101u) == 0x01010101u;  // bit 0 (F_SOLID) of all four cells
+}
+// True if the flag words overlapping chunk ch of a staged row (x offsets
+// ch V - V .. ch V - 1 from x0) say all their cells are solid; cells of the
+// chunk outside x0 - 4 .. x0 + 36 are never read.
+template <int V>
+__device__ __forceinline__ bool chunk_solid(const uint32_t *flrow, int ch) {
+  const int dx0 = ch * V - V, dx1 = dx0 + V;
+  const int w0 = ((dx0 > -4 ? dx0 : -4) + 4) >> 2;
+  const int w1 = ((dx1 < 36 ? dx1 : 36) + 7) >> 2;
+  bool solid = true;
+#pragma unroll
+  for (int k = 0; k < (V + 7) / 4; ++k)
+    if (w0 + k < w1) solid = solid && all_solid(flrow[w0 + k]);
+  return solid;
+}
+
+template <class S, class R, bool ODD, bool DIAG>
+__global__ void __launch_bounds__(PP_NT, PFLB_PIPE_MIN_BLOCKS)
+    k_pipe(const __grid_constant__ Args<S, R> a) {
+  using SM = PipeSmem<S, R>;
+  constexpr int V = SM::V, NCH = SM::NCH, HS = SM::HS;
+  static_assert(F_SOLID == 1, "all_solid tests bit 0");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SM &sm = *reinterpret_cast<SM *>(smem_raw);
+  __shared__ R wacc[DIAG_MAX_WARPS][32];
+  zero_next_diag(a);
+  const int tid = threadIdx.x, tx = tid % PP_BX, ty = tid / PP_BX;
+  const int nx = a.nx, ny = a.ny, nz = a.nz, sz = nx * ny;
+  const int x0 = blockIdx.x * PP_BX, y0 = blockIdx.y * PP_BY;
+  const int zb = blockIdx.z * a.lz, ze = min(zb + a.lz, nz);
+  // A column beyond a ragged lattice edge still sums the cell it wraps to:
+  // that is the periodic neighbour the last valid column needs.
+  const bool valid = (x0 + tx) < nx && (y0 + ty) < ny;
+  const int cx0 = (x0 + tx) % nx, cy0 = (y0 + ty) % ny;
+  const int col = cx0 + nx * cy0;
+  const bool ring = tid < PP_NR;
+  int rx = 0, ry = 0;
+  if (ring) {
+    if (tid < PP_PW) {
+      rx = tid;
+      ry = 0;
+    } else if (tid < 2 * PP_PW) {
+      rx = tid - PP_PW;
+      ry = PP_BY + 1;
+    } else {
+      const int k = tid - 2 * PP_PW;
+      rx = (k & 1) ? PP_BX + 1 : 0;
+      ry = 1 + (k >> 1);
+    }
+  }
+  // Plane wrap by additions: the planes touched lie within a few of [0, nz).
+  auto wrapz = [nz](int zu) {
+    while (zu < 0) zu += nz;
+    while (zu >= nz) zu -= nz;
+    return zu;
+  };
+  auto wrap = [](int v, int n) { return ((v % n) + n) % n; };
+
+  // Staging units, fixed for the whole march, so their periodic x and y
+  // wraps (integer divisions) are computed once: a unit is one staged row
+  // chunk (row r, chunk ch) and one half of the population slots.
+  constexpr int HU = 2 * PP_ROWS * NCH, GU = 2 * PP_BY * NCH;
+  constexpr int HPT = (HU + PP_NT - 1) / PP_NT, GPT = (GU + PP_NT - 1) / PP_NT;
+  int h_rc[HPT], h_off[HPT];     // (half << 16 | r << 8 | ch), in-plane offset; -1: none
+  int g_rc[GPT], g_off[GPT][3];  // offsets of the chunk in rows y0 + r - 1, y0 + r, y0 + r + 1
+#pragma unroll
+  for (int k = 0; k < HPT; ++k) {
+    const int u = tid + k * PP_NT;
+    h_rc[k] = -1;
+    h_off[k] = 0;
+    if (u < HU) {
+      const int half = u >= HU / 2, v = u - half * (HU / 2);
+      const int r = v / NCH, ch = v - r * NCH;
+      h_rc[k] = half << 16 | r << 8 | ch;
+      h_off[k] = wrap(x0 - V + ch * V, nx) + nx * wrap(y0 - 1 + r, ny);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < GPT; ++k) {
+    const int u = tid + k * PP_NT;
+    g_rc[k] = -1;
+    g_off[k][0] = g_off[k][1] = g_off[k][2] = 0;
+    if (u < GU) {
+      const int half = u >= GU / 2, v = u - half * (GU / 2);
+      const int r = v / NCH, ch = v - r * NCH;
+      g_rc[k] = half << 16 | r << 8 | ch;
+      const int xs = wrap(x0 - V + ch * V, nx);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) g_off[k][d] = xs + nx * wrap(y0 + r - 1 + d, ny);
+    }
+  }
+  int fl_off = -1;  // flag word of row tid / 10, word tid % 10
+  if (tid < PP_ROWS * PP_FW) {
+    const int r = tid / PP_FW, w = tid - r * PP_FW;
+    fl_off = wrap(x0 - 4 + 4 * w, nx) + nx * wrap(y0 - 1 + r, ny);
+  }
+
+  // Flag words of plane zu: 6 rows x 10 words, one copy per thread.
+  auto stage_flags = [&](int zu) {
+    if (fl_off >= 0) {
+      const int r = tid / PP_FW, w = tid - r * PP_FW;
+      cp_async_4(&sm.fl[zu & 3][r][w], a.flags + (fl_off + sz * wrapz(zu)));
+    }
+  };
+  // h of plane zu into slot zu & 1: 6 rows x NCH chunks x HS slots, the
+  // slots split into two halves over the block's two thread halves.
+  auto stage_h = [&](int zu, bool skip_solid) {
+    const int zoff = sz * wrapz(zu);
+    const uint32_t (*fl)[PP_FW] = sm.fl[zu & 3];
+    S(*dst)[PP_ROWS][SM::W] = sm.h[zu & 1];
+#pragma unroll
+    for (int k = 0; k < HPT; ++k) {
+      if (h_rc[k] < 0) continue;
+      const int half = h_rc[k] >> 16, r = (h_rc[k] >> 8) & 0xff, ch = h_rc[k] & 0xff;
+      if (skip_solid && chunk_solid<V>(fl[r], ch)) continue;
+      const int cell = h_off[k] + zoff;
+      if (!half) {
+#pragma unroll
+        for (int i = 0; i < 10; ++i) cp_async_16(&dst[i][r][ch * V], a.hin[i] + cell);
+      } else {
+#pragma unroll
+        for (int i = 10; i < HS; ++i) cp_async_16(&dst[i][r][ch * V], a.hin[i] + cell);
+      }
+    }
+  };
+  // g arriving at the cells of plane zu: for direction k, row r holds the
+  // source row of tile row r (A-A: slot k of the own cells on even steps,
+  // slot opp(k) of x - c_k on odd steps), in the chunks that hold the
+  // tile's sources.  Sources across a solid link are replaced from the wall
+  // populations at the update.
+  auto stage_g = [&](int zu) {
+    const int z = wrapz(zu);
+    const uint32_t (*fl)[PP_FW] = sm.fl[zu & 3];
+#pragma unroll
+    for (int u = 0; u < GPT; ++u) {
+      if (g_rc[u] < 0) continue;
+      const int half = g_rc[u] >> 16, r = (g_rc[u] >> 8) & 0xff, ch = g_rc[u] & 0xff;
+      const int k0 = half ? 10 : 0, k1 = half ? Q : 10;
+      if constexpr (!ODD) {
+        if (ch == 0 || ch == NCH - 1) continue;  // own cells only
+        if (chunk_solid<V>(fl[r + 1], ch)) continue;
+        const int cell = g_off[u][1] + sz * z;
+#pragma unroll
+        for (int k = 0; k < Q; ++k)
+          if (k >= k0 && k < k1) cp_async_16(&sm.g[k][r][ch * V], a.g[k] + cell);
+      } else {
+        const int zo[3] = {sz * wrapz(zu - 1), sz * z, sz * wrapz(zu + 1)};
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+          if (k < k0 || k >= k1) continue;
+          const int cxk = cx_of(k), cyk = cy_of(k), czk = cz_of(k);
+          const int lo = (V - (cxk > 0 ? cxk : 0)) / V;
+          const int hi = (V + PP_BX - 1 - (cxk < 0 ? cxk : 0)) / V;
+          if (ch < lo || ch > hi) continue;
+          // source row y - c_k and plane z - c_k
+          cp_async_16(&sm.g[k][r][ch * V], a.g[opp_of(k)] + (g_off[u][1 - cyk] + zo[1 - czk]));
+        }
+      }
+    }
+  };
+  // phi of plane zu (own column and ring cell) into ring slot zu & 3; a
+  // solid cell's phi is 0
+  // staged h of one cell, decoded (the 16-bit rest population is high part
+  // plus remainder), and its sum in the order cell_phi uses
+  auto cell_h = [&](const S (*st)[PP_ROWS][SM::W], int row, int idx, R h[Q]) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) h[i] = dec_pop<S, R>(st[i][row][idx], i);
+    if constexpr (HS > Q) h[0] += dec_pop<S, R>(st[Q][row][idx], 0);
+  };
+  auto staged_phi = [&](const S (*st)[PP_ROWS][SM::W], int row, int idx) {
+    R h[Q];
+    cell_h(st, row, idx, h);
+    R v = R(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) v += h[i];
+    return v;
+  };
+  auto phi_plane = [&](int zu) {
+    const S(*st)[PP_ROWS][SM::W] = sm.h[zu & 1];
+    const uint32_t (*fl)[PP_FW] = sm.fl[zu & 3];
+    R *dst = sm.phi[zu & 3];
+    dst[(ty + 1) * PP_PW + tx + 1] =
+        (flag_byte(fl, ty + 1, tx) & F_SOLID) ? R(0) : staged_phi(st, ty + 1, V + tx);
+    if (ring)
+      dst[ry * PP_PW + rx] = (flag_byte(fl, ry, rx - 1) & F_SOLID) ? R(0)
+                                                                   : staged_phi(st, ry, V - 1 + rx);
+  };
+
+  DiagAcc<R> tot;
+  tot.zero();
+  if (DIAG) diag_block_zero(wacc);  // first use follows the loop's barriers
+
+  // Prologue: flags of planes zb - 1 .. zb + 2 and h of zb - 1, zb (all
+  // chunks), then phi of zb - 1 and zb; then h of zb + 1 (into the slot of
+  // zb - 1) and g of zb.
+  for (int zu = zb - 1; zu <= zb + 2; ++zu) stage_flags(zu);
+  stage_h(zb - 1, false);
+  stage_h(zb, false);
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncthreads();
+  phi_plane(zb - 1);
+  phi_plane(zb);
+  __syncthreads();  // slot of zb - 1 read before it is refilled
+  stage_h(zb + 1, true);
+  stage_g(zb);
+  cp_async_commit();
+
+  const int o = (ty + 1) * PP_PW + tx + 1;
+  for (int z = zb; z < ze; ++z) {
+    cp_async_wait_all();
+    __syncthreads();  // staged h(z + 1), g(z), flags(z + 2) visible to all
+    phi_plane(z + 1);
+    const int c = col + sz * z;
+    const uint8_t f = flag_byte(sm.fl[z & 3], ty + 1, tx);
+    const bool fluid = valid && !(f & F_SOLID);
+    R h[Q], g[Q];
+    if (fluid) {
+      cell_h(sm.h[z & 1], ty + 1, V + tx, h);
+#pragma unroll
+      for (int k = 0; k < Q; ++k)
+        g[k] = dec_pop<S, R>(sm.g[k][ty][V + tx - (ODD ? cx_of(k) : 0)], k);
+    }
+    __syncthreads();  // phi ring complete; h slot z & 1 and the g buffer are free
+    if (z + 2 <= ze) stage_h(z + 2, true);
+    if (z + 1 < ze) stage_g(z + 1);
+    if (z + 3 <= ze) stage_flags(z + 3);
+    cp_async_commit();
+    if (fluid) {
+      Nbr nb;
+      nb.init(cx0, cy0, z, nx, ny, nz);
+      uint32_t lm = 0;
+      int rec = 0;
+      if (f & F_WALL) {
+        rec = a.widx[c];
+        lm = a.wmask[rec];
+#pragma unroll
+        for (int k = 1; k < Q; ++k)
+          if ((lm >> opp_of(k)) & 1u) g[k] = ld_g<S, R>(a.wp_rd + ((k - 1) * a.nw + rec), k);
+      }
+      const R *p0 = sm.phi[z & 3], *pm = sm.phi[(z - 1) & 3], *pp = sm.phi[(z + 1) & 3];
+      R val[Q];
+      const R phi = p0[o];
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        const R *pl = cz_of(i) == 0 ? p0 : (cz_of(i) > 0 ? pp : pm);
+        val[i] = pl[o + cy_of(i) * PP_PW + cx_of(i)];
+      }
+      DiagAcc<R> acc;
+      acc.zero();
+      finish_cell<S, R, ODD, MODE_STEP, DIAG, false, true>(a, cx0, cy0, z, c, f, lm, rec, nb, h,
+                                                           g, phi, val, acc);
+      if (DIAG) {
+#pragma unroll
+        for (int k = 0; k < D_UMAX; ++k) tot.v[k] += acc.v[k];
+        tot.umax = tot.umax > acc.umax ? tot.umax : acc.umax;
+        tot.front = tot.front > acc.front ? tot.front : acc.front;
+        tot.rear = tot.rear > acc.rear ? tot.rear : acc.rear;
+      }
+    }
+  }
+  cp_async_wait_all();  // nothing is in flight at exit
+  if (DIAG) {
+    diag_warp_add(wacc[tid >> 5], tot);
+    diag_block_flush(a.diag, wacc);
+  }
+}
+
+}  // namespace pflb

@@ -21,7 +21,7 @@ OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NAN, ERR_TIMEOUT, ERR_BUDGET, ERR_STATE = ra
 STORAGE_FP64, STORAGE_FP32, STORAGE_FP16, STORAGE_BF16 = 0, 1, 2, 3
 FIELD_PHI, FIELD_RHO, FIELD_P, FIELD_UX, FIELD_UY, FIELD_UZ = range(6)
 FIELDS = {"phi": 0, "rho": 1, "P": 2, "ux": 3, "uy": 4, "uz": 5}
-KERNEL_FUSED, KERNEL_TWOPASS, KERNEL_FUSED_TMA = 0, 1, 2
+KERNEL_FUSED, KERNEL_TWOPASS, KERNEL_FUSED_TMA, KERNEL_PIPE = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NAN",
                 5: "ERR_TIMEOUT", 6: "ERR_BUDGET", 7: "ERR_STATE"}
@@ -120,6 +120,7 @@ class Diag(C.Structure):
         ("n_p_light", C.c_double), ("dp", C.c_double), ("u_max", C.c_double),
         ("region_mass", C.c_double), ("cl_count", C.c_double), ("cl_mean", C.c_double * 3),
         ("cl_m2", C.c_double * 3), ("kinetic", C.c_double), ("nonfinite", C.c_double),
+        ("front_x", C.c_double), ("rear_x", C.c_double),
     ]
 
     def as_dict(self):

@@ -35,3 +35,39 @@ def test_bounded_wait_timeout_is_reported_and_contained():
     assert C.diag()["mass"] > 0
     with pytest.raises(pflb.PflbError):
         C.selftest_wait_timeout(0)
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32", "bf16"])
+@pytest.mark.parametrize("kernel", [0, 3])
+def test_non_finite_state_is_reported_as_err_nan(storage, kernel):
+    """A non-finite value injected on the host (one NaN cell in the initial
+    phi field given to pflb_init_phi, which does not screen its input) is
+    counted by the next diagnostic step and reported as PFLB_ERR_NAN by
+    pflb_last_diag and pflb_diag, with the diagnostics filled in.  Nothing
+    faults: it is a state error, not a CUDA error, so the lattice is not
+    poisoned, and initialising it again gives a clean run."""
+    import oracle as O
+    from paper_2512_01032_gb300 import pflb
+    g, p, init = CS.droplet_case(16, 4.0)
+    L = pflb.Lattice(g.nx, g.ny, g.nz, storage=storage, **p)
+    L.set_kernel(kernel)
+    phi = O.tanh_phi(0, (g.nx, g.ny, g.nz), init["center"], init["R"], p["W"])
+    phi[7 + g.nx * (8 + g.ny * 6)] = np.nan
+    L.init_phi(phi)
+    L.set_diag_every(1)
+    L.step(2)
+    with pytest.raises(pflb.PflbError) as ei:
+        L.last_diag()
+    assert ei.value.status == pflb.ERR_NAN
+    d = L.last_diag(allow_nan=True)
+    assert d["step"] == 1 and d["nonfinite"] >= 1
+    with pytest.raises(pflb.PflbError) as ei:
+        L.diag()
+    assert ei.value.status == pflb.ERR_NAN
+    assert L.diag(allow_nan=True)["nonfinite"] >= 1
+    # not poisoned: a fresh state steps cleanly
+    L.init_tanh(0, init["center"], init["R"])
+    L.step(3)
+    d = L.last_diag()
+    assert d["nonfinite"] == 0 and d["mass"] > 0
+    assert np.isfinite(L.read("phi")).all()

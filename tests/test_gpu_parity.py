@@ -35,7 +35,7 @@ def _compare(G, Orc, steps_list, storage, p_scale, label=""):
 
 
 @pytest.mark.parametrize("storage", ["fp64", "fp32"])
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 3])
 def test_static_droplet_400_steps(storage, kernel):
     """Periodic 32^3 droplet (R=8, W=4, ratio 1000, sigma=0.01, tau=0.8,
     M=0.02): phi, P, u after 0, 1, 2, 7 and 400 steps."""
@@ -45,7 +45,7 @@ def test_static_droplet_400_steps(storage, kernel):
 
 
 @pytest.mark.parametrize("storage", ["fp64", "fp32"])
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 3])
 def test_sessile_sphere_walls_wetting_free_slip(storage, kernel):
     """Droplet on a voxelised sphere between two planes (32^3 scaling of the
     128^3 workload), theta=60, optimised model: tanh F, free-slip band,
@@ -57,7 +57,8 @@ def test_sessile_sphere_walls_wetting_free_slip(storage, kernel):
 
 @pytest.mark.parametrize("storage", ["fp64", "fp32"])
 @pytest.mark.parametrize("F_mode", [0, 1])
-def test_slit_with_force_and_viscosity_ratio(storage, F_mode):
+@pytest.mark.parametrize("kernel", [0, 3])
+def test_slit_with_force_and_viscosity_ratio(storage, F_mode, kernel):
     """Capillary slit (scaled): walls with theta=45 only in the channel,
     viscosity ratio 50, a small body force, free-slip band and blend.
 
@@ -73,7 +74,7 @@ def test_slit_with_force_and_viscosity_ratio(storage, F_mode):
     p = dict(p, F_mode=F_mode)
     if storage == "fp32":
         p["free_slip"] = 0
-    G, Orc = CS.make_pair(g, p, init, storage=storage)
+    G, Orc = CS.make_pair(g, p, init, storage=storage, kernel=kernel)
     tol = TOL[storage]
     t = 0
     for s in ((3, 60) if storage == "fp64" else (3, 20)):
@@ -112,8 +113,10 @@ def test_ragged_and_tiny_lattices(dims):
     init = dict(shape=0, center=(nx / 2.0 + 0.37, ny / 2.0 - 0.21, nz / 2.0 + 0.13),
                 R=max(1.5, min(dims) / 3.0))
     for storage in ("fp64", "fp32"):
-        G, Orc = CS.make_pair(g, p, init, storage=storage, kernel=0)
-        _compare(G, Orc, [1, 9], storage, 2 * p["sigma"] / init["R"], f"ragged{dims}")
+        for kernel in (0, 3):
+            G, Orc = CS.make_pair(g, p, init, storage=storage, kernel=kernel)
+            _compare(G, Orc, [1, 9], storage, 2 * p["sigma"] / init["R"],
+                     f"ragged{dims} kernel {kernel}")
 
 
 def test_zero_steps_and_a_lattice_without_fluid():
@@ -155,6 +158,7 @@ def test_tile_shapes_bitwise_identical(tile):
     from paper_2512_01032_gb300 import pflb
     ref = pflb.Lattice(g.nx, g.ny, g.nz, solid=g.solid, wall_normal=g.normals(),
                        theta_cells=g.theta(), storage="fp32", **p)
+    ref.set_kernel(pflb.KERNEL_FUSED)
     ref.init_tanh(0, init["center"], init["R"])
     ref.step(11)
     L = pflb.Lattice(g.nx, g.ny, g.nz, solid=g.solid, wall_normal=g.normals(),
@@ -178,7 +182,7 @@ def test_sessile_sphere_64_parity_fp32():
     """The curved-wall workload at 64^3 (all lengths halved), FP32 storage,
     the bench launch configuration, 100 steps."""
     g, p, init = CS.sessile_case(64, 90.0)
-    G, Orc = CS.make_pair(g, p, init, storage="fp32", kernel=0)
+    G, Orc = CS.make_pair(g, p, init, storage="fp32", kernel=3)
     _compare(G, Orc, [100], "fp32", 2 * p["sigma"] / init["R"], "sessile64")
 
 
@@ -187,7 +191,7 @@ def test_full_size_128_first_steps_fp32():
     """Full 128^3 curved-wall workload in the bench launch configuration:
     every cell against the oracle after 2 steps."""
     g, p, init = CS.sessile_case(128, 30.0)
-    G, Orc = CS.make_pair(g, p, init, storage="fp32", kernel=0)
+    G, Orc = CS.make_pair(g, p, init, storage="fp32", kernel=3)
     _compare(G, Orc, [2], "fp32", 2 * p["sigma"] / init["R"], "sessile128")
 
 
@@ -238,7 +242,7 @@ def test_staged_kernel_matches_plain_bitwise(dims):
 
 
 @pytest.mark.parametrize("storage", ["fp64", "fp32"])
-@pytest.mark.parametrize("kernel", [0, 1, 2])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3])
 def test_diagnostics_match_oracle_fields(storage, kernel):
     """The FP64 diagnostics reduced inside the step kernel (and by the
     macro pass) equal the same sums taken over the oracle's fields: mass,
@@ -271,7 +275,20 @@ def test_diagnostics_match_oracle_fields(storage, kernel):
         Z, Y, X = np.meshgrid(np.arange(g.nz), np.arange(g.ny), np.arange(g.nx), indexing="ij")
         X, Y, Z = X.reshape(-1), Y.reshape(-1), Z.reshape(-1)
         reg = (X >= box[0]) & (X < box[1]) & (Y >= box[2]) & (Y < box[3]) & (Z >= box[4]) & (Z < box[5])
+        # phi = 0.5 crossings towards a fluid +x neighbour inside the box
+        phi3 = phi.reshape(g.nz, g.ny, g.nx)
+        pn3 = np.roll(phi3, -1, axis=2)
+        ok3 = (fluid & reg).reshape(g.nz, g.ny, g.nx) & np.roll(fluid.reshape(g.nz, g.ny, g.nx), -1, axis=2)
+        X3 = X.reshape(g.nz, g.ny, g.nx)
+        down = ok3 & (phi3 >= 0.5) & (pn3 < 0.5)
+        up = ok3 & (phi3 < 0.5) & (pn3 >= 0.5)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            xd = X3 + (phi3 - 0.5) / (phi3 - pn3)
+            xu = X3 + (0.5 - phi3) / (pn3 - phi3)
+        front = xd[down].max() if down.any() else -1.0
+        rear = xu[up].min() if up.any() else -1.0
         return dict(mass=phi[fluid].sum(), n_heavy=float(((phi >= 0.5) & fluid).sum()),
+                    front_x=front, rear_x=rear,
                     p_heavy=P[fluid & (phi > 0.95)].mean(), p_light=P[fluid & (phi < 0.05)].mean(),
                     u_max=np.sqrt(u2[fluid].max()), kinetic=(0.5 * m["rho"] * u2)[fluid].sum(),
                     cl_count=float(cl.sum()), cl_mean=[X[cl].mean(), Y[cl].mean(), Z[cl].mean()],
@@ -290,6 +307,10 @@ def test_diagnostics_match_oracle_fields(storage, kernel):
         assert abs(d["u_max"] - e["u_max"]) <= TOL_U[storage]
         assert abs(d["kinetic"] - e["kinetic"]) <= 1e-4 * e["kinetic"] + 1e-15
         assert d["nonfinite"] == 0
+        assert e["front_x"] > 0 and e["rear_x"] > 0
+        xtol = 1e-9 if storage == "fp64" else 1e-3
+        assert abs(d["front_x"] - e["front_x"]) <= xtol, (d["front_x"], e["front_x"])
+        assert abs(d["rear_x"] - e["rear_x"]) <= xtol, (d["rear_x"], e["rear_x"])
 
 
 def test_async_diagnostics_match_sync_reads():

@@ -9,9 +9,10 @@ compensation of its own outgoing ones (rest population), at most
 2 (1 - w_0) 2^-12 = 3.3e-4 (FP16) or 2.6e-3 (BF16) per step; the test allows
 n times that.  Total phi is conserved (mass-conserving rounding of h).
 
-Physics: the Laplace pressure jump of the static droplet and the mass drift
-after 2000 steps, against the FP64 oracle (target for the reduced-precision
-form: Laplace pressure within 1 % of the oracle)."""
+Error table: the Laplace pressure jump of the static droplet, the contact
+angle of a drop on a flat wall and the mass drift, for each storage format
+against the FP64 oracle (target for the reduced-precision form: Laplace
+pressure and contact angle within 1 % of the oracle)."""
 import numpy as np
 import pytest
 
@@ -36,36 +37,98 @@ def test_reduced_storage_pointwise_bound(storage, kernel):
         assert e["phi"] <= max(s, 1) * PER_STEP[storage] * 1.0001, (storage, s, e)
 
 
-@pytest.mark.slow
-def test_reduced_storage_laplace_and_mass():
-    """Static droplet (32^3, R=8): pressure jump p_heavy - p_light and mass
-    after 2000 steps for FP32, FP16 and BF16 storage against the oracle."""
+def _drop_on_flat_wall(theta):
+    """Quasi 2-D drop on a flat floor (72 x 1 x 30, walls z = 0 and 29, the
+    lid at 90 deg), started as a half disc of radius 14: geometry, params
+    and initial phi, as in the oracle's contact-angle pin."""
+    nx, ny, nz, R, W = 72, 1, 30, 14.0, 4.0
+    solid = np.zeros((nz, ny, nx), np.uint8)
+    solid[0] = 1
+    solid[-1] = 1
+    nw = np.zeros((nz, ny, nx, 3))
+    nw[1, :, :, 2] = 1
+    nw[-2, :, :, 2] = -1
+    th = np.full((nz, ny, nx), theta)
+    th[-2] = 90.0
+    p = dict(sigma=0.01, W=W, M=0.05, rho_H=1.0, rho_L=1e-3, nu_H=0.1, nu_L=0.1, blend=0.0)
+    Z, Y, X = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    r = np.sqrt((X - 36.0) ** 2 + (Z - 0.5) ** 2)
+    phi0 = (0.5 * (1 + np.tanh(2 * (R - r) / W)) * (1 - solid)).reshape(-1)
+    return (nx, ny, nz), solid.reshape(-1), nw.reshape(-1), th.reshape(-1), p, phi0
+
+
+def _wall_angle(phi, dims):
+    """Contact angle (deg) from a circle fitted to the phi = 0.5 contour above
+    the wall's diffuse layer (Sec. IV A), wall plane at z = 0.5."""
+    import math
+    import synth
+    nx, ny, nz = dims
+    phi = phi.reshape(nz, ny, nx)[:, 0, :]
+    pts = synth.contour_points(phi[1:-1], 0.5)
+    pts[:, 1] += 1.0
+    pts = pts[pts[:, 1] > 0.5 + 2.0]
+    cx, cz, rr = synth.fit_circle(pts)
+    return math.degrees(math.acos(max(-1.0, min(1.0, (0.5 - cz) / rr))))
+
+
+# Error table of the reduced-precision form against the FP64 oracle (the
+# acceptance bar for 16-bit storage: Laplace pressure and contact angle each
+# within 1 % of the oracle; FP32 is held to the parity scale).
+BAR_DP = {"fp32": 1e-5, "fp16": 1e-2, "bf16": 1e-2}
+BAR_ANGLE = {"fp32": 1e-5, "fp16": 1e-2, "bf16": 1e-2}
+BAR_DRIFT = {"fp32": 5e-6, "fp16": 1e-4, "bf16": 1e-4}
+
+
+def test_precision_error_table():
+    """Laplace pressure jump of the static droplet (32^3, R = 8, 2000 steps),
+    contact angle of a drop on a flat wall (60 and 120 deg, 3000 steps) and
+    relative mass drift, for FP32, FP16 and BF16 storage (FP32 arithmetic),
+    each against the FP64 oracle run of the same case; the table is printed
+    and every entry held to its bar."""
     import os
     import oracle as O
     from paper_2512_01032_gb300 import pflb
+    rows = {st: {} for st in ("fp32", "fp16", "bf16")}
+    # Laplace jump
     g, p, init = CS.droplet_case()
     op = {k: v for k, v in p.items() if k in CS.ORACLE_KEYS}
     Orc = O.OracleLattice(g.nx, g.ny, g.nz, nthreads=os.cpu_count() or 1, **op)
     phi0 = O.tanh_phi(0, (g.nx, g.ny, g.nz), init["center"], init["R"], p["W"])
     Orc.init_phi(phi0)
-    m0 = Orc.macros()
     Orc.step(2000)
     m = Orc.macros()
     ref_dp = m["P"][m["phi"] > 0.95].mean() - m["P"][m["phi"] < 0.05].mean()
-    ref_mass0 = m0["phi"].sum()
-    out = {}
-    for storage in ("fp32", "fp16", "bf16"):
-        L = pflb.Lattice(g.nx, g.ny, g.nz, storage=storage, **p)
+    for st in rows:
+        L = pflb.Lattice(g.nx, g.ny, g.nz, storage=st, **p)
         L.init_tanh(0, init["center"], init["R"])
         d0 = L.diag()
         L.step(2000)
         d = L.diag()
-        out[storage] = dict(dp_err=abs(d["dp"] - ref_dp) / abs(ref_dp),
-                            drift=abs(d["mass"] - d0["mass"]) / ref_mass0)
-    print("precision errors vs FP64 oracle:", out, "reference dp", ref_dp)
-    assert out["fp32"]["dp_err"] < 1e-3
-    assert out["fp16"]["dp_err"] < 1e-2
-    assert out["fp32"]["drift"] < 1e-5
-    assert out["fp16"]["drift"] < 1e-5
-    assert out["bf16"]["drift"] < 1e-5
-    assert out["bf16"]["dp_err"] < 0.2
+        rows[st]["dp"] = (d["dp"] - ref_dp) / ref_dp
+        rows[st]["drift_drop"] = (d["mass"] - d0["mass"]) / d0["mass"]
+        L.close()
+    # contact angle on a flat wall
+    for theta in (60.0, 120.0):
+        dims, solid, nw, th, pw, phi0 = _drop_on_flat_wall(theta)
+        Orc = O.OracleLattice(*dims, solid=solid, wall_normal=nw, theta_cells=th,
+                              nthreads=os.cpu_count() or 1, **pw)
+        Orc.init_phi(phi0)
+        Orc.step(3000)
+        ref = _wall_angle(Orc.macros()["phi"], dims)
+        for st in rows:
+            L = pflb.Lattice(*dims, solid=solid, wall_normal=nw, theta_cells=th, storage=st, **pw)
+            L.init_phi(phi0)
+            d0 = L.diag()
+            L.step(3000)
+            d = L.diag()
+            rows[st][f"angle{theta:.0f}"] = (_wall_angle(L.read("phi"), dims) - ref) / ref
+            rows[st][f"drift_wall{theta:.0f}"] = (d["mass"] - d0["mass"]) / d0["mass"]
+            L.close()
+    print("relative errors against the FP64 oracle (reference dp %.6e):" % ref_dp)
+    for st, r in rows.items():
+        print(" ", st, {k: "%+.2e" % v for k, v in r.items()})
+    for st, r in rows.items():
+        assert abs(r["dp"]) <= BAR_DP[st], (st, r)
+        assert abs(r["angle60"]) <= BAR_ANGLE[st] and abs(r["angle120"]) <= BAR_ANGLE[st], (st, r)
+        for k in ("drift_drop", "drift_wall60", "drift_wall120"):
+            assert abs(r[k]) <= BAR_DRIFT[st], (st, k, r)

@@ -53,9 +53,14 @@ def test_fields_noalloc_matches_existing_pass(tmp_path):
     for call in range(2):
         fields.fill_(float("nan"))
         torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         d = pflb.fields_noalloc(nx, ny, nz, h_t.data_ptr(), g_t.data_ptr(), p,
                                 fields_ptr=fields.data_ptr(), stream=None)
         torch.cuda.synchronize()
+        if call == 1:
+            # the first call on a device loads the entry point's code and
+            # scratch; a later call must not take any device memory
+            assert torch.cuda.mem_get_info()[0] == free0
         f = fields.cpu().numpy().reshape(6, N)
         for k, name in enumerate(("phi", "rho", "P", "ux", "uy", "uz")):
             ref = ref_f[name]
@@ -85,3 +90,20 @@ def test_fields_noalloc_rejects_oversize_lattice():
         pflb.fields_noalloc(128, 128, 128, buf.data_ptr(), buf.data_ptr(), p)
     assert ei.value.status == pflb.ERR_ARG
     assert "at most" in str(ei.value)
+
+
+def test_fields_noalloc_rejects_16_bit_storage():
+    """The entry point reads FP32 populations; parameters that name another
+    storage are refused instead of being reinterpreted."""
+    import torch
+    from paper_2512_01032_gb300 import pflb
+
+    buf = torch.zeros(19 * 8 * 8 * 8, device="cuda")
+    out = torch.empty(6 * 8 * 8 * 8, dtype=torch.float64, device="cuda")
+    for st in ("bf16", "fp16", "fp64"):
+        p = pflb.default_params(storage=st)
+        with pytest.raises(pflb.PflbError) as ei:
+            pflb.fields_noalloc(8, 8, 8, buf.data_ptr(), buf.data_ptr(), p,
+                                fields_ptr=out.data_ptr())
+        assert ei.value.status == pflb.ERR_ARG
+        assert "FP32" in str(ei.value)
