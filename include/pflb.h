@@ -342,11 +342,15 @@ pflb_status pflb_fields_noalloc(int nx, int ny, int nz, const float *h_dev, cons
                                 pflb_diag_t *diag_out, void *cuda_stream);
 
 /* ------------------------------------------------------------- batches
- * Many independent lattices (of any sizes) advanced together by one
- * persistent kernel: a grid of (SMs x blocks per SM) blocks pulls work
- * items -- one per (lattice, tile column, chunk of z planes) -- from a device
- * work list, so small lattices that could not fill the GPU on their own
- * share it.  No work item reads another lattice, so a lattice's result does
+ * Many independent lattices (of any sizes) advanced together by persistent
+ * kernels: a grid of (SMs x blocks per SM) blocks pulls work items -- one
+ * per (lattice, tile column, chunk of z planes) -- from a device work list,
+ * so small lattices that could not fill the GPU on their own share it.
+ * Lattices that PFLB_KERNEL_PIPE can run (periodic x, nx a multiple of 4, of
+ * 8 at 16-bit storage) are marched by its pipelined per-cell code, 32 x 4
+ * tiles with an automatic number of planes, their wall nodes by a second
+ * small kernel; the others by the fused tile march with the launch shape
+ * below.  No work item reads another lattice, so a lattice's result does
  * not depend on what it is batched with: it is bit-identical to the same
  * lattice in a batch of its own.  Against pflb_step on that lattice it
  * agrees to rounding (the two kernels are compiled separately and may
@@ -360,9 +364,10 @@ typedef struct pflb_batch pflb_batch;
 pflb_status pflb_batch_create(pflb_lattice *const *lattices, int count, void *cuda_stream,
                               pflb_batch **out);
 
-/* Launch shape: bx * by threads per block (same rules as pflb_set_kernel),
- * lz planes per work item, blocks per SM (0 = as many as fit, at most 4);
- * zeros keep the current values (default 32 x 4 x 16, 0). */
+/* Launch shape of the fused tile march: bx * by threads per block (same
+ * rules as pflb_set_kernel), lz planes per work item, blocks per SM (0 = as
+ * many as fit, at most 4); zeros keep the current values (default
+ * 32 x 4 x 16, 0). */
 pflb_status pflb_batch_set_launch(pflb_batch *b, int bx, int by, int lz, int blocks_per_sm);
 
 /* Autotuner: times trial_steps steps of each of a fixed set of launch shapes

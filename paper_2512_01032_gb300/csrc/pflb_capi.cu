@@ -39,6 +39,7 @@ struct pflb_batch {
   cudaEvent_t ev = nullptr;
   cudaGraphExec_t graph = nullptr;  // kGraphSteps plain steps
   int graph_nxbc = -1;               // open-boundary lattice count the graph was captured for
+  std::vector<char> pipe_set;        // lattices the work lists were built to march pipelined
   bool poisoned = false;
 };
 static constexpr int kGraphSteps = 16;
@@ -212,6 +213,7 @@ std::vector<uint32_t> link_masks(const pflb_geometry *g) {
 struct HostGeom {
   std::vector<uint8_t> flags;
   std::vector<int> widx;
+  std::vector<int> wcell;    // [nw] cell of each wall node
   std::vector<uint32_t> wmask;
   std::vector<double> wgeo;  // [5][nw]
 };
@@ -236,6 +238,19 @@ void build_geometry(const pflb_geometry *g, const pflb_params *p, HostGeom &hg) 
   }
   const size_t nw = cells.size();
   hg.wmask = masks;
+  hg.wcell.assign(cells.begin(), cells.end());
+  // cells whose phi a wall node's stencil reads: the node and its fluid
+  // neighbours (periodic wrap)
+  for (size_t k = 0; k < nw; ++k) {
+    const long long c = cells[k];
+    const int x = (int)(c % g->nx), y = (int)((c / g->nx) % g->ny), z = (int)(c / ((long long)g->nx * g->ny));
+    for (int i = 0; i < pflb::Q; ++i) {
+      const long long nb = wrap(x + pflb::cx_of(i), g->nx) +
+                           (long long)g->nx * (wrap(y + pflb::cy_of(i), g->ny) +
+                                               (long long)g->ny * wrap(z + pflb::cz_of(i), g->nz));
+      if (!(hg.flags[nb] & pflb::F_SOLID)) hg.flags[nb] |= pflb::F_NEAR;
+    }
+  }
   hg.wgeo.assign(5 * nw, 0.0);
   for (size_t k = 0; k < nw; ++k) {
     const long long c = cells[k];
@@ -272,7 +287,8 @@ cudaError_t dev_alloc(Lattice *L, T **ptr, size_t count) {
 
 void free_all(Lattice *L) {
   void *ptrs[] = {L->h[0], L->h[1], L->g, L->wp[0], L->wp[1], L->flags, L->widx, L->wmask,
-                  L->wgeo, L->ghost, L->phi, L->diag, L->out, L->phi0, L->err, L->bcm};
+                  L->wgeo, L->ghost, L->phi, L->diag, L->out, L->phi0, L->err, L->bcm,
+                  L->wcell};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (L->aux) cudaStreamDestroy(L->aux);
@@ -288,7 +304,7 @@ int64_t bytes_for(long long N, long long nw, int storage) {
   const int64_t r = (int64_t)compute_bytes(storage);
   const int64_t flag_bytes = (N + 3) & ~(int64_t)3;  // whole 4-byte words
   return (2 * (int64_t)h_slots_of(storage) + 19) * N * e + 2 * 18 * nw * e + flag_bytes +
-         N * 4 + nw * 4 + 5 * nw * r + 18 * nw * r + N * r + 96 * 8 + 4;
+         N * 4 + nw * 8 + 5 * nw * r + 18 * nw * r + N * r + 96 * 8 + 4;
 }
 
 // TMA descriptors of the two h buffers (4-D: x, y, z, direction; box
@@ -414,6 +430,7 @@ pflb_status pflb_create(const pflb_geometry *geom, const pflb_params *params, vo
   A((void **)&L->flags, (N + 3) & ~(size_t)3);  // whole 4-byte words (staged copies)
   A((void **)&L->widx, N * sizeof(int));
   A((void **)&L->wmask, nw * sizeof(uint32_t));
+  A((void **)&L->wcell, nw * sizeof(int));
   A(&L->wgeo, 5 * nw * Rb);
   A(&L->ghost, 18 * nw * Rb);
   A(&L->phi, N * Rb);
@@ -446,6 +463,8 @@ pflb_status pflb_create(const pflb_geometry *geom, const pflb_params *params, vo
     e = cudaMemcpyAsync(L->widx, hg.widx.data(), N * sizeof(int), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && nw)
     e = cudaMemcpyAsync(L->wmask, hg.wmask.data(), nw * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && nw)
+    e = cudaMemcpyAsync(L->wcell, hg.wcell.data(), nw * sizeof(int), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && nw)
     e = cudaMemcpyAsync(L->wgeo, wgeo_src, 5 * nw * Rb, cudaMemcpyHostToDevice, st);
   void *zero_bufs[] = {L->h[0], L->h[1], L->g, L->wp[0], L->wp[1], L->ghost, L->phi, L->err};
@@ -924,11 +943,86 @@ static void batch_drop_graph(pflb_batch *b) {
   b->graph = nullptr;
 }
 
+// Which lattices of the batch the pipelined march can run (the others use
+// the fused tile march of k_batch).
+static std::vector<char> batch_pipe_set(const pflb_batch *b) {
+  std::vector<char> on(b->lats.size());
+  for (size_t l = 0; l < b->lats.size(); ++l) on[l] = pflb::pipe_layout_ok(*b->lats[l]) ? 1 : 0;
+  return on;
+}
+
+// Work lists of the pipelined lattices (tile columns of 32 x 4 in chunks of
+// plz planes, plz minimising rounds of resident blocks x (plz + 0.6) as for
+// a single lattice; wall nodes in chunks of 128), and their grid.
+static pflb_status batch_build_pipe_items(pflb_batch *b) {
+  BCK(b, cudaStreamSynchronize(b->dev.stream));  // the old lists may still be in use
+  std::vector<int4> items;
+  std::vector<int2> witems;
+  long long cols = 0;
+  int maxz = 1;
+  for (int l = 0; l < (int)b->lats.size(); ++l) {
+    if (!b->pipe_set[l]) continue;
+    const Lattice *L = b->lats[l];
+    cols += (long long)((L->nx + 31) / 32) * ((L->ny + 3) / 4);
+    maxz = std::max(maxz, L->nz);
+    for (int r = 0; r < L->nw; r += 128) witems.push_back(make_int2(l, r));
+  }
+  const int per = dispatch_storage(b->storage, [&](auto *s_, auto *r_) {
+    PFLB_SR_TYPES
+    return pflb::batch_pipe_blocks_per_sm<S, R>();
+  });
+  const long long slots = (long long)per * b->nsm;
+  int best = 8;
+  double best_cost = 1e300;
+  for (int lz = std::min(32, maxz); lz >= 2 && cols > 0; --lz) {
+    long long blocks = 0;
+    for (int l = 0; l < (int)b->lats.size(); ++l)
+      if (b->pipe_set[l]) {
+        const Lattice *L = b->lats[l];
+        blocks += (long long)((L->nx + 31) / 32) * ((L->ny + 3) / 4) * ((L->nz + lz - 1) / lz);
+      }
+    const double cost = (double)((blocks + slots - 1) / slots) * (lz + 0.6);
+    if (cost < best_cost - 1e-9) {
+      best_cost = cost;
+      best = lz;
+    }
+  }
+  b->dev.plz = best;
+  for (int l = 0; l < (int)b->lats.size(); ++l) {
+    if (!b->pipe_set[l]) continue;
+    const Lattice *L = b->lats[l];
+    for (int z0 = 0; z0 < L->nz; z0 += best)
+      for (int y0 = 0; y0 < L->ny; y0 += 4)
+        for (int x0 = 0; x0 < L->nx; x0 += 32) items.push_back(make_int4(l, x0, y0, z0));
+  }
+  if (b->dev.pitems) cudaFree(b->dev.pitems);
+  if (b->dev.witems) cudaFree(b->dev.witems);
+  b->dev.pitems = b->dev.witems = nullptr;
+  b->dev.npitems = (int)items.size();
+  b->dev.nwitems = (int)witems.size();
+  if (!items.empty()) {
+    BCK(b, cudaMalloc(&b->dev.pitems, items.size() * sizeof(int4)));
+    BCK(b, cudaMemcpyAsync(b->dev.pitems, items.data(), items.size() * sizeof(int4),
+                           cudaMemcpyHostToDevice, b->dev.stream));
+  }
+  if (!witems.empty()) {
+    BCK(b, cudaMalloc(&b->dev.witems, witems.size() * sizeof(int2)));
+    BCK(b, cudaMemcpyAsync(b->dev.witems, witems.data(), witems.size() * sizeof(int2),
+                           cudaMemcpyHostToDevice, b->dev.stream));
+  }
+  b->dev.pgrid = (int)std::max(1LL, std::min<long long>(b->dev.npitems, slots));
+  return PFLB_OK;
+}
+
 // Work list for the current launch shape, and the persistent grid size.
 static pflb_status batch_build_items(pflb_batch *b) {
+  b->pipe_set = batch_pipe_set(b);
+  pflb_status pst = batch_build_pipe_items(b);
+  if (pst != PFLB_OK) return pst;
   std::vector<int4> items;
   const int bx = b->dev.bx, by = b->dev.by, lz = b->dev.lz;
   for (int l = 0; l < (int)b->lats.size(); ++l) {
+    if (b->pipe_set[l]) continue;
     const Lattice *L = b->lats[l];
     for (int z0 = 0; z0 < L->nz; z0 += lz)
       for (int y0 = 0; y0 < L->ny; y0 += by)
@@ -941,8 +1035,9 @@ static pflb_status batch_build_items(pflb_batch *b) {
     b->items_cap = items.size();
   }
   b->dev.nitems = (int)items.size();
-  BCK(b, cudaMemcpyAsync(b->dev.items, items.data(), items.size() * sizeof(int4),
-                         cudaMemcpyHostToDevice, b->dev.stream));
+  if (!items.empty())
+    BCK(b, cudaMemcpyAsync(b->dev.items, items.data(), items.size() * sizeof(int4),
+                           cudaMemcpyHostToDevice, b->dev.stream));
   const int fit = dispatch_storage(b->storage, [&](auto *s_, auto *r_) {
     PFLB_SR_TYPES
     return pflb::batch_max_blocks_per_sm<S, R>(bx, by);
@@ -990,6 +1085,7 @@ extern "C" pflb_status pflb_batch_create(pflb_lattice *const *lattices, int coun
   if (e == cudaSuccess) e = cudaMalloc(&b->dev.descs, 2 * (size_t)count * b->desc_bytes);
   if (e == cudaSuccess) e = cudaMalloc((void **)&b->dev.par0, count * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc((void **)&b->dev.counter, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&b->dev.pcounter, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc((void **)&b->dev.bstep, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc((void **)&b->dev.xspecs, count * sizeof(pflb::XbcSpec));
   if (e == cudaSuccess) e = cudaMalloc((void **)&b->dev.xlist, count * sizeof(int));
@@ -1027,6 +1123,12 @@ extern "C" pflb_status pflb_batch_set_launch(pflb_batch *b, int bx, int by, int 
 // Runs nsteps on the batch stream (graph replay for the plain steps).
 static pflb_status batch_run(pflb_batch *b, int64_t nsteps, bool diag_last) {
   const int n = (int)b->lats.size();
+  // open boundaries switched on or off since the work lists were built
+  // move a lattice between the pipelined and the fused march
+  if (batch_pipe_set(b) != b->pipe_set) {
+    pflb_status st = batch_build_items(b);
+    if (st != PFLB_OK) return st;
+  }
   // order after every lattice's own stream
   for (Lattice *L : b->lats) {
     if (L->stream == b->dev.stream) continue;
@@ -1149,8 +1251,9 @@ extern "C" void pflb_batch_destroy(pflb_batch *b) {
   if (!b) return;
   if (b->dev.stream) cudaStreamSynchronize(b->dev.stream);
   batch_drop_graph(b);
-  void *ptrs[] = {b->dev.descs, b->dev.par0, b->dev.items, b->dev.counter, b->dev.bstep,
-                  b->dev.xspecs, b->dev.xlist};
+  void *ptrs[] = {b->dev.descs,   b->dev.par0,   b->dev.items,  b->dev.counter,
+                  b->dev.bstep,   b->dev.xspecs, b->dev.xlist,  b->dev.pitems,
+                  b->dev.witems,  b->dev.pcounter};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (b->ev) cudaEventDestroy(b->ev);

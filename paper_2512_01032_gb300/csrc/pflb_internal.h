@@ -30,6 +30,7 @@ struct Lattice {
   uint8_t *flags = nullptr;         // [N]
   int *widx = nullptr;              // [N]
   uint32_t *wmask = nullptr;        // [nw]
+  int *wcell = nullptr;             // [nw] cell of each wall node
   void *wgeo = nullptr;             // [5][nw] compute type
   void *ghost = nullptr;            // [18][nw] compute type
   void *phi = nullptr;              // [N] compute type (two-pass path)
@@ -81,15 +82,27 @@ struct BatchDev {
   XbcSpec *xspecs = nullptr;  // [nlat] open-boundary specs (type 0: periodic x)
   int *xlist = nullptr;       // [nxbc] lattices with open boundaries
   int nxbc = 0;
+  // lattices run by the pipelined march (pipe_layout_ok): their own work
+  // list of 32 x 4 tile columns in chunks of plz planes, and their wall
+  // nodes in chunks of 128 records (int2: lattice, first record)
+  void *pitems = nullptr;
+  int npitems = 0;
+  int *pcounter = nullptr;
+  int plz = 8, pgrid = 0;
+  void *witems = nullptr;
+  int nwitems = 0;
 };
 
 // The pipelined step kernel runs with periodic x and nx a multiple of the
 // values per 16-byte chunk (4 at FP32, 8 at 16-bit storage) and of 4 (its
 // 4-byte flag words), so that its row chunks and flag words are aligned;
 // elsewhere PFLB_KERNEL_PIPE falls back to the fused kernel.
-inline bool pipe_kernel_runs(const Lattice &L) {
+inline bool pipe_layout_ok(const Lattice &L) {
   const int v = 16 / (int)L.elem;
-  return L.kernel == PFLB_KERNEL_PIPE && !L.bc_on && L.nx % (v > 4 ? v : 4) == 0;
+  return !L.bc_on && L.nx % (v > 4 ? v : 4) == 0;
+}
+inline bool pipe_kernel_runs(const Lattice &L) {
+  return L.kernel == PFLB_KERNEL_PIPE && pipe_layout_ok(L);
 }
 
 // Sets the thread-local message returned by pflb_last_error().
@@ -135,6 +148,7 @@ template <class S, class R> size_t batch_desc_bytes();
 template <class S, class R> void batch_build_descs(Lattice *const *lats, int n, char *host);
 template <class S, class R> cudaError_t batch_launch_step(const BatchDev &b, bool diag);
 template <class S, class R> int batch_max_blocks_per_sm(int bx, int by);
+template <class S, class R> int batch_pipe_blocks_per_sm();
 
 }  // namespace pflb
 

@@ -51,11 +51,13 @@ struct Args {
   const uint8_t *flags;
   const int *widx;
   const uint32_t *wmask;
+  const int *wcell;  // [nw] cell of each wall node
   const R *wgeo;     // [5][nw]: n_w (x,y,z), cos theta, sin theta
   R *ghost;          // [18][nw]
   const S *wp_rd;    // [18][nw]
   S *wp_wr;          // [18][nw]
   const R *phi;      // [N] phi field (two-pass path and field reads)
+  R *phi_w;          // the same field, written by the pipelined kernel for wall nodes' reads
   Model<R> m;
   double *diag;      // [D_COUNT] accumulator of this launch, or null
   double *diag_zero; // [32] accumulator of the next diagnostic launch, zeroed here
@@ -331,7 +333,7 @@ __device__ __forceinline__ void store_cell(const Args<S, R> &a, int c, uint32_t 
 
 // Full update (or macro evaluation) of one fluid cell: wall data, g
 // gather, then finish_cell.
-template <class S, class R, bool ODD, int MODE, bool DIAG, bool XBC = false>
+template <class S, class R, bool ODD, int MODE, bool DIAG, bool XBC = false, bool PAIRS = false>
 __device__ __forceinline__ void update_cell(const Args<S, R> &a, int x, int y, int z, int c,
                                             uint8_t f, R h[Q], R phi, R val[Q],
                                             DiagAcc<R> &acc) {
@@ -345,7 +347,8 @@ __device__ __forceinline__ void update_cell(const Args<S, R> &a, int x, int y, i
   }
   R g[Q];
   gather_g<S, R, ODD>(a, c, lm, rec, nb, g);
-  finish_cell<S, R, ODD, MODE, DIAG, XBC>(a, x, y, z, c, f, lm, rec, nb, h, g, phi, val, acc);
+  finish_cell<S, R, ODD, MODE, DIAG, XBC, PAIRS>(a, x, y, z, c, f, lm, rec, nb, h, g, phi, val,
+                                                 acc);
 }
 
 // Diagnostics are reduced in three levels: each cell's contributions (a

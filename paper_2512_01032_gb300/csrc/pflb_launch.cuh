@@ -63,11 +63,13 @@ static Args<S, R> make_args(Lattice &L) {
   a.flags = L.flags;
   a.widx = L.widx;
   a.wmask = L.wmask;
+  a.wcell = L.wcell;
   a.wgeo = (const R *)L.wgeo;
   a.ghost = (R *)L.ghost;
   a.wp_rd = (const S *)L.wp[rd];
   a.wp_wr = (S *)L.wp[rd ^ 1];
   a.phi = (const R *)L.phi;
+  a.phi_w = (R *)L.phi;
   a.m = make_model<R>(L.p);
   a.diag = nullptr;
   a.diag_zero = nullptr;
@@ -174,6 +176,9 @@ static cudaError_t launch_pipe_t(Lattice &L, Args<S, R> &a) {
   const dim3 grid((L.nx + PP_BX - 1) / PP_BX, (L.ny + PP_BY - 1) / PP_BY,
                   (L.nz + L.lz - 1) / L.lz);
   k_pipe<S, R, ODD, DIAG><<<grid, PP_NT, sizeof(PipeSmem<S, R>), L.stream>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || L.nw == 0) return e;
+  k_wall<S, R, ODD, DIAG><<<(L.nw + 127) / 128, 128, 0, L.stream>>>(a);
   return cudaGetLastError();
 }
 
@@ -335,6 +340,67 @@ void batch_build_descs(Lattice *const *lats, int n, char *host) {
   }
 }
 
+template <class S, class R, bool DIAG>
+static cudaError_t batch_pipe_attrs() {
+  static unsigned long long done = 0;  // bit d: set on device d
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+  if (bit && (done & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(k_batch_pipe<S, R, DIAG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(PipeSmem<S, R>) + sizeof(Args<S, R>)));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_batch_pipe<S, R, DIAG>,
+                           cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e != cudaSuccess) return e;
+  done |= bit;
+  return cudaSuccess;
+}
+
+template <class S, class R>
+int batch_pipe_blocks_per_sm() {
+  int nb = 0;
+  if (batch_pipe_attrs<S, R, true>() != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &nb, k_batch_pipe<S, R, true>, PP_NT, sizeof(PipeSmem<S, R>) + sizeof(Args<S, R>)) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return nb > 0 ? nb : 1;
+}
+
+// The pipelined lattices of a batch: their march, then their wall nodes.
+template <class S, class R>
+static cudaError_t batch_launch_pipe(const BatchDev &b, bool diag) {
+  if (b.npitems == 0) return cudaSuccess;
+  const Args<S, R> *d = (const Args<S, R> *)b.descs;
+  cudaError_t e = cudaMemsetAsync(b.pcounter, 0, sizeof(int), b.stream);
+  if (e != cudaSuccess) return e;
+  const size_t smem = sizeof(PipeSmem<S, R>) + sizeof(Args<S, R>);
+  const int4 *it = (const int4 *)b.pitems;
+  if (diag) {
+    e = batch_pipe_attrs<S, R, true>();
+    if (e != cudaSuccess) return e;
+    k_batch_pipe<S, R, true><<<b.pgrid, PP_NT, smem, b.stream>>>(d, b.par0, it, b.npitems,
+                                                                b.pcounter, b.bstep, b.plz);
+  } else {
+    e = batch_pipe_attrs<S, R, false>();
+    if (e != cudaSuccess) return e;
+    k_batch_pipe<S, R, false><<<b.pgrid, PP_NT, smem, b.stream>>>(d, b.par0, it, b.npitems,
+                                                                 b.pcounter, b.bstep, b.plz);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess || b.nwitems == 0) return e;
+  const int2 *wit = (const int2 *)b.witems;
+  if (diag)
+    k_batch_wall<S, R, true><<<b.nwitems, 128, 0, b.stream>>>(d, b.par0, wit, b.bstep);
+  else
+    k_batch_wall<S, R, false><<<b.nwitems, 128, 0, b.stream>>>(d, b.par0, wit, b.bstep);
+  return cudaGetLastError();
+}
+
 template <class S, class R>
 cudaError_t batch_launch_step(const BatchDev &b, bool diag) {
   cudaError_t e = cudaMemsetAsync(b.counter, 0, sizeof(int), b.stream);
@@ -347,6 +413,12 @@ cudaError_t batch_launch_step(const BatchDev &b, bool diag) {
                                                               b.bstep);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+  }
+  e = batch_launch_pipe<S, R>(b, diag);
+  if (e != cudaSuccess) return e;
+  if (b.nitems == 0) {  // every lattice ran the pipelined march
+    k_batch_tick<<<1, 1, 0, b.stream>>>(b.bstep);
+    return cudaGetLastError();
   }
   const dim3 grid(b.grid), block(b.bx * b.by);
   if (diag && b.nxbc > 0)
@@ -382,6 +454,7 @@ int batch_max_blocks_per_sm(int bx, int by) {
 }
 
 #define PFLB_INSTANTIATE(S, R)                                                   \
+  template int batch_pipe_blocks_per_sm<S, R>();                                 \
   template size_t batch_desc_bytes<S, R>();                                      \
   template void batch_build_descs<S, R>(Lattice *const *, int, char *);         \
   template cudaError_t batch_launch_step<S, R>(const BatchDev &, bool);          \

@@ -85,6 +85,7 @@ enum {
 constexpr uint8_t F_SOLID = 1;
 constexpr uint8_t F_WALL = 2;
 constexpr uint8_t F_BC = 4;  // fluid cell of an open x boundary plane (reading R22)
+constexpr uint8_t F_NEAR = 8;  // fluid cell whose phi a wall node reads (the node or a neighbour)
 
 // Model parameters in the compute precision R (derived constants included).
 template <class R>

@@ -25,8 +25,10 @@
 // and nx is a multiple of V, a chunk never straddles the periodic seam and
 // wraps as a whole.  Rows and planes wrap individually.  Chunks whose cells
 // are all solid are not copied, using flag words staged one iteration
-// earlier still.  Wall cells read their wall records and wall populations
-// with ordinary loads; they are few.  16-bit storage stages the stored
+// earlier still.  Wall nodes (a few percent of the cells; their update
+// reads wall records, ghosts and wall populations) are left to k_wall,
+// launched after this kernel: k_pipe writes the phi of the cells those
+// nodes read to the phi field.  16-bit storage stages the stored
 // (weight-scaled) values and decodes them when they are read.
 //
 // Shared memory per block (FP32): h 2 planes x 19 x 6 rows x 40, g 19 x 4
@@ -98,36 +100,41 @@ __device__ __forceinline__ bool chunk_solid(const uint32_t *flrow, int ch) {
   return solid;
 }
 
+// One tile column (x0, y0) over planes [zb, ze) of lattice a, by the whole
+// block (PP_NT threads), with shared memory sm and the warp slots wacc of
+// the diagnostics (flushed into a.diag at the end).  Every thread returns
+// with no copy in flight; the caller separates two marches that reuse sm
+// by a barrier.
 template <class S, class R, bool ODD, bool DIAG>
-__global__ void __launch_bounds__(PP_NT, PFLB_PIPE_MIN_BLOCKS)
-    k_pipe(const __grid_constant__ Args<S, R> a) {
+__device__ __forceinline__ void pipe_march(const Args<S, R> &a, int x0, int y0, int zb, int ze,
+                                           PipeSmem<S, R> &sm, R (*wacc)[32]) {
   using SM = PipeSmem<S, R>;
   constexpr int V = SM::V, NCH = SM::NCH, HS = SM::HS;
   static_assert(F_SOLID == 1, "all_solid tests bit 0");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  SM &sm = *reinterpret_cast<SM *>(smem_raw);
-  __shared__ R wacc[DIAG_MAX_WARPS][32];
-  zero_next_diag(a);
   const int tid = threadIdx.x, tx = tid % PP_BX, ty = tid / PP_BX;
   const int nx = a.nx, ny = a.ny, nz = a.nz, sz = nx * ny;
-  const int x0 = blockIdx.x * PP_BX, y0 = blockIdx.y * PP_BY;
-  const int zb = blockIdx.z * a.lz, ze = min(zb + a.lz, nz);
   // A column beyond a ragged lattice edge still sums the cell it wraps to:
   // that is the periodic neighbour the last valid column needs.
   const bool valid = (x0 + tx) < nx && (y0 + ty) < ny;
   const int cx0 = (x0 + tx) % nx, cy0 = (y0 + ty) % ny;
   const int col = cx0 + nx * cy0;
-  const bool ring = tid < PP_NR;
+  // Side jobs (a ring cell's phi, staging units) go to the first `count`
+  // threads in thread order, so that a warp's copies and ring reads are
+  // contiguous (measured faster than spreading them evenly over the warps);
+  // job_of returns the job of this thread among `count`, or -1.
+  auto job_of = [&](int count) { return tid < count ? tid : -1; };
+  const int rj = job_of(PP_NR);
+  const bool ring = rj >= 0;
   int rx = 0, ry = 0;
   if (ring) {
-    if (tid < PP_PW) {
-      rx = tid;
+    if (rj < PP_PW) {
+      rx = rj;
       ry = 0;
-    } else if (tid < 2 * PP_PW) {
-      rx = tid - PP_PW;
+    } else if (rj < 2 * PP_PW) {
+      rx = rj - PP_PW;
       ry = PP_BY + 1;
     } else {
-      const int k = tid - 2 * PP_PW;
+      const int k = rj - 2 * PP_PW;
       rx = (k & 1) ? PP_BX + 1 : 0;
       ry = 1 + (k >> 1);
     }
@@ -149,10 +156,10 @@ __global__ void __launch_bounds__(PP_NT, PFLB_PIPE_MIN_BLOCKS)
   int g_rc[GPT], g_off[GPT][3];  // offsets of the chunk in rows y0 + r - 1, y0 + r, y0 + r + 1
 #pragma unroll
   for (int k = 0; k < HPT; ++k) {
-    const int u = tid + k * PP_NT;
+    const int u = HU <= PP_NT ? job_of(HU) : tid + k * PP_NT;
     h_rc[k] = -1;
     h_off[k] = 0;
-    if (u < HU) {
+    if (u >= 0 && u < HU) {
       const int half = u >= HU / 2, v = u - half * (HU / 2);
       const int r = v / NCH, ch = v - r * NCH;
       h_rc[k] = half << 16 | r << 8 | ch;
@@ -161,10 +168,10 @@ __global__ void __launch_bounds__(PP_NT, PFLB_PIPE_MIN_BLOCKS)
   }
 #pragma unroll
   for (int k = 0; k < GPT; ++k) {
-    const int u = tid + k * PP_NT;
+    const int u = GU <= PP_NT ? job_of(GU) : tid + k * PP_NT;
     g_rc[k] = -1;
     g_off[k][0] = g_off[k][1] = g_off[k][2] = 0;
-    if (u < GU) {
+    if (u >= 0 && u < GU) {
       const int half = u >= GU / 2, v = u - half * (GU / 2);
       const int r = v / NCH, ch = v - r * NCH;
       g_rc[k] = half << 16 | r << 8 | ch;
@@ -173,18 +180,14 @@ __global__ void __launch_bounds__(PP_NT, PFLB_PIPE_MIN_BLOCKS)
       for (int d = 0; d < 3; ++d) g_off[k][d] = xs + nx * wrap(y0 + r - 1 + d, ny);
     }
   }
-  int fl_off = -1;  // flag word of row tid / 10, word tid % 10
-  if (tid < PP_ROWS * PP_FW) {
-    const int r = tid / PP_FW, w = tid - r * PP_FW;
-    fl_off = wrap(x0 - 4 + 4 * w, nx) + nx * wrap(y0 - 1 + r, ny);
-  }
+  const int fj = job_of(PP_ROWS * PP_FW);  // flag word fj % 10 of row fj / 10
+  int fl_off = -1;
+  if (fj >= 0) fl_off = wrap(x0 - 4 + 4 * (fj % PP_FW), nx) + nx * wrap(y0 - 1 + fj / PP_FW, ny);
 
   // Flag words of plane zu: 6 rows x 10 words, one copy per thread.
   auto stage_flags = [&](int zu) {
-    if (fl_off >= 0) {
-      const int r = tid / PP_FW, w = tid - r * PP_FW;
-      cp_async_4(&sm.fl[zu & 3][r][w], a.flags + (fl_off + sz * wrapz(zu)));
-    }
+    if (fl_off >= 0)
+      cp_async_4(&sm.fl[zu & 3][fj / PP_FW][fj % PP_FW], a.flags + (fl_off + sz * wrapz(zu)));
   };
   // h of plane zu into slot zu & 1: 6 rows x NCH chunks x HS slots, the
   // slots split into two halves over the block's two thread halves.
@@ -263,8 +266,11 @@ __global__ void __launch_bounds__(PP_NT, PFLB_PIPE_MIN_BLOCKS)
     const S(*st)[PP_ROWS][SM::W] = sm.h[zu & 1];
     const uint32_t (*fl)[PP_FW] = sm.fl[zu & 3];
     R *dst = sm.phi[zu & 3];
-    dst[(ty + 1) * PP_PW + tx + 1] =
-        (flag_byte(fl, ty + 1, tx) & F_SOLID) ? R(0) : staged_phi(st, ty + 1, V + tx);
+    const uint8_t f = flag_byte(fl, ty + 1, tx);
+    const R v = (f & F_SOLID) ? R(0) : staged_phi(st, ty + 1, V + tx);
+    dst[(ty + 1) * PP_PW + tx + 1] = v;
+    // the cells whose phi a wall node reads go to the field for k_wall
+    if ((f & F_NEAR) && valid && zu >= zb && zu < ze) a.phi_w[col + sz * zu] = v;
     if (ring)
       dst[ry * PP_PW + rx] = (flag_byte(fl, ry, rx - 1) & F_SOLID) ? R(0)
                                                                    : staged_phi(st, ry, V - 1 + rx);
@@ -297,7 +303,7 @@ __global__ void __launch_bounds__(PP_NT, PFLB_PIPE_MIN_BLOCKS)
     phi_plane(z + 1);
     const int c = col + sz * z;
     const uint8_t f = flag_byte(sm.fl[z & 3], ty + 1, tx);
-    const bool fluid = valid && !(f & F_SOLID);
+    const bool fluid = valid && !(f & (F_SOLID | F_WALL));  // wall nodes: k_wall
     R h[Q], g[Q];
     if (fluid) {
       cell_h(sm.h[z & 1], ty + 1, V + tx, h);
@@ -313,15 +319,6 @@ __global__ void __launch_bounds__(PP_NT, PFLB_PIPE_MIN_BLOCKS)
     if (fluid) {
       Nbr nb;
       nb.init(cx0, cy0, z, nx, ny, nz);
-      uint32_t lm = 0;
-      int rec = 0;
-      if (f & F_WALL) {
-        rec = a.widx[c];
-        lm = a.wmask[rec];
-#pragma unroll
-        for (int k = 1; k < Q; ++k)
-          if ((lm >> opp_of(k)) & 1u) g[k] = ld_g<S, R>(a.wp_rd + ((k - 1) * a.nw + rec), k);
-      }
       const R *p0 = sm.phi[z & 3], *pm = sm.phi[(z - 1) & 3], *pp = sm.phi[(z + 1) & 3];
       R val[Q];
       const R phi = p0[o];
@@ -332,8 +329,9 @@ __global__ void __launch_bounds__(PP_NT, PFLB_PIPE_MIN_BLOCKS)
       }
       DiagAcc<R> acc;
       acc.zero();
-      finish_cell<S, R, ODD, MODE_STEP, DIAG, false, true>(a, cx0, cy0, z, c, f, lm, rec, nb, h,
-                                                           g, phi, val, acc);
+      // a bulk cell: no wall flag, no solid link
+      finish_cell<S, R, ODD, MODE_STEP, DIAG, false, true>(a, cx0, cy0, z, c, 0, 0u, 0, nb, h, g,
+                                                           phi, val, acc);
       if (DIAG) {
 #pragma unroll
         for (int k = 0; k < D_UMAX; ++k) tot.v[k] += acc.v[k];
@@ -346,6 +344,173 @@ __global__ void __launch_bounds__(PP_NT, PFLB_PIPE_MIN_BLOCKS)
   cp_async_wait_all();  // nothing is in flight at exit
   if (DIAG) {
     diag_warp_add(wacc[tid >> 5], tot);
+    diag_block_flush(a.diag, wacc);
+  }
+}
+
+// One lattice: a grid of (tile column, chunk of lz planes) blocks.
+template <class S, class R, bool ODD, bool DIAG>
+__global__ void __launch_bounds__(PP_NT, PFLB_PIPE_MIN_BLOCKS)
+    k_pipe(const __grid_constant__ Args<S, R> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ R wacc[DIAG_MAX_WARPS][32];
+  zero_next_diag(a);
+  const int zb = blockIdx.z * a.lz;
+  pipe_march<S, R, ODD, DIAG>(a, blockIdx.x * PP_BX, blockIdx.y * PP_BY, zb, min(zb + a.lz, a.nz),
+                              *reinterpret_cast<PipeSmem<S, R> *>(smem_raw), wacc);
+}
+
+// Many lattices: a persistent grid pulls work items (lattice, x0, y0, z0)
+// from an atomic counter, copies the lattice's step descriptor for its A-A
+// parity at this batch step ((par0[l] + t) & 1) into shared memory and
+// marches the item's tile column over LZ planes.  The first item of each
+// lattice zeroes its next diagnostic accumulator.
+// The step descriptor lives in shared memory here, so its fields cost
+// registers that k_pipe's constant-bank parameters do not: three blocks per
+// SM (168 registers) instead of four keep the march from spilling.
+template <class S, class R, bool DIAG>
+__global__ void __launch_bounds__(PP_NT, 3)
+    k_batch_pipe(const Args<S, R> *__restrict__ descs, const int *__restrict__ par0,
+                 const int4 *__restrict__ items, int nitems, int *counter, const int *bstep,
+                 int LZ) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PipeSmem<S, R> &sm = *reinterpret_cast<PipeSmem<S, R> *>(smem_raw);
+  Args<S, R> *sa = reinterpret_cast<Args<S, R> *>(smem_raw + sizeof(PipeSmem<S, R>));
+  __shared__ R wacc[DIAG_MAX_WARPS][32];
+  __shared__ int s_item;
+  const int tid = threadIdx.x;
+  const int t = *bstep;
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int idx = s_item;
+    if (idx >= nitems) break;
+    const int4 it = items[idx];
+    const int p = (par0[it.x] + t) & 1;
+    const int *src = reinterpret_cast<const int *>(descs + 2 * it.x + p);
+    int *dst = reinterpret_cast<int *>(sa);
+    for (int k = tid; k < (int)(sizeof(Args<S, R>) / 4); k += blockDim.x) dst[k] = src[k];
+    __syncthreads();
+    const Args<S, R> &a = *sa;
+    if (DIAG && it.y == 0 && it.z == 0 && it.w == 0 && tid < 32 && a.diag_zero)
+      a.diag_zero[tid] = 0.0;
+    const int ze = min(it.w + LZ, a.nz);
+    if (p)
+      pipe_march<S, R, true, DIAG>(a, it.y, it.z, it.w, ze, sm, wacc);
+    else
+      pipe_march<S, R, false, DIAG>(a, it.y, it.z, it.w, ze, sm, wacc);
+    __syncthreads();  // shared descriptor and staging buffers are reused by the next item
+  }
+}
+
+// Update of wall node rec of lattice a (k_cell's per-cell step: populations,
+// wall records and wall populations loaded directly; the neighbours' phi from
+// the field the pipelined march wrote for exactly these reads; solid
+// neighbours replaced by the lagged ghosts).
+__device__ __forceinline__ void prefetch_l1(const void *p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+// A wall node's update is a chain of dependent loads (record -> cell ->
+// link mask -> sources).  With only a few warps per SM nothing hides it, so
+// every line the update will read is prefetched into L1 first, in two
+// rounds: what the record indexes, then what the cell indexes.
+template <class S, class R, bool ODD>
+__device__ __forceinline__ void wall_prefetch(const Args<S, R> &a, int rec) {
+  const int nw = a.nw;
+  prefetch_l1(a.wcell + rec);
+  prefetch_l1(a.wmask + rec);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) prefetch_l1(a.wgeo + (k * nw + rec));
+#pragma unroll
+  for (int i = 0; i < Q - 1; ++i) {
+    prefetch_l1(a.ghost + (i * nw + rec));
+    prefetch_l1(a.wp_rd + (i * nw + rec));
+  }
+  const int c = a.wcell[rec];
+  const int x = c % a.nx, y = (c / a.nx) % a.ny, z = c / (a.nx * a.ny);
+  Nbr nb;
+  nb.init(x, y, z, a.nx, a.ny, a.nz);
+  prefetch_l1(a.flags + c);
+  prefetch_l1(a.widx + c);
+#pragma unroll
+  for (int i = 0; i < h_slots<S>(); ++i) prefetch_l1(a.hin[i] + c);
+#pragma unroll
+  for (int i = 1; i < Q; ++i) prefetch_l1(a.phi + (c + nb.off(i)));
+#pragma unroll
+  for (int k = 0; k < Q; ++k)
+    prefetch_l1(ODD ? a.g[opp_of(k)] + (c + nb.off(opp_of(k))) : a.g[k] + c);
+}
+
+template <class S, class R, bool ODD, bool DIAG>
+__device__ __forceinline__ void wall_node(const Args<S, R> &a, int rec, DiagAcc<R> &acc) {
+  wall_prefetch<S, R, ODD>(a, rec);
+  const int c = a.wcell[rec];
+  const uint8_t f = a.flags[c];
+  const int x = c % a.nx, y = (c / a.nx) % a.ny, z = c / (a.nx * a.ny);
+  Nbr nb;
+  nb.init(x, y, z, a.nx, a.ny, a.nz);
+  R h[Q], val[Q];
+  ld_h_cell<S, R>(a.hin, c, h);
+  R phi = R(0);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) phi += h[i];
+#pragma unroll
+  for (int i = 1; i < Q; ++i) val[i] = a.phi[c + nb.off(i)];
+  update_cell<S, R, ODD, MODE_STEP, DIAG, false, true>(a, x, y, z, c, f, h, phi, val, acc);
+}
+
+// Wall nodes of a step whose bulk cells k_pipe updates, one thread per wall
+// node; it runs after k_pipe on the same stream.  The two kernels touch
+// disjoint data: under A-A every g slot is read and written by one cell,
+// h is pushed from each cell into slots no other cell writes, and only wall
+// nodes use the ghosts and wall populations.
+template <class S, class R, bool ODD, bool DIAG>
+__global__ void __launch_bounds__(128) k_wall(const __grid_constant__ Args<S, R> a) {
+  __shared__ R wacc[DIAG_MAX_WARPS][32];
+  if (DIAG) {
+    diag_block_zero(wacc);
+    __syncthreads();
+  }
+  const int rec = blockIdx.x * blockDim.x + threadIdx.x;
+  DiagAcc<R> acc;
+  acc.zero();
+  if (rec < a.nw) wall_node<S, R, ODD, DIAG>(a, rec, acc);
+  if (DIAG) {
+    diag_warp_add(wacc[threadIdx.x >> 5], acc);
+    diag_block_flush(a.diag, wacc);
+  }
+}
+
+// Wall nodes of the batch's pipelined lattices: block b takes item
+// (lattice, first record) = witems[b] and its 128 records, for the
+// lattice's parity at this batch step.
+template <class S, class R, bool DIAG>
+__global__ void __launch_bounds__(128)
+    k_batch_wall(const Args<S, R> *__restrict__ descs, const int *__restrict__ par0,
+                 const int2 *__restrict__ witems, const int *bstep) {
+  __shared__ R wacc[DIAG_MAX_WARPS][32];
+  __shared__ __align__(16) unsigned char sa_raw[sizeof(Args<S, R>)];
+  Args<S, R> *sa = reinterpret_cast<Args<S, R> *>(sa_raw);
+  const int2 it = witems[blockIdx.x];
+  const int p = (par0[it.x] + *bstep) & 1;
+  const int *src = reinterpret_cast<const int *>(descs + 2 * it.x + p);
+  int *dst = reinterpret_cast<int *>(sa);
+  for (int k = threadIdx.x; k < (int)(sizeof(Args<S, R>) / 4); k += blockDim.x) dst[k] = src[k];
+  if (DIAG) diag_block_zero(wacc);
+  __syncthreads();
+  const Args<S, R> &a = *sa;
+  const int rec = it.y + threadIdx.x;
+  DiagAcc<R> acc;
+  acc.zero();
+  if (rec < a.nw) {
+    if (p)
+      wall_node<S, R, true, DIAG>(a, rec, acc);
+    else
+      wall_node<S, R, false, DIAG>(a, rec, acc);
+  }
+  if (DIAG) {
+    diag_warp_add(wacc[threadIdx.x >> 5], acc);
     diag_block_flush(a.diag, wacc);
   }
 }

@@ -170,7 +170,9 @@ def test_estimate_bytes_counts_wall_nodes():
     N = n ** 3
     assert empty == 3 * 19 * N * 4 + N * 5 + N * 4 + 96 * 8 + 4
     nw = 2 * n * n  # planes z = 1 and z = n-1 (periodic) touch the solid layer
-    assert walled - empty == nw * (2 * 18 * 4 + 4 + 5 * 4 + 18 * 4)
+    # per wall node: two wall-population buffers, link mask, cell index,
+    # geometry (5) and ghosts (18)
+    assert walled - empty == nw * (2 * 18 * 4 + 4 + 4 + 5 * 4 + 18 * 4)
 
 
 def test_no_cpu_fallback_without_a_gpu():

@@ -6,10 +6,13 @@ A-A parity each lattice starts from, and the split of the step count into
 captured-graph replays and single launches: the per-cell code is the same
 compiled function and no cell reads another lattice's data.
 
-Against the single-lattice fused kernel the agreement is to rounding: the
-two kernels are compiled separately, so the compiler may contract a
-multiply and an add into one FMA in one and not in the other (a difference
-of one rounding, 1e-16 relative in FP64, that the step map then carries)."""
+A batch marches each lattice with the per-cell code of the kernel that
+lattice runs alone by default: the pipelined march where its x extent and
+boundaries allow it, the fused tile march otherwise.  Against that
+single-lattice kernel the agreement is to rounding: the kernels are compiled
+separately, so the compiler may contract a multiply and an add into one FMA
+in one and not in the other (a difference of one rounding, 1e-16 relative in
+FP64, that the step map then carries)."""
 import numpy as np
 import pytest
 
@@ -105,6 +108,10 @@ def test_batch_mix_bitwise_equals_batch_of_one(storage):
 
 @pytest.mark.parametrize("storage", ["fp64", "fp32", "bf16"])
 def test_batch_matches_single_lattice_kernel(storage):
+    """Against the default single-lattice kernel: a batch marches each
+    lattice with the per-cell code of the kernel that lattice would run
+    alone (the pipelined march where its x extent and boundaries allow it,
+    the fused tile march otherwise)."""
     from paper_2512_01032_gb300 import pflb
     alone, mixed = _pairs(storage)
     B = pflb.Batch(mixed)
