@@ -500,6 +500,54 @@ def main_serve(args):
     return 0
 
 
+def batch_compare(dev, steps=100, warmup=5):
+    """Compact batching figure for the default line: eight serving-trace
+    lattices (square ducts with a central constriction, w = 48 .. 96, liquid
+    slug, body-force drive) advanced as one batch at BF16 storage and, beside
+    it, the same lattices at FP32 storage stepped one lattice at a time (the
+    per-lattice loop of plain serving).  Device time of `steps` steps each
+    (CUDA events on the lattices' stream), a few seconds in all."""
+    import torch
+    from paper_2512_01032_gb300 import pflb
+    stream = torch.cuda.Stream(device=dev)
+    out = {"workload": "8 serving-trace lattices (w = 48, 52, .., 96 ducts with a central "
+                       "constriction), BF16 batch vs per-lattice FP32 loop", "steps": steps}
+    for storage, batched in (("bf16", True), ("fp32", False)):
+        lats, fluid = [], 0
+        for w in (48, 52, 56, 64, 72, 80, 88, 96):
+            r = synth.constriction_request(dict(w=w, ratio=0.5, theta=120.0))
+            g, i = r["geometry"], r["init"]
+            L = pflb.Lattice(g.nx, g.ny, g.nz, solid=g.solid, wall_normal=g.normals(),
+                             theta_cells=g.theta(), stream=stream, storage=storage,
+                             **r["params"])
+            L.init_tanh(i["shape"], i["center"], i["R"], i["normal"])
+            L.set_force((r["beta0"] * r["p_crit"] / r["length"], 0.0, 0.0))
+            lats.append(L)
+            fluid += int(g.N - g.solid.sum())
+        B = pflb.Batch(lats, stream=stream) if batched else None
+        run = (lambda n: B.step(n)) if batched else (
+            lambda n: [L.step(1) for _ in range(n) for L in lats])
+        run(warmup)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        a.record(stream)
+        run(steps)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        key = "batched_bf16" if batched else "per_lattice_fp32"
+        out[key] = {"value": fluid * steps / (ms * 1e-3) / 1e6, "unit": "MLUPS",
+                    "fluid_cells": fluid, "ms_per_step": ms / steps,
+                    "kernels": sorted({KERNEL_NAMES.get(L.get_kernel()["kind"], "?")
+                                       for L in lats})}
+        if B is not None:
+            B.close()
+        for L in lats:
+            L.close()
+    out["ratio"] = out["batched_bf16"]["value"] / out["per_lattice_fp32"]["value"]
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -509,6 +557,8 @@ def main(argv=None):
     ap.add_argument("--tile", type=str, default="", help="bx,by,lz of the fused kernel")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the compact batched-vs-per-lattice figure of the default line")
     ap.add_argument("--workload", choices=["sessile", "channels", "serve"], default="sessile",
                     help="sessile: the 128^3 sessile droplet (default); channels: many "
                          "uneven channel lattices advanced as one batch; serve: a request "
@@ -652,6 +702,10 @@ def main(argv=None):
                "final_mass": float(phi_out.sum()), "final_diag_mass": last["mass"]}
         L2.close()
 
+    batch = None
+    if rank == 0 and world == 1 and not args.no_batch:
+        batch = batch_compare(dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(g, p, drop)
@@ -668,7 +722,8 @@ def main(argv=None):
                                f"workload ({CLOCK_WINDOW_S:.1f} s) just before the timed "
                                "region, and the timed region"),
                 "diag_last": {"mass": d["mass"], "dp": d["dp"], "u_max": d["u_max"],
-                              "nonfinite": d["nonfinite"]}}
+                              "nonfinite": d["nonfinite"]},
+                "batch": batch}
         print(json.dumps(line), flush=True)
     L.close()
     if world > 1:
