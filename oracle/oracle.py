@@ -74,6 +74,8 @@ def _load():
                   "orc_set_ghost", "orc_set_phi_field", "orc_get_normals"):
             getattr(lib, n).argtypes = [C.c_void_p, _d]
         lib.orc_update_ghosts_only.argtypes = [C.c_void_p]
+        lib.orc_set_solid_fraction.argtypes = [C.c_void_p, _d, _d]
+        lib.orc_set_solid_fraction.restype = C.c_int
         lib.orc_set_nthreads.argtypes = [C.c_void_p, C.c_int]
         lib.orc_set_force.argtypes = [C.c_void_p, _d]
         lib.orc_set_x_boundaries.argtypes = [C.c_void_p, C.c_int, _d, C.c_int, _d, C.c_int64]
@@ -241,7 +243,9 @@ class OracleLattice:
     """One periodic lattice advanced by the FP64 oracle."""
 
     def __init__(self, nx, ny, nz, solid=None, wall_normal=None, theta_cells=None, nthreads=1,
-                 **params):
+                 solid_frac=None, **params):
+        """solid_frac: optional solid volume fraction per cell (reading R23:
+        walls that cut fluid cells); fluid cells in [0, 1)."""
         lib = _load()
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.N = self.nx * self.ny * self.nz
@@ -264,6 +268,14 @@ class OracleLattice:
         if not self._h:
             raise MemoryError("oracle allocation failed")
         self._lib = lib
+        if solid_frac is not None:
+            fr = _f64(solid_frac).reshape(-1)
+            if fr.size != self.N:
+                raise ValueError("solid_frac must hold one value per cell")
+            self._keep = self._keep + (fr,)
+            if lib.orc_set_solid_fraction(self._h, _ptr(fr),
+                                          _ptr(nw) if nw is not None else None) != 0:
+                raise ValueError("solid_frac of a fluid cell outside [0, 1)")
 
     def __del__(self):
         h = getattr(self, "_h", None)

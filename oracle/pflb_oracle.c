@@ -61,6 +61,22 @@
  *       linearly over a number of steps from those in effect (the rest
  *       state P = 0, u = 0 when the boundaries were off).
  *
+ *   R23 Sub-voxel walls (Sec. II B's volume-weighted sampling, the offset
+ *       walls of Sec. IV A), a light form of the volumetric overlap
+ *       weighting: each cell carries a solid volume fraction s (1 on solid
+ *       voxels, 0 on plain fluid cells, 0 < s < 1 on fluid cells that the
+ *       wall cuts).  Cut cells are fluid cells in every other respect (they
+ *       hold populations; bounce-back and the free-slip band act only at
+ *       links into solid voxels).  A wall node is a fluid cell with a
+ *       neighbour of s > 0, and it keeps one ghost phi_{s,i} per such link.
+ *       Its sample phi_smpl averages phi over a parallelepiped one spacing
+ *       thick standing on the wall: (1 - s_x) phi(x) + s_x phi(x + c_n),
+ *       with c_n the axis direction nearest the wall normal (phi(x) in
+ *       place of phi(x + c_n) when that cell is solid).  In the CD stencils
+ *       the neighbour y = x + c_i contributes s_y phi_{s,i} + (1 - s_y)
+ *       phi(y): the ghost for the part of y inside the wall, y's own phi for
+ *       the rest.  With every s in {0, 1} this is R6 exactly.
+ *
  * Parity unpinned by the paper (pinned only oracle <-> GPU): the sub-step
  * order (R3), the ghost lag (R11), the blend side (R12) and the free-slip
  * band rule (R14).
@@ -109,6 +125,8 @@ typedef struct {
     int64_t N;
     orc_params p;
     uint8_t *solid;   /* [N] */
+    double *frac;     /* [N] solid volume fraction (R23), NULL: s = solid[] */
+    int8_t *cn;       /* [N] axis direction nearest the wall normal (R23) */
     double *nw;       /* [N*3] wall normal into the fluid (wall nodes) */
     double *cth, *sth;/* [N] cos/sin of the input contact angle */
     double *h, *g;    /* [N*Q] current populations (post-stream) */
@@ -144,10 +162,15 @@ static inline int64_t shift(const orc_lattice *L, int64_t cell, int dx, int dy, 
     return x + (int64_t)L->nx * (y + (int64_t)L->ny * z);
 }
 
+/* Solid volume fraction of a cell (R23). */
+static inline double sfrac(const orc_lattice *L, int64_t cell) {
+    return L->solid[cell] ? 1.0 : (L->frac ? L->frac[cell] : 0.0);
+}
+
 static inline int is_wall_node(const orc_lattice *L, int64_t cell) {
     if (L->solid[cell]) return 0;
     for (int i = 1; i < Q; ++i)
-        if (L->solid[nbr(L, cell, i)]) return 1;
+        if (sfrac(L, nbr(L, cell, i)) > 0.0) return 1;
     return 0;
 }
 
@@ -296,11 +319,12 @@ void orc_filtered_collide(const double g[Q], const double K[Q], const double E[Q
 
 /* Wettability ghosts of Sec. II B (Eqs. 12-15) for one wall node:
  * w = n_w rotated by pi - theta about n_w x grad (R9), then for every
- * solid link i, phi_{s,i} = (1 + tanh((x - x0 + d_i)/(W/2)))/2 with
+ * ghost link i, phi_{s,i} = (1 + tanh((x - x0 + d_i)/(W/2)))/2 with
  * x - x0 = (W/2) artanh(2 phi_smpl - 1) and d_i = w . c_i.
- * solid_links: bit i set when x + c_i is solid.  Writes out[i] for those. */
+ * links: bit i set when x + c_i is solid (or cut, R23).  Writes out[i] for
+ * those. */
 void orc_ghost_values(const orc_params *p, double phi_smpl, const double nw[3], double cth,
-                      double sth, const double grad[3], uint32_t solid_links, double out[Q]) {
+                      double sth, const double grad[3], uint32_t links, double out[Q]) {
     double gn = grad[0] * nw[0] + grad[1] * nw[1] + grad[2] * nw[2];
     double gt[3] = {grad[0] - gn * nw[0], grad[1] - gn * nw[1], grad[2] - gn * nw[2]};
     double gtn = sqrt(gt[0] * gt[0] + gt[1] * gt[1] + gt[2] * gt[2]);
@@ -318,7 +342,7 @@ void orc_ghost_values(const orc_params *p, double phi_smpl, const double nw[3], 
     if (s < -lim) s = -lim;
     double xx0 = 0.5 * p->W * atanh(s); /* Eq. 14 */
     for (int i = 1; i < Q; ++i) {
-        if (!(solid_links >> i & 1u)) continue;
+        if (!(links >> i & 1u)) continue;
         double di = w[0] * CX[i] + w[1] * CY[i] + w[2] * CZ[i];
         out[i] = 0.5 * (1.0 + tanh((xx0 + di) / (0.5 * p->W))); /* Eq. 15 */
     }
@@ -401,10 +425,50 @@ orc_lattice *orc_create(int nx, int ny, int nz, const uint8_t *solid, const doub
 
 void orc_destroy(orc_lattice *L) {
     if (!L) return;
-    free(L->solid); free(L->nw); free(L->cth); free(L->sth);
+    free(L->solid); free(L->frac); free(L->cn); free(L->nw); free(L->cth); free(L->sth);
     free(L->h); free(L->g); free(L->h2); free(L->g2);
     free(L->phi); free(L->ghost); free(L->ghost_old); free(L->bstate);
     free(L);
+}
+
+/* Solid volume fractions of the cells (R23), before orc_init_phi: frac[c]
+ * in [0, 1) on fluid cells (solid cells count 1 whatever is given).  Wall
+ * normals of the wall nodes this adds come from wall_normal, else from the
+ * fraction-weighted mask -sum_i w_i c_i s(x + c_i).  Returns 0, or -1 for a
+ * fraction out of range. */
+int orc_set_solid_fraction(orc_lattice *L, const double *frac, const double *wall_normal) {
+    int64_t N = L->N;
+    if (N <= 0) return -1;
+    for (int64_t c = 0; c < N; ++c)
+        if (!L->solid[c] && !(frac[c] >= 0.0 && frac[c] < 1.0)) return -1;
+    if (!L->frac) L->frac = (double *)malloc(N * sizeof(double));
+    if (!L->cn) L->cn = (int8_t *)calloc((size_t)N, 1);
+    for (int64_t c = 0; c < N; ++c) L->frac[c] = L->solid[c] ? 1.0 : frac[c];
+    for (int64_t c = 0; c < N; ++c) {
+        L->cn[c] = 0;
+        if (!is_wall_node(L, c)) continue;
+        double *n = L->nw + 3 * c;
+        if (wall_normal) {
+            for (int a = 0; a < 3; ++a) n[a] = wall_normal[3 * c + a];
+        } else {
+            n[0] = n[1] = n[2] = 0.0;
+            for (int i = 1; i < Q; ++i) {
+                double s = sfrac(L, nbr(L, c, i));
+                n[0] -= WQ[i] * CX[i] * s;
+                n[1] -= WQ[i] * CY[i] * s;
+                n[2] -= WQ[i] * CZ[i] * s;
+            }
+            double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+            for (int a = 0; a < 3; ++a) n[a] = nn > 0 ? n[a] / nn : 0.0;
+        }
+        /* c_n: the axis direction (1..6) with the largest c . n_w */
+        double best = 0.0;
+        for (int i = 1; i <= 6; ++i) {
+            double d = CX[i] * n[0] + CY[i] * n[1] + CZ[i] * n[2];
+            if (d > best) { best = d; L->cn[c] = (int8_t)i; }
+        }
+    }
+    return 0;
 }
 
 /* Neighbour values for the CD stencil at fluid cell x: phi of fluid
@@ -413,15 +477,31 @@ static void stencil_values(const orc_lattice *L, int64_t x, const double *ghost,
     val[0] = L->phi[x];
     for (int i = 1; i < Q; ++i) {
         int64_t y = nbr(L, x, i);
-        val[i] = L->solid[y] ? ghost[x * Q + i] : L->phi[y];
+        double s = sfrac(L, y);
+        if (s >= 1.0)
+            val[i] = ghost[x * Q + i];
+        else if (s > 0.0) /* R23: ghost for the part of y inside the wall */
+            val[i] = s * ghost[x * Q + i] + (1.0 - s) * L->phi[y];
+        else
+            val[i] = L->phi[y];
     }
 }
 
-static uint32_t solid_links(const orc_lattice *L, int64_t x) {
+/* Links of x that carry a ghost: bit i set when x + c_i is solid or cut. */
+static uint32_t ghost_links(const orc_lattice *L, int64_t x) {
     uint32_t m = 0;
     for (int i = 1; i < Q; ++i)
-        if (L->solid[nbr(L, x, i)]) m |= 1u << i;
+        if (sfrac(L, nbr(L, x, i)) > 0.0) m |= 1u << i;
     return m;
+}
+
+/* phi_smpl of wall node x (R6; R23 with a cut cell). */
+static double phi_sample(const orc_lattice *L, int64_t x) {
+    double sx = L->frac ? L->frac[x] : 0.0;
+    if (sx <= 0.0 || L->cn[x] <= 0) return L->phi[x];
+    int64_t y = nbr(L, x, L->cn[x]);
+    double py = L->solid[y] ? L->phi[x] : L->phi[y];
+    return (1.0 - sx) * L->phi[x] + sx * py;
 }
 
 /* Equilibrium initialisation (reading R16). */
@@ -540,12 +620,13 @@ static void update_ghosts(orc_lattice *L, double *ghost_out) {
 #pragma omp parallel for num_threads(L->p.nthreads) schedule(static)
     for (int64_t c = 0; c < N; ++c) {
         if (L->solid[c] || bc_side(L, c) >= 0) continue;  /* R22: no ghost update */
-        uint32_t m = solid_links(L, c);
+        uint32_t m = ghost_links(L, c);
         if (!m) continue;
         double val[Q], grad[3], lap, fresh[Q];
         stencil_values(L, c, L->ghost_old, val);
         orc_cd_stencil(val, grad, &lap);
-        orc_ghost_values(p, L->phi[c], L->nw + 3 * c, L->cth[c], L->sth[c], grad, m, fresh);
+        orc_ghost_values(p, phi_sample(L, c), L->nw + 3 * c, L->cth[c], L->sth[c], grad, m,
+                         fresh);
         for (int i = 1; i < Q; ++i)
             if (m >> i & 1u)
                 ghost_out[c * Q + i] = p->blend * L->ghost_old[c * Q + i] + (1.0 - p->blend) * fresh[i];
