@@ -165,8 +165,8 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def workload():
-    return synth.sessile_sphere(N_BOX, THETA)
+def workload(n=N_BOX):
+    return synth.sessile_sphere(n, THETA)
 
 
 def config_of(g, fluid, kind=3):
@@ -563,6 +563,9 @@ def main(argv=None):
                     help="sessile: the 128^3 sessile droplet (default); channels: many "
                          "uneven channel lattices advanced as one batch; serve: a request "
                          "trace through the batching server and the plain server")
+    ap.add_argument("--size", type=int, default=N_BOX,
+                    help="sessile: lattice edge (the headline workload is 128; smaller "
+                         "sizes are for profiler captures)")
     ap.add_argument("--storage", choices=["fp32", "fp16", "bf16", "fp64"], default="bf16",
                     help="population storage of the channels workload")
     ap.add_argument("--count", type=int, default=64,
@@ -596,7 +599,7 @@ def main(argv=None):
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
 
-    g, p, drop = workload()
+    g, p, drop = workload(args.size)
     fluid = int(g.N - g.solid.sum())
     L = pflb.Lattice(g.nx, g.ny, g.nz, solid=g.solid, wall_normal=g.normals(),
                      theta_cells=g.theta(), stream=stream, storage="fp32", **p)

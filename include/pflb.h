@@ -51,12 +51,13 @@ typedef enum {
 } pflb_status;
 
 /* Population storage.  The collision computes in FP64 for FP64 storage and
- * in FP32 otherwise.  The 16-bit formats store each population divided by
- * its lattice weight, h_i / w_i and g_i / w_i (at rest these are phi and
- * P/T, so every stored value has the scale of a macroscopic field), with
- * the rounding of a cell's moving h compensated in its rest population so
- * that total phi does not drift (bytes per cell and step: 305 at FP32, 157
- * at FP16/BF16, 609 at FP64). */
+ * in FP32 otherwise.  FP16 stores each population divided by its lattice
+ * weight, h_i / w_i and g_i / w_i (at rest these are phi and P/T, so every
+ * stored value has the scale of a macroscopic field, clear of FP16's
+ * subnormals); BF16, whose exponent range is FP32's, stores the value
+ * itself.  Both 16-bit formats compensate the rounding of a cell's moving h
+ * in its rest population so that total phi does not drift (bytes per cell
+ * and step: 305 at FP32, 157 at FP16/BF16, 609 at FP64). */
 enum { PFLB_STORAGE_FP64 = 0, PFLB_STORAGE_FP32 = 1, PFLB_STORAGE_FP16 = 2,
        PFLB_STORAGE_BF16 = 3 };
 

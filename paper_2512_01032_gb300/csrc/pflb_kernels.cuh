@@ -279,9 +279,10 @@ __device__ __forceinline__ void store_cell(const Args<S, R> &a, int c, uint32_t 
                                            const Nbr &nb, R h[Q], R g[Q], const R val[Q],
                                            bool in_band) {
   const Model<R> &m = a.m;
-  S he[Q], h_lo;
+  S he[Q], h_lo, ge[Q];
   enc_h_cell<S, R>(h, he, &h_lo);
-  if constexpr (Codec<S>::scaled) a.hout[Q][c] = h_lo;  // rest population stays
+  enc_g_cell<S, R>(g, ge);
+  if constexpr (Codec<S>::narrow) a.hout[Q][c] = h_lo;  // rest population stays
 
   if (lm == 0) {  // bulk cell: plain streaming of both sets
 #pragma unroll
@@ -289,9 +290,9 @@ __device__ __forceinline__ void store_cell(const Args<S, R> &a, int c, uint32_t 
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       if (!ODD)
-        st_g<S, R>(a.g[opp_of(i)] + c, i, g[i]);
+        a.g[opp_of(i)][c] = ge[i];
       else
-        st_g<S, R>(a.g[i] + (c + nb.off(i)), i, g[i]);
+        a.g[i][c + nb.off(i)] = ge[i];
     }
     return;
   }
@@ -322,11 +323,11 @@ __device__ __forceinline__ void store_cell(const Args<S, R> &a, int c, uint32_t 
           }
         }
       }
-      st_g<S, R>(a.wp_wr + ((ddir - 1) * a.nw + drec), i, g[i]);
+      a.wp_wr[(ddir - 1) * a.nw + drec] = ge[i];
     } else if (!ODD) {
-      st_g<S, R>(a.g[opp_of(i)] + c, i, g[i]);
+      a.g[opp_of(i)][c] = ge[i];
     } else {
-      st_g<S, R>(a.g[i] + (c + nb.off(i)), i, g[i]);
+      a.g[i][c + nb.off(i)] = ge[i];
     }
   }
 }
@@ -768,7 +769,7 @@ __global__ void k_init(const __grid_constant__ Args<S, R> a, const double *phi0,
   // g = g_eq(P0, u = 0) = w_i P0/T - K_i/2 with K_i = w_i (mu c_i.grad + c_i.F)/T.
   S he[Q], h_lo;
   enc_h_cell<S, R>(h, he, &h_lo);
-  if constexpr (Codec<S>::scaled) h0base[Q * N + c] = h_lo;
+  if constexpr (Codec<S>::narrow) h0base[Q * N + c] = h_lo;
   const R mu = m.mu_a * phi * (phi - R(1)) * (phi - R(0.5)) - m.mu_b * lap;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {

@@ -119,27 +119,32 @@ template <class S> __device__ __forceinline__ S ld_ro(const S *p) { return __ldg
 
 // ------------------------------------------------------------ codecs
 // Populations are stored in S and computed in R.  FP64 and FP32 store the
-// value itself.  The 16-bit formats store each population divided by the
-// lattice weight of its direction (values of order phi in [0, 1] for h and
-// of order P/T for g, the rest value of g being w_i P / T), and the h set is
-// made mass-conserving: the rest population never moves, so each cell adds
-// the rounding error of the 18 moving h populations it writes to its own
-// rest population, which is kept as a pair of 16-bit values (a high part and
-// the remainder, about 22 significant bits).  The sum of all stored h then
-// equals the sum of the computed ones up to FP32 rounding, so total phi does
-// not drift.  i is a compile-time constant at every call, so the scale
-// folds into one multiply.
+// value itself.  The two 16-bit formats ("narrow") make the h set
+// mass-conserving: the rest population never moves, so each cell adds the
+// rounding error of the 18 moving h populations it writes to its own rest
+// population, which is kept as a pair of 16-bit values (a high part and the
+// remainder, about 22 significant bits at FP16, 16 at BF16).  The sum of all
+// stored h then equals the sum of the computed ones up to FP32 rounding, so
+// total phi does not drift.
+// FP16 ("scaled") stores each population divided by the lattice weight of
+// its direction: values of order phi in [0, 1] for h and of order P/T for g
+// (the rest value of g being w_i P / T), which keeps them above FP16's
+// normal range limit of 6.1e-5 down to phi or P/T of that size.  BF16 has
+// FP32's exponent range, so its relative spacing is the same at any
+// magnitude and it stores the value itself: dividing by w_i would change no
+// rounding, only add a multiply to every encode and decode.  i is a
+// compile-time constant at every call, so the scale folds into one multiply.
 template <class S> struct Codec {
   template <class R> static __device__ __forceinline__ R to(S v) { return (R)v; }
   template <class R> static __device__ __forceinline__ S from(R v) { return (S)v; }
-  static constexpr bool scaled = false;
+  static constexpr bool scaled = false, narrow = false;
 };
 template <> struct Codec<__half> {
   template <class R> static __device__ __forceinline__ R to(__half v) { return (R)__half2float(v); }
   template <class R> static __device__ __forceinline__ __half from(R v) {
     return __float2half_rn((float)v);
   }
-  static constexpr bool scaled = true;
+  static constexpr bool scaled = true, narrow = true;
 };
 template <> struct Codec<__nv_bfloat16> {
   template <class R> static __device__ __forceinline__ R to(__nv_bfloat16 v) {
@@ -148,12 +153,12 @@ template <> struct Codec<__nv_bfloat16> {
   template <class R> static __device__ __forceinline__ __nv_bfloat16 from(R v) {
     return __float2bfloat16_rn((float)v);
   }
-  static constexpr bool scaled = true;
+  static constexpr bool scaled = false, narrow = true;
 };
 
 // Number of h slots per cell: 19, plus the remainder of the rest population
 // for the 16-bit formats (slot 19).
-template <class S> __host__ __device__ constexpr int h_slots() { return Codec<S>::scaled ? Q + 1 : Q; }
+template <class S> __host__ __device__ constexpr int h_slots() { return Codec<S>::narrow ? Q + 1 : Q; }
 
 __host__ __device__ constexpr double inv_w_of(int i) { return i == 0 ? 3.0 : (i <= 6 ? 18.0 : 36.0); }
 
@@ -162,14 +167,39 @@ __device__ __forceinline__ R dec_pop(S v, int i) {
   if constexpr (Codec<S>::scaled)
     return Codec<S>::template to<R>(v) * R(w_of(i));
   else
-    return (R)v;
+    return Codec<S>::template to<R>(v);
 }
 template <class S, class R>
 __device__ __forceinline__ S enc_pop(R v, int i) {
   if constexpr (Codec<S>::scaled)
     return Codec<S>::template from<R>(v * R(inv_w_of(i)));
   else
-    return (S)v;
+    return Codec<S>::template from<R>(v);
+}
+// Two populations encoded together: the 16-bit formats round both with one
+// packed conversion (round to nearest even, as the single conversions).
+template <class S, class R>
+__device__ __forceinline__ void enc_pop2(R a, int i, R b, int j, S &ea, S &eb) {
+  if constexpr (Codec<S>::narrow && sizeof(S) == 2 && !Codec<S>::scaled) {
+    const __nv_bfloat162 p = __floats2bfloat162_rn((float)a, (float)b);
+    ea = __low2bfloat16(p);
+    eb = __high2bfloat16(p);
+  } else if constexpr (Codec<S>::narrow) {
+    const __half2 p =
+        __floats2half2_rn((float)(a * R(inv_w_of(i))), (float)(b * R(inv_w_of(j))));
+    ea = __low2half(p);
+    eb = __high2half(p);
+  } else {
+    ea = (S)a;
+    eb = (S)b;
+  }
+}
+// The 19 g of a cell encoded for storage (pairs share a conversion).
+template <class S, class R>
+__device__ __forceinline__ void enc_g_cell(const R g[Q], S ge[Q]) {
+  ge[0] = enc_pop<S, R>(g[0], 0);
+#pragma unroll
+  for (int i = 1; i < Q; i += 2) enc_pop2<S, R>(g[i], i, g[i + 1], i + 1, ge[i], ge[i + 1]);
 }
 template <class S, class R> __device__ __forceinline__ R ld_g(const S *p, int i) {
   return dec_pop<S, R>(*p, i);
@@ -183,19 +213,19 @@ template <class S, class R>
 __device__ __forceinline__ void ld_h_cell(const S *const *hb, int c, R h[Q]) {
 #pragma unroll
   for (int i = 0; i < Q; ++i) h[i] = dec_pop<S, R>(ld_ro<S>(hb[i] + c), i);
-  if constexpr (Codec<S>::scaled) h[0] += dec_pop<S, R>(ld_ro<S>(hb[Q] + c), 0);
+  if constexpr (Codec<S>::narrow) h[0] += dec_pop<S, R>(ld_ro<S>(hb[Q] + c), 0);
 }
 // Encodes the 19 post-collision h of a cell; for the 16-bit formats the
 // rounding error of directions 1..18 is moved into the rest population,
 // whose high part goes to enc[0] and remainder to *rest_lo.
 template <class S, class R>
 __device__ __forceinline__ void enc_h_cell(const R h[Q], S enc[Q], S *rest_lo) {
-  if constexpr (Codec<S>::scaled) {
+  if constexpr (Codec<S>::narrow) {
     R err = R(0);
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      enc[i] = enc_pop<S, R>(h[i], i);
-      err += dec_pop<S, R>(enc[i], i) - h[i];
+    for (int i = 1; i < Q; i += 2) {
+      enc_pop2<S, R>(h[i], i, h[i + 1], i + 1, enc[i], enc[i + 1]);
+      err += (dec_pop<S, R>(enc[i], i) - h[i]) + (dec_pop<S, R>(enc[i + 1], i + 1) - h[i + 1]);
     }
     const R h0 = h[0] - err;
     enc[0] = enc_pop<S, R>(h0, 0);

@@ -29,7 +29,7 @@
 // reads wall records, ghosts and wall populations) are left to k_wall,
 // launched after this kernel: k_pipe writes the phi of the cells those
 // nodes read to the phi field.  16-bit storage stages the stored
-// (weight-scaled) values and decodes them when they are read.
+// values and decodes them when they are read.
 //
 // Shared memory per block (FP32): h 2 planes x 19 x 6 rows x 40, g 19 x 4
 // rows x 40, flags 4 planes x 6 x 10 words, phi 4 planes x 34 x 6: 54 KB,
