@@ -76,9 +76,12 @@ enum { PFLB_FIELD_PHI = 0, PFLB_FIELD_RHO = 1, PFLB_FIELD_P = 2,
  *   PFLB_KERNEL_TWOPASS: a phi pass followed by a per-cell pass;
  *   PFLB_KERNEL_FUSED_TMA: the fused pass with h staged through shared
  *     memory by TMA (FP32 storage, nx a multiple of 4 and nx >= 64;
- *     otherwise PFLB_KERNEL_FUSED runs). */
+ *     otherwise PFLB_KERNEL_FUSED runs);
+ *   PFLB_KERNEL_PIPE2: PFLB_KERNEL_PIPE with two neighbouring cells per
+ *     thread and their arithmetic in packed FP32 (two results per
+ *     instruction) at FP32 storage; at other storage PFLB_KERNEL_PIPE runs. */
 enum { PFLB_KERNEL_FUSED = 0, PFLB_KERNEL_TWOPASS = 1, PFLB_KERNEL_FUSED_TMA = 2,
-       PFLB_KERNEL_PIPE = 3 };
+       PFLB_KERNEL_PIPE = 3, PFLB_KERNEL_PIPE2 = 4 };
 
 /* Geometry, read during pflb_create only.
  *   solid       : host, nx*ny*nz bytes, nonzero = solid voxel.
@@ -88,12 +91,26 @@ enum { PFLB_KERNEL_FUSED = 0, PFLB_KERNEL_TWOPASS = 1, PFLB_KERNEL_FUSED_TMA = 2
  *                 normalised -sum_i w_i c_i [x + c_i solid].
  *   theta_deg   : host, one input contact angle per cell (degrees, measured
  *                 inside the phi = 1 phase), read at wall nodes; NULL = use
- *                 params.theta_deg everywhere. */
+ *                 params.theta_deg everywhere.
+ *   solid_frac  : host, one double per cell, or NULL (voxel walls).  Walls
+ *                 that cut fluid cells (Sec. II B's volume-weighted sampling;
+ *                 the offset walls of Sec. IV A): the solid volume fraction s
+ *                 of each fluid cell, in [0, 1) (values on solid voxels are
+ *                 ignored; a fluid value outside [0, 1) is PFLB_ERR_ARG).  A
+ *                 cut cell (s > 0) stays a fluid cell (bounce-back acts only
+ *                 at links into solid voxels); a fluid cell next to one is a
+ *                 wall node that keeps a ghost for that link, and its CD
+ *                 stencils take s_y ghost + (1 - s_y) phi(y) for the cut
+ *                 neighbour y; a cut wall node samples phi as
+ *                 (1 - s) phi(x) + s phi(x + c_n), c_n the axis direction
+ *                 nearest its wall normal.  Wall normals are read at these
+ *                 wall nodes too (NULL: the fraction-weighted mask). */
 typedef struct {
   int nx, ny, nz;
   const uint8_t *solid;
   const double *wall_normal;
   const double *theta_deg;
+  const double *solid_frac;
 } pflb_geometry;
 
 /* Model parameters (lattice units).

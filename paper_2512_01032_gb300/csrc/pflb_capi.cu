@@ -210,30 +210,77 @@ std::vector<uint32_t> link_masks(const pflb_geometry *g) {
   return mask;
 }
 
+// Solid volume fraction of cell c (sub-voxel walls): 1 on solid voxels.
+inline double cell_frac(const pflb_geometry *g, long long c) {
+  return g->solid[c] ? 1.0 : (g->solid_frac ? g->solid_frac[c] : 0.0);
+}
+
+// Cut-link bits (bit i set when x + c_i is a fluid cell with solid fraction
+// > 0) of every fluid cell; all zero without fractions.
+std::vector<uint32_t> cut_masks(const pflb_geometry *g) {
+  const int nx = g->nx, ny = g->ny, nz = g->nz;
+  const long long N = (long long)nx * ny * nz;
+  std::vector<uint32_t> mask((size_t)N, 0);
+  if (!g->solid_frac) return mask;
+  parallel_z(nz, N, [&](int z0, int z1) {
+    for (int z = z0; z < z1; ++z)
+      for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+          const long long c = x + (long long)nx * (y + (long long)ny * z);
+          if (g->solid[c]) continue;
+          uint32_t m = 0;
+          for (int i = 1; i < pflb::Q; ++i) {
+            const long long nb = wrap(x + pflb::cx_of(i), nx) +
+                                 (long long)nx * (wrap(y + pflb::cy_of(i), ny) +
+                                                  (long long)ny * wrap(z + pflb::cz_of(i), nz));
+            if (!g->solid[nb] && g->solid_frac[nb] > 0.0) m |= 1u << i;
+          }
+          mask[(size_t)c] = m;
+        }
+  });
+  return mask;
+}
+
+// True if every fluid cell's solid fraction is in [0, 1).
+bool fractions_ok(const pflb_geometry *g) {
+  if (!g->solid_frac) return true;
+  const long long N = (long long)g->nx * g->ny * g->nz;
+  for (long long c = 0; c < N; ++c)
+    if (!g->solid[c] && !(g->solid_frac[c] >= 0.0 && g->solid_frac[c] < 1.0)) return false;
+  return true;
+}
+
 struct HostGeom {
   std::vector<uint8_t> flags;
   std::vector<int> widx;
   std::vector<int> wcell;    // [nw] cell of each wall node
   std::vector<uint32_t> wmask;
   std::vector<double> wgeo;  // [5][nw]
+  std::vector<uint32_t> wcut;   // [nw] cut links | c_n << 24; empty without cut cells
+  std::vector<double> sfrac;    // [N]; empty without cut cells
 };
 
 // Flags, wall list (cell order), solid-link masks, normals and angles.
 void build_geometry(const pflb_geometry *g, const pflb_params *p, HostGeom &hg) {
   const long long N = (long long)g->nx * g->ny * g->nz;
   const std::vector<uint32_t> all = link_masks(g);
+  const std::vector<uint32_t> cut = cut_masks(g);
+  bool has_cut = false;
+  if (g->solid_frac)
+    for (long long c = 0; c < N && !has_cut; ++c) has_cut = !g->solid[c] && g->solid_frac[c] > 0;
   hg.flags.assign(N, 0);
   hg.widx.assign(N, -1);
-  std::vector<uint32_t> masks;
+  std::vector<uint32_t> masks, cuts;
   std::vector<long long> cells;
   for (long long c = 0; c < N; ++c) {
     if (g->solid[c]) {
       hg.flags[c] = pflb::F_SOLID;
-    } else if (all[c]) {
+    } else if (all[c] || cut[c]) {
       hg.flags[c] = pflb::F_WALL;
       hg.widx[c] = (int)cells.size();
       cells.push_back(c);
       masks.push_back(all[c]);
+      cuts.push_back(cut[c]);
     }
   }
   const size_t nw = cells.size();
@@ -255,18 +302,38 @@ void build_geometry(const pflb_geometry *g, const pflb_params *p, HostGeom &hg) 
   for (size_t k = 0; k < nw; ++k) {
     const long long c = cells[k];
     double n[3] = {0, 0, 0};
+    const int x = (int)(c % g->nx), y = (int)((c / g->nx) % g->ny);
+    const int z = (int)(c / ((long long)g->nx * g->ny));
+    auto nbr = [&](int i) {
+      return wrap(x + pflb::cx_of(i), g->nx) +
+             (long long)g->nx * (wrap(y + pflb::cy_of(i), g->ny) +
+                                 (long long)g->ny * wrap(z + pflb::cz_of(i), g->nz));
+    };
     if (g->wall_normal) {
       for (int a = 0; a < 3; ++a) n[a] = g->wall_normal[3 * c + a];
     } else {
-      for (int i = 1; i < pflb::Q; ++i)
-        if ((masks[k] >> i) & 1u) {
-          n[0] -= pflb::w_of(i) * pflb::cx_of(i);
-          n[1] -= pflb::w_of(i) * pflb::cy_of(i);
-          n[2] -= pflb::w_of(i) * pflb::cz_of(i);
-        }
+      // -sum_i w_i c_i s(x + c_i), s = 1 on solid voxels
+      for (int i = 1; i < pflb::Q; ++i) {
+        const double sf = ((masks[k] >> i) & 1u) ? 1.0 : (((cuts[k] >> i) & 1u) ? cell_frac(g, nbr(i)) : 0.0);
+        n[0] -= pflb::w_of(i) * pflb::cx_of(i) * sf;
+        n[1] -= pflb::w_of(i) * pflb::cy_of(i) * sf;
+        n[2] -= pflb::w_of(i) * pflb::cz_of(i) * sf;
+      }
       const double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
       if (nn > 0)
         for (int a = 0; a < 3; ++a) n[a] /= nn;
+    }
+    if (has_cut) {
+      // c_n: the axis direction (1..6) with the largest c . n_w (first on
+      // ties); 0 when the node is not cut or that neighbour is solid
+      int cn = 0;
+      double best = 0.0;
+      for (int i = 1; i <= 6; ++i) {
+        const double d = pflb::cx_of(i) * n[0] + pflb::cy_of(i) * n[1] + pflb::cz_of(i) * n[2];
+        if (d > best) { best = d; cn = i; }
+      }
+      if (!(cell_frac(g, c) > 0.0) || g->solid[nbr(cn)]) cn = 0;
+      hg.wcut.push_back(cuts[k] | ((uint32_t)cn << 24));
     }
     const double th = (g->theta_deg ? g->theta_deg[c] : p->theta_deg) * (3.14159265358979323846 / 180.0);
     hg.wgeo[0 * nw + k] = n[0];
@@ -274,6 +341,10 @@ void build_geometry(const pflb_geometry *g, const pflb_params *p, HostGeom &hg) 
     hg.wgeo[2 * nw + k] = n[2];
     hg.wgeo[3 * nw + k] = std::cos(th);
     hg.wgeo[4 * nw + k] = std::sin(th);
+  }
+  if (has_cut) {
+    hg.sfrac.resize((size_t)N);
+    for (long long c = 0; c < N; ++c) hg.sfrac[(size_t)c] = cell_frac(g, c);
   }
 }
 
@@ -288,7 +359,7 @@ cudaError_t dev_alloc(Lattice *L, T **ptr, size_t count) {
 void free_all(Lattice *L) {
   void *ptrs[] = {L->h[0], L->h[1], L->g, L->wp[0], L->wp[1], L->flags, L->widx, L->wmask,
                   L->wgeo, L->ghost, L->phi, L->diag, L->out, L->phi0, L->err, L->bcm,
-                  L->wcell};
+                  L->wcell, L->wcut, L->sfrac};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (L->aux) cudaStreamDestroy(L->aux);
@@ -299,12 +370,13 @@ void free_all(Lattice *L) {
   L->ev_init = nullptr;
 }
 
-int64_t bytes_for(long long N, long long nw, int storage) {
+int64_t bytes_for(long long N, long long nw, int storage, bool has_cut = false) {
   const int64_t e = (int64_t)storage_bytes(storage);
   const int64_t r = (int64_t)compute_bytes(storage);
   const int64_t flag_bytes = (N + 3) & ~(int64_t)3;  // whole 4-byte words
   return (2 * (int64_t)h_slots_of(storage) + 19) * N * e + 2 * 18 * nw * e + flag_bytes +
-         N * 4 + nw * 8 + 5 * nw * r + 18 * nw * r + N * r + 96 * 8 + 4;
+         N * 4 + nw * 8 + 5 * nw * r + 18 * nw * r + N * r + 96 * 8 + 4 +
+         (has_cut ? nw * 4 + N * r : 0);
 }
 
 // TMA descriptors of the two h buffers (4-D: x, y, z, direction; box
@@ -394,6 +466,7 @@ pflb_status pflb_create(const pflb_geometry *geom, const pflb_params *params, vo
     return fail(PFLB_ERR_ARG, "lattice too large (nx*ny*nz must be below 2^31)");
   pflb_status s = check_params(params);
   if (s != PFLB_OK) return s;
+  if (!fractions_ok(geom)) return fail(PFLB_ERR_ARG, "solid_frac of a fluid cell outside [0, 1)");
 
   pflb_lattice *L = new (std::nothrow) pflb_lattice();
   if (!L) return fail(PFLB_ERR_OOM, "host allocation failed");
@@ -432,6 +505,10 @@ pflb_status pflb_create(const pflb_geometry *geom, const pflb_params *params, vo
   A((void **)&L->wmask, nw * sizeof(uint32_t));
   A((void **)&L->wcell, nw * sizeof(int));
   A(&L->wgeo, 5 * nw * Rb);
+  if (!hg.sfrac.empty()) {
+    A((void **)&L->wcut, nw * sizeof(uint32_t));
+    A(&L->sfrac, N * Rb);
+  }
   A(&L->ghost, 18 * nw * Rb);
   A(&L->phi, N * Rb);
   A((void **)&L->diag, 96 * sizeof(double));
@@ -467,6 +544,19 @@ pflb_status pflb_create(const pflb_geometry *geom, const pflb_params *params, vo
     e = cudaMemcpyAsync(L->wcell, hg.wcell.data(), nw * sizeof(int), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && nw)
     e = cudaMemcpyAsync(L->wgeo, wgeo_src, 5 * nw * Rb, cudaMemcpyHostToDevice, st);
+  std::vector<float> sfrac_f;
+  if (!hg.sfrac.empty()) {
+    const void *sfrac_src = hg.sfrac.data();
+    if (!is_fp64(L)) {
+      sfrac_f.assign(hg.sfrac.begin(), hg.sfrac.end());
+      sfrac_src = sfrac_f.data();
+    }
+    if (e == cudaSuccess && nw)
+      e = cudaMemcpyAsync(L->wcut, hg.wcut.data(), nw * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                          st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(L->sfrac, sfrac_src, N * Rb, cudaMemcpyHostToDevice, st);
+  }
   void *zero_bufs[] = {L->h[0], L->h[1], L->g, L->wp[0], L->wp[1], L->ghost, L->phi, L->err};
   size_t zero_len[] = {HS * N * E, HS * N * E, 19 * N * E, 18 * nw * E, 18 * nw * E,
                        18 * nw * Rb, N * Rb, sizeof(int)};
@@ -578,7 +668,7 @@ pflb_status pflb_set_kernel(pflb_lattice *L, int kind, int bx, int by, int lz) {
   pflb_status s = check_lattice(L);
   if (s != PFLB_OK) return s;
   if (kind != PFLB_KERNEL_FUSED && kind != PFLB_KERNEL_TWOPASS && kind != PFLB_KERNEL_FUSED_TMA &&
-      kind != PFLB_KERNEL_PIPE)
+      kind != PFLB_KERNEL_PIPE && kind != PFLB_KERNEL_PIPE2)
     return fail(PFLB_ERR_ARG, "unknown kernel");
   if (lz < -1) return fail(PFLB_ERR_ARG, "lz must be > 0, 0 (keep) or -1 (automatic)");
   const int nbx = bx > 0 ? bx : L->bx, nby = by > 0 ? by : L->by;
@@ -654,10 +744,14 @@ pflb_status pflb_get_kernel(const pflb_lattice *L, int out[4]) {
   if (!out) return fail(PFLB_ERR_ARG, "null output");
   const bool tma = L->kernel == PFLB_KERNEL_FUSED_TMA && L->p.storage == PFLB_STORAGE_FP32 &&
                    L->tma_ok && !L->bc_on;
-  const bool pipe = pflb::pipe_kernel_runs(*L);
+  const bool pipe2 = pflb::pipe2_kernel_runs(*L);
+  const bool pipe = pipe2 || pflb::pipe_kernel_runs(*L);
   // the kind that runs: the pipelined and TMA kernels fall back to the
-  // fused one where they do not apply
-  out[0] = pipe || tma || L->kernel == PFLB_KERNEL_TWOPASS ? L->kernel : PFLB_KERNEL_FUSED;
+  // fused one where they do not apply (the two-cell form to the one-cell
+  // form at storage other than FP32)
+  out[0] = pipe2 ? PFLB_KERNEL_PIPE2
+                 : (pipe ? PFLB_KERNEL_PIPE
+                         : (tma || L->kernel == PFLB_KERNEL_TWOPASS ? L->kernel : PFLB_KERNEL_FUSED));
   out[1] = tma ? 32 : (pipe ? 32 : L->bx);
   out[2] = tma ? 8 : (pipe ? 4 : L->by);
   out[3] = L->lz;
@@ -826,9 +920,15 @@ int64_t pflb_device_bytes(const pflb_lattice *L) { return L ? L->dev_bytes : 0; 
 int64_t pflb_estimate_bytes(const pflb_geometry *geom, int storage) {
   if (!geom || !geom->solid || geom->nx < 1 || geom->ny < 1 || geom->nz < 1) return -1;
   const long long N = (long long)geom->nx * geom->ny * geom->nz;
+  if (!fractions_ok(geom)) return -1;
+  const std::vector<uint32_t> all = link_masks(geom), cut = cut_masks(geom);
   long long nw = 0;
-  for (uint32_t m : link_masks(geom)) nw += m != 0;
-  return bytes_for(N, nw, storage);
+  bool has_cut = false;
+  for (long long c = 0; c < N; ++c) {
+    nw += (all[(size_t)c] | cut[(size_t)c]) != 0;
+    has_cut = has_cut || (geom->solid_frac && !geom->solid[c] && geom->solid_frac[c] > 0.0);
+  }
+  return bytes_for(N, nw, storage, has_cut);
 }
 
 static const char kMagic[8] = {'P', 'F', 'L', 'B', 'C', 'K', 'P', '1'};

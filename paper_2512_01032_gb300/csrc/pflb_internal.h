@@ -32,6 +32,8 @@ struct Lattice {
   uint32_t *wmask = nullptr;        // [nw]
   int *wcell = nullptr;             // [nw] cell of each wall node
   void *wgeo = nullptr;             // [5][nw] compute type
+  uint32_t *wcut = nullptr;         // [nw] cut links | c_n << 24 (sub-voxel walls), or null
+  void *sfrac = nullptr;            // [N] solid volume fraction, compute type, or null
   void *ghost = nullptr;            // [18][nw] compute type
   void *phi = nullptr;              // [N] compute type (two-pass path)
   double *diag = nullptr;           // [32]
@@ -101,8 +103,15 @@ inline bool pipe_layout_ok(const Lattice &L) {
   const int v = 16 / (int)L.elem;
   return !L.bc_on && L.nx % (v > 4 ? v : 4) == 0;
 }
+// The two-cell form (PFLB_KERNEL_PIPE2) at FP32 storage; at other storage
+// that kind runs the one-cell form.
+inline bool pipe2_kernel_runs(const Lattice &L) {
+  return L.kernel == PFLB_KERNEL_PIPE2 && L.p.storage == PFLB_STORAGE_FP32 && pipe_layout_ok(L);
+}
 inline bool pipe_kernel_runs(const Lattice &L) {
-  return L.kernel == PFLB_KERNEL_PIPE && pipe_layout_ok(L);
+  return (L.kernel == PFLB_KERNEL_PIPE ||
+          (L.kernel == PFLB_KERNEL_PIPE2 && L.p.storage != PFLB_STORAGE_FP32)) &&
+         pipe_layout_ok(L);
 }
 
 // Sets the thread-local message returned by pflb_last_error().

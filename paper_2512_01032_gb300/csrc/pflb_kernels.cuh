@@ -53,6 +53,8 @@ struct Args {
   const uint32_t *wmask;
   const int *wcell;  // [nw] cell of each wall node
   const R *wgeo;     // [5][nw]: n_w (x,y,z), cos theta, sin theta
+  const uint32_t *wcut; // [nw] links into cut cells (bits 1..18) | c_n << 24, or null
+  const R *sfrac;    // [N] solid volume fraction (1 on solid cells), or null
   R *ghost;          // [18][nw]
   const S *wp_rd;    // [18][nw]
   S *wp_wr;          // [18][nw]
@@ -198,22 +200,76 @@ __device__ __forceinline__ void finish_cell(const Args<S, R> &a, int x, int y, i
   }
   val[0] = phi;
   R gx, gy, gz, lap;
+  // Stencil corrections of the cut links (sub-voxel walls): a cut
+  // neighbour y enters the CD stencils as s_y ghost + (1 - s_y) phi(y); val
+  // keeps phi(y), which the free-slip band and the front probe read, and
+  // s_y (ghost - phi(y)) is added through the stencil weights (3 w_i c_i
+  // for the gradient, 6 w_i for the Laplacian).
+  R cgx = R(0), cgy = R(0), cgz = R(0), clap = R(0);
   const bool wall = (f & F_WALL) != 0;
   if (wall) {
     const int nw = a.nw;
+    // sub-voxel walls: links into cut cells and the sample direction c_n
+    const uint32_t cw = a.wcut ? a.wcut[rec] : 0u;
+    const uint32_t lc = cw & 0x7fffeu;
 #pragma unroll
     for (int i = 1; i < Q; ++i)
       if ((lm >> i) & 1u) val[i] = a.ghost[(i - 1) * nw + rec];
+    // phi_smpl: the node's phi, or for a cut node the average over the
+    // parallelepiped on the wall, (1 - s_x) phi + s_x phi(x + c_n)
+    R smpl = phi;
+    if (cw >> 24) {
+      const int cn = (int)(cw >> 24);
+      R pn = phi;
+#pragma unroll
+      for (int i = 1; i <= 6; ++i)
+        if (i == cn) pn = val[i];
+      const R sx = a.sfrac[c];
+      smpl = (R(1) - sx) * phi + sx * pn;
+    }
     cd_stencil(val, gx, gy, gz, lap);  // grad phi with the previous ghosts
-    wall_ghosts(m, phi, gx, gy, gz, a.wgeo[rec], a.wgeo[nw + rec], a.wgeo[2 * nw + rec],
-                a.wgeo[3 * nw + rec], a.wgeo[4 * nw + rec], lm, val);
-    if (MODE == MODE_STEP) {
+    if (lc) {
 #pragma unroll
       for (int i = 1; i < Q; ++i)
-        if ((lm >> i) & 1u) a.ghost[(i - 1) * nw + rec] = val[i];
+        if ((lc >> i) & 1u) {
+          const R d = a.sfrac[c + nb.off(i)] * (a.ghost[(i - 1) * nw + rec] - val[i]) *
+                      R(3.0 * w_of(i));
+          gx += R(cx_of(i)) * d;
+          gy += R(cy_of(i)) * d;
+          gz += R(cz_of(i)) * d;
+        }
+    }
+    const WallDir<R> wd = wall_dir(smpl, gx, gy, gz, a.wgeo[rec], a.wgeo[nw + rec],
+                                   a.wgeo[2 * nw + rec], a.wgeo[3 * nw + rec],
+                                   a.wgeo[4 * nw + rec]);
+#pragma unroll
+    for (int i = 1; i < Q; ++i)
+      if ((lm >> i) & 1u) {
+        val[i] = m.blend * val[i] + (R(1) - m.blend) * fresh_ghost(m, wd, i);
+        if (MODE == MODE_STEP) a.ghost[(i - 1) * nw + rec] = val[i];
+      }
+    if (lc) {
+#pragma unroll
+      for (int i = 1; i < Q; ++i)
+        if ((lc >> i) & 1u) {
+          const R gnew = m.blend * a.ghost[(i - 1) * nw + rec] +
+                         (R(1) - m.blend) * fresh_ghost(m, wd, i);
+          if (MODE == MODE_STEP) a.ghost[(i - 1) * nw + rec] = gnew;
+          const R d = a.sfrac[c + nb.off(i)] * (gnew - val[i]);
+          cgx += R(3.0 * w_of(i) * cx_of(i)) * d;
+          cgy += R(3.0 * w_of(i) * cy_of(i)) * d;
+          cgz += R(3.0 * w_of(i) * cz_of(i)) * d;
+          clap += R(6.0 * w_of(i)) * d;
+        }
     }
   }
   cd_stencil(val, gx, gy, gz, lap);
+  if (wall) {
+    gx += cgx;
+    gy += cgy;
+    gz += cgz;
+    lap += clap;
+  }
   const Macro<R> mc = macros(m, g, phi, gx, gy, gz, lap);
 
   if (DIAG) {
@@ -751,15 +807,25 @@ __global__ void k_init(const __grid_constant__ Args<S, R> a, const double *phi0,
   const R phi = (R)phi0[c];
   R val[Q];
   val[0] = phi;
-  uint32_t lm = 0;
+  uint32_t lm = 0, lc = 0;
   int rec = 0;
-  if (f & F_WALL) { rec = a.widx[c]; lm = a.wmask[rec]; }
+  if (f & F_WALL) {
+    rec = a.widx[c];
+    lm = a.wmask[rec];
+    if (a.wcut) lc = a.wcut[rec] & 0x7fffeu;
+  }
 #pragma unroll
-  for (int i = 1; i < Q; ++i) val[i] = ((lm >> i) & 1u) ? phi : (R)phi0[c + nb.off(i)];
+  for (int i = 1; i < Q; ++i) {
+    val[i] = ((lm >> i) & 1u) ? phi : (R)phi0[c + nb.off(i)];
+    if ((lc >> i) & 1u) {  // a cut neighbour: s ghost + (1 - s) phi, ghost = phi here
+      const R sy = a.sfrac[c + nb.off(i)];
+      val[i] = sy * phi + (R(1) - sy) * val[i];
+    }
+  }
   if (f & F_WALL) {
 #pragma unroll
     for (int i = 1; i < Q; ++i)
-      if ((lm >> i) & 1u) a.ghost[(i - 1) * a.nw + rec] = phi;
+      if (((lm | lc) >> i) & 1u) a.ghost[(i - 1) * a.nw + rec] = phi;
   }
   R gx, gy, gz, lap;
   cd_stencil(val, gx, gy, gz, lap);

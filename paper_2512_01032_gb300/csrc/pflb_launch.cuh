@@ -9,6 +9,7 @@
 #include "pflb_internal.h"
 #include "pflb_kernels.cuh"
 #include "pflb_pipe.cuh"
+#include "pflb_pipe2.cuh"
 
 namespace pflb {
 
@@ -65,6 +66,8 @@ static Args<S, R> make_args(Lattice &L) {
   a.wmask = L.wmask;
   a.wcell = L.wcell;
   a.wgeo = (const R *)L.wgeo;
+  a.wcut = L.wcut;
+  a.sfrac = (const R *)L.sfrac;
   a.ghost = (R *)L.ghost;
   a.wp_rd = (const S *)L.wp[rd];
   a.wp_wr = (S *)L.wp[rd ^ 1];
@@ -182,8 +185,42 @@ static cudaError_t launch_pipe_t(Lattice &L, Args<S, R> &a) {
   return cudaGetLastError();
 }
 
+template <bool ODD, bool DIAG>
+static cudaError_t pipe2_attrs() {
+  static unsigned long long done = 0;  // bit d: set on device d
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+  if (bit && (done & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(k_pipe2<ODD, DIAG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(Pipe2Smem));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_pipe2<ODD, DIAG>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           100);
+  if (e != cudaSuccess) return e;
+  done |= bit;
+  return cudaSuccess;
+}
+
+template <bool ODD, bool DIAG>
+static cudaError_t launch_pipe2_t(Lattice &L, Args<float, float> &a) {
+  cudaError_t e = pipe2_attrs<ODD, DIAG>();
+  if (e != cudaSuccess) return e;
+  const dim3 grid((L.nx + PP_BX - 1) / PP_BX, (L.ny + PP_BY - 1) / PP_BY,
+                  (L.nz + L.lz - 1) / L.lz);
+  k_pipe2<ODD, DIAG><<<grid, P2_NT, sizeof(Pipe2Smem), L.stream>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || L.nw == 0) return e;
+  k_wall<float, float, ODD, DIAG><<<(L.nw + 127) / 128, 128, 0, L.stream>>>(a);
+  return cudaGetLastError();
+}
+
 template <class S, class R, bool ODD, bool DIAG>
 static cudaError_t launch_fused_t(Lattice &L, Args<S, R> &a) {
+  if constexpr (std::is_same<S, float>::value && std::is_same<R, float>::value) {
+    if (pipe2_kernel_runs(L)) return launch_pipe2_t<ODD, DIAG>(L, a);
+  }
   if constexpr (pipe_storage<S>()) {
     if (pipe_eligible(L)) return launch_pipe_t<S, R, ODD, DIAG>(L, a);
   }
@@ -226,15 +263,22 @@ static cudaError_t launch_cell_t(Lattice &L, Args<S, R> &a) {
 template <class S, class R>
 int auto_lz(const Lattice &L) {
   int dev = 0, nsm = 0, per = 0;
-  bool tma = false, pipe = false;
-  if constexpr (std::is_same<S, float>::value && std::is_same<R, float>::value)
+  bool tma = false, pipe = false, pipe2 = false;
+  if constexpr (std::is_same<S, float>::value && std::is_same<R, float>::value) {
     tma = async_eligible(L);
-  if constexpr (pipe_storage<S>()) pipe = pipe_eligible(L);
+    pipe2 = pipe2_kernel_runs(L);
+  }
+  if constexpr (pipe_storage<S>()) pipe = pipe2 || pipe_eligible(L);
   const int bx = pipe ? PP_BX : (tma ? AB_X : L.bx), by = pipe ? PP_BY : (tma ? AB_Y : L.by);
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) {
-    if (pipe) {
+    if (pipe2) {
+      e = pipe2_attrs<false, true>();
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pipe2<false, true>, P2_NT,
+                                                          sizeof(Pipe2Smem));
+    } else if (pipe) {
       if constexpr (pipe_storage<S>()) {
         e = pipe_attrs<S, R, false, true>();
         if (e == cudaSuccess)

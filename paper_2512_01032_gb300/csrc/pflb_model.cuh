@@ -281,32 +281,37 @@ __device__ __forceinline__ void cd_stencil(const R v[Q], R &gx, R &gy, R &gz, R 
 // ------------------------------------------------------------ wetting
 // Ghost values of Eqs. 14-15 with the hysteresis blend of Sec. III A.
 // The tanh of a sum is evaluated through tanh(a + b) = (s + tb)/(1 + s tb)
-// with s = tanh(a) = 2 phi - 1 (clamped to [-1, 1]) and tb = tanh(2 d_i/W),
-// which is algebraically identical to the artanh form and needs no artanh.
-// In: old ghosts in val[i] for solid links, grad from those values.
-// Out: val[i] <- new ghost for each solid link (also returned in gnew).
+// with s = tanh(a) = 2 phi_smpl - 1 (clamped to [-1, 1]) and
+// tb = tanh(2 d_i/W), which is algebraically identical to the artanh form
+// and needs no artanh.  WallDir holds what a node's links share: w (n_w
+// rotated by pi - theta about n_w x grad) and s.
 template <class R>
-__device__ __forceinline__ void wall_ghosts(const Model<R> &m, R phi, R gx, R gy, R gz, R nwx,
-                                            R nwy, R nwz, R cth, R sth, uint32_t links,
-                                            R val[Q]) {
+struct WallDir {
+  R wx, wy, wz, s;
+};
+template <class R>
+__device__ __forceinline__ WallDir<R> wall_dir(R phi_smpl, R gx, R gy, R gz, R nwx, R nwy,
+                                               R nwz, R cth, R sth) {
   R gn = gx * nwx + gy * nwy + gz * nwz;
   R tx = gx - gn * nwx, ty = gy - gn * nwy, tz = gz - gn * nwz;
   R tn2 = tx * tx + ty * ty + tz * tz;
   R inv = tn2 >= R(1e-20) ? div_(R(1), sqrt_(tn2)) : R(0);
   tx *= inv; ty *= inv; tz *= inv;
-  R wx = -cth * nwx + sth * tx, wy = -cth * nwy + sth * ty, wz = -cth * nwz + sth * tz;
-  R s = R(2) * phi - R(1);
-  s = s > R(1) ? R(1) : (s < R(-1) ? R(-1) : s);
-#pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    if (!((links >> i) & 1u)) continue;
-    R d = wx * R(cx_of(i)) + wy * R(cy_of(i)) + wz * R(cz_of(i));
-    R tb = tanh_(m.two_over_W * d);
-    R fresh = R(0.5) * (R(1) + div_(s + tb, R(1) + s * tb));
-    val[i] = m.blend * val[i] + (R(1) - m.blend) * fresh;
-  }
+  WallDir<R> d;
+  d.wx = -cth * nwx + sth * tx;
+  d.wy = -cth * nwy + sth * ty;
+  d.wz = -cth * nwz + sth * tz;
+  R s = R(2) * phi_smpl - R(1);
+  d.s = s > R(1) ? R(1) : (s < R(-1) ? R(-1) : s);
+  return d;
 }
-
+// The unblended ghost phi_{s,i} of link i (Eq. 15 with d_i = w . c_i).
+template <class R>
+__device__ __forceinline__ R fresh_ghost(const Model<R> &m, const WallDir<R> &w, int i) {
+  R d = w.wx * R(cx_of(i)) + w.wy * R(cy_of(i)) + w.wz * R(cz_of(i));
+  R tb = tanh_(m.two_over_W * d);
+  return R(0.5) * (R(1) + div_(w.s + tb, R(1) + w.s * tb));
+}
 // ------------------------------------------------------------ macros
 template <class R>
 struct Macro {

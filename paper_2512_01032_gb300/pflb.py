@@ -21,7 +21,7 @@ OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NAN, ERR_TIMEOUT, ERR_BUDGET, ERR_STATE = ra
 STORAGE_FP64, STORAGE_FP32, STORAGE_FP16, STORAGE_BF16 = 0, 1, 2, 3
 FIELD_PHI, FIELD_RHO, FIELD_P, FIELD_UX, FIELD_UY, FIELD_UZ = range(6)
 FIELDS = {"phi": 0, "rho": 1, "P": 2, "ux": 3, "uy": 4, "uz": 5}
-KERNEL_FUSED, KERNEL_TWOPASS, KERNEL_FUSED_TMA, KERNEL_PIPE = 0, 1, 2, 3
+KERNEL_FUSED, KERNEL_TWOPASS, KERNEL_FUSED_TMA, KERNEL_PIPE, KERNEL_PIPE2 = 0, 1, 2, 3, 4
 
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NAN",
                 5: "ERR_TIMEOUT", 6: "ERR_BUDGET", 7: "ERR_STATE"}
@@ -97,7 +97,8 @@ class PflbError(RuntimeError):
 
 class Geometry(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
-                ("solid", _P(C.c_uint8)), ("wall_normal", _d), ("theta_deg", _d)]
+                ("solid", _P(C.c_uint8)), ("wall_normal", _d), ("theta_deg", _d),
+                ("solid_frac", _d)]
 
 
 class Params(C.Structure):
@@ -270,8 +271,10 @@ def _f64(a) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
 
 
-def make_geometry(nx, ny, nz, solid=None, wall_normal=None, theta_cells=None):
-    """Build a ``Geometry`` struct plus the numpy arrays it points into."""
+def make_geometry(nx, ny, nz, solid=None, wall_normal=None, theta_cells=None, solid_frac=None):
+    """Build a ``Geometry`` struct plus the numpy arrays it points into
+    (solid_frac: the solid volume fraction of each cell for walls that cut
+    fluid cells, or None for voxel walls)."""
     N = int(nx) * int(ny) * int(nz)
     s = np.zeros(N, np.uint8) if solid is None else np.ascontiguousarray(
         np.asarray(solid, np.uint8).reshape(-1))
@@ -283,10 +286,14 @@ def make_geometry(nx, ny, nz, solid=None, wall_normal=None, theta_cells=None):
         raise ValueError("wall_normal must hold 3 values per cell")
     if th is not None and th.size != N:
         raise ValueError("theta_cells must hold one value per cell")
+    fr = None if solid_frac is None else _f64(solid_frac).reshape(-1)
+    if fr is not None and fr.size != N:
+        raise ValueError("solid_frac must hold one value per cell")
     g = Geometry(int(nx), int(ny), int(nz), s.ctypes.data_as(_P(C.c_uint8)),
                  nw.ctypes.data_as(_d) if nw is not None else None,
-                 th.ctypes.data_as(_d) if th is not None else None)
-    return g, (s, nw, th)
+                 th.ctypes.data_as(_d) if th is not None else None,
+                 fr.ctypes.data_as(_d) if fr is not None else None)
+    return g, (s, nw, th, fr)
 
 
 def fields_noalloc(nx, ny, nz, h_ptr: int, g_ptr: int, params: Params, fields_ptr=None,
@@ -303,8 +310,8 @@ def fields_noalloc(nx, ny, nz, h_ptr: int, g_ptr: int, params: Params, fields_pt
     return d.as_dict() if want_diag else None
 
 
-def estimate_bytes(nx, ny, nz, solid=None, storage=STORAGE_FP32) -> int:
-    g, keep = make_geometry(nx, ny, nz, solid)
+def estimate_bytes(nx, ny, nz, solid=None, storage=STORAGE_FP32, solid_frac=None) -> int:
+    g, keep = make_geometry(nx, ny, nz, solid, solid_frac=solid_frac)
     return int(load().pflb_estimate_bytes(C.byref(g), int(storage)))
 
 
@@ -312,12 +319,12 @@ class Lattice:
     """Owner of one ``pflb_lattice`` handle."""
 
     def __init__(self, nx, ny, nz, solid=None, wall_normal=None, theta_cells=None, stream=None,
-                 params: Params | None = None, **kw):
+                 params: Params | None = None, solid_frac=None, **kw):
         lib = load()
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.N = self.nx * self.ny * self.nz
         self.params = params if params is not None else default_params(**kw)
-        geom, keep = make_geometry(nx, ny, nz, solid, wall_normal, theta_cells)
+        geom, keep = make_geometry(nx, ny, nz, solid, wall_normal, theta_cells, solid_frac)
         self._stream = stream
         h = C.c_void_p()
         _check(lib.pflb_create(C.byref(geom), C.byref(self.params),

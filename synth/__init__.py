@@ -101,6 +101,8 @@ class Geometry:
             solid |= s.sdf(*self._XYZ) < 0
         self.solid3 = solid
         self.theta3 = np.full((nz, ny, nx), float(theta_deg))
+        # solid volume fraction of fluid cells that a wall cuts (0: voxel walls)
+        self.frac3 = np.zeros((nz, ny, nx))
 
     @property
     def N(self):
@@ -111,12 +113,19 @@ class Geometry:
         return self.solid3.astype(np.uint8).reshape(-1)
 
     def wall_nodes3(self) -> np.ndarray:
-        """Fluid cells with at least one solid D3Q19 neighbour."""
+        """Fluid cells with at least one solid or cut D3Q19 neighbour."""
         s = self.solid3
+        sc = s | (self.frac3 > 0)
         w = np.zeros_like(s)
         for dx, dy, dz in _OFFS:
-            w |= np.roll(s, shift=(-dz, -dy, -dx), axis=(0, 1, 2))
+            w |= np.roll(sc, shift=(-dz, -dy, -dx), axis=(0, 1, 2))
         return w & ~s
+
+    def solid_frac(self):
+        """Solid volume fraction per cell (x fastest), or None for voxel walls."""
+        if not (self.frac3 > 0).any():
+            return None
+        return np.where(self.solid3, 1.0, self.frac3).reshape(-1)
 
     def normals(self) -> np.ndarray:
         """Unit wall normals (into the fluid) at wall nodes, zero elsewhere.
@@ -240,6 +249,24 @@ def static_slug(theta_deg, H=32, length=64, nx=192, nz=4):
     p = dict(sigma=0.01, W=4.0, M=0.02, rho_H=1.0, rho_L=1e-3, nu_H=0.1, nu_L=0.1,
              theta_deg=theta_deg, F_mode=1, mobility_corr=1, free_slip=1, blend=0.95)
     init = dict(shape=2, center=(nx / 2.0 - 0.5, 0.0, 0.0), R=length / 2.0, normal=(1.0, 0.0, 0.0))
+    return g, p, init
+
+
+def offset_slug(theta_deg, delta, H=32, length=64, nx=192, nz=4):
+    """The static slug between flat plates with both walls moved into the
+    channel by delta in [0, 1) (Sec. IV A: the lattice-aligned walls at 0
+    and H become delta and H - delta): solid rows y = 0 and y = H + 1 as in
+    static_slug, and the rows y = 1 and y = H cut by the walls with solid
+    fraction delta (the walls at y = 0.5 + delta and H + 0.5 - delta).  The
+    gap between the walls is H - 2 delta.  Voxels count as solid only when
+    the wall covers them whole, so the cut rows stay fluid cells."""
+    g, p, init = static_slug(theta_deg, H=H, length=length, nx=nx, nz=nz)
+    if not 0.0 <= delta < 1.0:
+        raise ValueError("delta must lie in [0, 1)")
+    g.frac3[:, 1, :] = delta
+    g.frac3[:, H, :] = delta
+    g.shapes = [Plane((0, 0.5 + delta, 0), (0, 1, 0)),
+                Plane((0, H + 0.5 - delta, 0), (0, -1, 0))]
     return g, p, init
 
 

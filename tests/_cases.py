@@ -24,16 +24,17 @@ def make_pair(geom: synth.Geometry, params: dict, init: dict, storage="fp64", ke
 
     nrm = geom.normals() if use_normals else None
     th = geom.theta() if use_theta else None
+    fr = geom.solid_frac()
     gp = dict(params)
     G = pflb.Lattice(geom.nx, geom.ny, geom.nz, solid=geom.solid, wall_normal=nrm,
-                     theta_cells=th, storage=storage, **gp)
+                     theta_cells=th, storage=storage, solid_frac=fr, **gp)
     if tile is not None:
         G.set_kernel(kernel, *tile)
     else:
         G.set_kernel(kernel)
     op = {k: v for k, v in gp.items() if k in ORACLE_KEYS}
     Orc = O.OracleLattice(geom.nx, geom.ny, geom.nz, solid=geom.solid, wall_normal=nrm,
-                          theta_cells=th, nthreads=NTHREADS, **op)
+                          theta_cells=th, nthreads=NTHREADS, solid_frac=fr, **op)
     shape = init.get("shape", 0)
     G.init_tanh(shape, init["center"], init.get("R", 0.0), init.get("normal"), P0)
     phi0 = O.tanh_phi(shape, (geom.nx, geom.ny, geom.nz), init["center"], init.get("R", 0.0),

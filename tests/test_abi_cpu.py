@@ -175,6 +175,26 @@ def test_estimate_bytes_counts_wall_nodes():
     assert walled - empty == nw * (2 * 18 * 4 + 4 + 4 + 5 * 4 + 18 * 4)
 
 
+def test_estimate_bytes_with_cut_cells():
+    """Sub-voxel walls: the cells next to a cut row become wall nodes, and a
+    lattice with cut cells keeps a cut-link word per wall node and a
+    fraction per cell; a fluid fraction outside [0, 1) is refused (-1)."""
+    from paper_2512_01032_gb300 import pflb
+    n = 16
+    N = n ** 3
+    solid = np.zeros((n, n, n), np.uint8)
+    solid[0] = 1
+    walled = pflb.estimate_bytes(n, n, n, solid)
+    frac = np.zeros((n, n, n))
+    frac[1] = 0.3  # the plane z = 1 is cut
+    cut = pflb.estimate_bytes(n, n, n, solid, solid_frac=frac)
+    per_node = 2 * 18 * 4 + 4 + 4 + 5 * 4 + 18 * 4
+    # z = 2 joins the wall nodes (z = 1 and z = n - 1 already are)
+    assert cut - walled == n * n * per_node + 3 * n * n * 4 + N * 4
+    frac[1, 0, 0] = 1.0
+    assert pflb.estimate_bytes(n, n, n, solid, solid_frac=frac) == -1
+
+
 def test_no_cpu_fallback_without_a_gpu():
     """With the library built but no GPU, a valid lattice is refused with a
     CUDA error; nothing falls back to host computation.  (Skipped where a
