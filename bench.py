@@ -49,13 +49,10 @@ N_BOX = 128
 CLOCK_WINDOW_S = 1.0  # untimed load before the timed region, for the clock record
 KERNEL_SOURCES = ("pflb_kernels.cuh", "pflb_model.cuh", "pflb_launch.cuh", "pflb_pipe.cuh",
                   "pflb_f32.cu")
-KERNEL_NAMES = {0: "k_fused", 1: "k_phi + k_cell", 2: "k_fused_async", 3: "k_pipe",
-                4: "k_pipe2"}
+KERNEL_NAMES = {0: "k_fused", 1: "k_phi + k_cell", 2: "k_fused_async", 3: "k_pipe"}
 KERNEL_TEXT = {0: "fused z-marching, direct loads", 1: "phi pass + per-cell pass",
                2: "fused z-marching, h staged by TMA",
-               3: "fused z-marching, populations staged one plane ahead by cp.async",
-               4: "fused z-marching, populations staged one plane ahead by cp.async, two cells "
-                  "per thread in packed FP32"}
+               3: "fused z-marching, populations staged one plane ahead by cp.async"}
 ORACLE_KEYS = ("sigma", "W", "M", "rho_H", "rho_L", "nu_H", "nu_L", "theta_deg", "Fex", "blend",
                "F_mode", "mobility_corr", "free_slip")
 
@@ -652,7 +649,7 @@ def main(argv=None):
 
     launch = L.get_kernel()
     # the pipelined kernel leaves wall nodes to a second launch (k_wall)
-    launches_per_step = 2 if launch["kind"] in (3, 4) and g.wall_nodes3().any() else 1
+    launches_per_step = 2 if launch["kind"] == 3 and g.wall_nodes3().any() else 1
     peak, peak_kind = hbm_peak()
     achieved = fluid * ALGO_BYTES_FP32 / (ms_step * 1e-3) / 1e9
     traffic = recorded_traffic(KERNEL_NAMES.get(launch["kind"], ""))

@@ -76,12 +76,9 @@ enum { PFLB_FIELD_PHI = 0, PFLB_FIELD_RHO = 1, PFLB_FIELD_P = 2,
  *   PFLB_KERNEL_TWOPASS: a phi pass followed by a per-cell pass;
  *   PFLB_KERNEL_FUSED_TMA: the fused pass with h staged through shared
  *     memory by TMA (FP32 storage, nx a multiple of 4 and nx >= 64;
- *     otherwise PFLB_KERNEL_FUSED runs);
- *   PFLB_KERNEL_PIPE2: PFLB_KERNEL_PIPE with two neighbouring cells per
- *     thread and their arithmetic in packed FP32 (two results per
- *     instruction) at FP32 storage; at other storage PFLB_KERNEL_PIPE runs. */
+ *     otherwise PFLB_KERNEL_FUSED runs). */
 enum { PFLB_KERNEL_FUSED = 0, PFLB_KERNEL_TWOPASS = 1, PFLB_KERNEL_FUSED_TMA = 2,
-       PFLB_KERNEL_PIPE = 3, PFLB_KERNEL_PIPE2 = 4 };
+       PFLB_KERNEL_PIPE = 3 };
 
 /* Geometry, read during pflb_create only.
  *   solid       : host, nx*ny*nz bytes, nonzero = solid voxel.

@@ -68,14 +68,17 @@
  *       wall cuts).  Cut cells are fluid cells in every other respect (they
  *       hold populations; bounce-back and the free-slip band act only at
  *       links into solid voxels).  A wall node is a fluid cell with a
- *       neighbour of s > 0, and it keeps one ghost phi_{s,i} per such link.
+ *       neighbour of s > 0; it keeps one ghost phi_{s,i} per link into a
+ *       solid voxel and per link into a cut cell that points into the wall.
  *       Its sample phi_smpl averages phi over a parallelepiped one spacing
  *       thick standing on the wall: (1 - s_x) phi(x) + s_x phi(x + c_n),
  *       with c_n the axis direction nearest the wall normal (phi(x) in
  *       place of phi(x + c_n) when that cell is solid).  In the CD stencils
- *       the neighbour y = x + c_i contributes s_y phi_{s,i} + (1 - s_y)
- *       phi(y): the ghost for the part of y inside the wall, y's own phi for
- *       the rest.  With every s in {0, 1} this is R6 exactly.
+ *       a cut neighbour y = x + c_i along a link into the wall (c_i . n_w
+ *       < 0) contributes s_y phi_{s,i} + (1 - s_y) phi(y): the ghost for the
+ *       part of y inside the wall, y's own phi for the rest; a link parallel
+ *       to the wall or away from it does not cross the wall and takes phi(y).
+ *       With every s in {0, 1} this is R6 exactly.
  *
  * Parity unpinned by the paper (pinned only oracle <-> GPU): the sub-step
  * order (R3), the ghost lag (R11), the blend side (R12) and the free-slip
@@ -473,6 +476,12 @@ int orc_set_solid_fraction(orc_lattice *L, const double *frac, const double *wal
 
 /* Neighbour values for the CD stencil at fluid cell x: phi of fluid
  * neighbours, the wall node's ghost for solid ones (Sec. II B). */
+/* Link i of x points into the wall: c_i . n_w(x) < 0 (R23). */
+static inline int into_wall(const orc_lattice *L, int64_t x, int i) {
+    const double *n = L->nw + 3 * x;
+    return CX[i] * n[0] + CY[i] * n[1] + CZ[i] * n[2] < -1e-9;
+}
+
 static void stencil_values(const orc_lattice *L, int64_t x, const double *ghost, double val[Q]) {
     val[0] = L->phi[x];
     for (int i = 1; i < Q; ++i) {
@@ -480,18 +489,21 @@ static void stencil_values(const orc_lattice *L, int64_t x, const double *ghost,
         double s = sfrac(L, y);
         if (s >= 1.0)
             val[i] = ghost[x * Q + i];
-        else if (s > 0.0) /* R23: ghost for the part of y inside the wall */
+        else if (s > 0.0 && into_wall(L, x, i)) /* R23: ghost for y's part inside the wall */
             val[i] = s * ghost[x * Q + i] + (1.0 - s) * L->phi[y];
         else
             val[i] = L->phi[y];
     }
 }
 
-/* Links of x that carry a ghost: bit i set when x + c_i is solid or cut. */
+/* Links of x that carry a ghost: bit i set when x + c_i is solid, or cut
+ * with link i pointing into the wall. */
 static uint32_t ghost_links(const orc_lattice *L, int64_t x) {
     uint32_t m = 0;
-    for (int i = 1; i < Q; ++i)
-        if (sfrac(L, nbr(L, x, i)) > 0.0) m |= 1u << i;
+    for (int i = 1; i < Q; ++i) {
+        double s = sfrac(L, nbr(L, x, i));
+        if (s >= 1.0 || (s > 0.0 && into_wall(L, x, i))) m |= 1u << i;
+    }
     return m;
 }
 

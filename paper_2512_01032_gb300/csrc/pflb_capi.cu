@@ -39,6 +39,7 @@ struct pflb_batch {
   cudaEvent_t ev = nullptr;
   cudaGraphExec_t graph = nullptr;  // kGraphSteps plain steps
   int graph_nxbc = -1;               // open-boundary lattice count the graph was captured for
+  int graph_pmask = -1;              // A-A parities of the pipelined lattices at capture
   std::vector<char> pipe_set;        // lattices the work lists were built to march pipelined
   bool poisoned = false;
 };
@@ -333,7 +334,13 @@ void build_geometry(const pflb_geometry *g, const pflb_params *p, HostGeom &hg) 
         if (d > best) { best = d; cn = i; }
       }
       if (!(cell_frac(g, c) > 0.0) || g->solid[nbr(cn)]) cn = 0;
-      hg.wcut.push_back(cuts[k] | ((uint32_t)cn << 24));
+      // only links into the wall (c_i . n_w < 0) cross it; links to cut
+      // cells parallel to the wall or away from it take the cell's phi
+      uint32_t cm = cuts[k];
+      for (int i = 1; i < pflb::Q; ++i)
+        if (!(pflb::cx_of(i) * n[0] + pflb::cy_of(i) * n[1] + pflb::cz_of(i) * n[2] < -1e-9))
+          cm &= ~(1u << i);
+      hg.wcut.push_back(cm | ((uint32_t)cn << 24));
     }
     const double th = (g->theta_deg ? g->theta_deg[c] : p->theta_deg) * (3.14159265358979323846 / 180.0);
     hg.wgeo[0 * nw + k] = n[0];
@@ -668,7 +675,7 @@ pflb_status pflb_set_kernel(pflb_lattice *L, int kind, int bx, int by, int lz) {
   pflb_status s = check_lattice(L);
   if (s != PFLB_OK) return s;
   if (kind != PFLB_KERNEL_FUSED && kind != PFLB_KERNEL_TWOPASS && kind != PFLB_KERNEL_FUSED_TMA &&
-      kind != PFLB_KERNEL_PIPE && kind != PFLB_KERNEL_PIPE2)
+      kind != PFLB_KERNEL_PIPE)
     return fail(PFLB_ERR_ARG, "unknown kernel");
   if (lz < -1) return fail(PFLB_ERR_ARG, "lz must be > 0, 0 (keep) or -1 (automatic)");
   const int nbx = bx > 0 ? bx : L->bx, nby = by > 0 ? by : L->by;
@@ -744,14 +751,10 @@ pflb_status pflb_get_kernel(const pflb_lattice *L, int out[4]) {
   if (!out) return fail(PFLB_ERR_ARG, "null output");
   const bool tma = L->kernel == PFLB_KERNEL_FUSED_TMA && L->p.storage == PFLB_STORAGE_FP32 &&
                    L->tma_ok && !L->bc_on;
-  const bool pipe2 = pflb::pipe2_kernel_runs(*L);
-  const bool pipe = pipe2 || pflb::pipe_kernel_runs(*L);
+  const bool pipe = pflb::pipe_kernel_runs(*L);
   // the kind that runs: the pipelined and TMA kernels fall back to the
-  // fused one where they do not apply (the two-cell form to the one-cell
-  // form at storage other than FP32)
-  out[0] = pipe2 ? PFLB_KERNEL_PIPE2
-                 : (pipe ? PFLB_KERNEL_PIPE
-                         : (tma || L->kernel == PFLB_KERNEL_TWOPASS ? L->kernel : PFLB_KERNEL_FUSED));
+  // fused one where they do not apply
+  out[0] = pipe || tma || L->kernel == PFLB_KERNEL_TWOPASS ? L->kernel : PFLB_KERNEL_FUSED;
   out[1] = tma ? 32 : (pipe ? 32 : L->bx);
   out[2] = tma ? 8 : (pipe ? 4 : L->by);
   out[3] = L->lz;
@@ -1243,6 +1246,13 @@ static pflb_status batch_run(pflb_batch *b, int64_t nsteps, bool diag_last) {
     return 0;
   });
   for (int l = 0; l < n; ++l) par[l] = (int)(b->lats[l]->step & 1);
+  // parities the pipelined lattices start this call at (one march launch
+  // per parity present at each step)
+  int pmask = 0;
+  for (int l = 0; l < n; ++l)
+    if (b->pipe_set[l]) pmask |= 1 << par[l];
+  b->dev.pmask = pmask;
+  if (pmask != b->graph_pmask) batch_drop_graph(b);
   // open x boundaries: specs of every lattice (type 0 = periodic) and the
   // list of those that have them; the values may change between calls
   std::vector<pflb::XbcSpec> specs(n);
@@ -1264,31 +1274,38 @@ static pflb_status batch_run(pflb_batch *b, int64_t nsteps, bool diag_last) {
   BCK(b, cudaMemcpyAsync(b->dev.par0, par.data(), n * sizeof(int), cudaMemcpyHostToDevice,
                          b->dev.stream));
   BCK(b, cudaMemsetAsync(b->dev.bstep, 0, sizeof(int), b->dev.stream));
-  auto launch = [&](bool diag) {
+  // tpar: parity of the batch step (the device counter bstep starts at 0
+  // with each call and advances by one per step)
+  auto launch = [&](bool diag, int tpar) {
     return dispatch_storage(b->storage, [&](auto *s_, auto *r_) {
       PFLB_SR_TYPES
-      return pflb::batch_launch_step<S, R>(b->dev, diag);
+      return pflb::batch_launch_step<S, R>(b->dev, diag, tpar);
     });
   };
   int64_t plain = nsteps - (diag_last ? 1 : 0);
+  int64_t t = 0;
   if (plain >= kGraphSteps && !b->graph) {
     cudaGraph_t g = nullptr;
     BCK(b, cudaStreamBeginCapture(b->dev.stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) e = launch(false);
+    for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) e = launch(false, k & 1);
     cudaError_t e2 = cudaStreamEndCapture(b->dev.stream, &g);
     if (e == cudaSuccess) e = e2;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
     if (g) cudaGraphDestroy(g);
     if (e != cudaSuccess) return batch_fail(b, e, "graph capture");
     b->graph_nxbc = b->dev.nxbc;
+    b->graph_pmask = b->dev.pmask;
   }
+  // replays come first, so each starts at an even batch step (kGraphSteps
+  // is even), as the captured parities assume
   while (plain >= kGraphSteps) {
     BCK(b, cudaGraphLaunch(b->graph, b->dev.stream));
     plain -= kGraphSteps;
+    t += kGraphSteps;
   }
-  for (; plain > 0; --plain) BCK(b, launch(false));
-  if (diag_last) BCK(b, launch(true));
+  for (; plain > 0; --plain, ++t) BCK(b, launch(false, (int)(t & 1)));
+  if (diag_last) BCK(b, launch(true, (int)(t & 1)));
   for (Lattice *L : b->lats) {
     L->step += nsteps;
     if (diag_last) {

@@ -91,6 +91,7 @@ struct BatchDev {
   int npitems = 0;
   int *pcounter = nullptr;
   int plz = 8, pgrid = 0;
+  int pmask = 0;  // bit q: a pipelined lattice starts the batch call at A-A parity q
   void *witems = nullptr;
   int nwitems = 0;
 };
@@ -103,15 +104,8 @@ inline bool pipe_layout_ok(const Lattice &L) {
   const int v = 16 / (int)L.elem;
   return !L.bc_on && L.nx % (v > 4 ? v : 4) == 0;
 }
-// The two-cell form (PFLB_KERNEL_PIPE2) at FP32 storage; at other storage
-// that kind runs the one-cell form.
-inline bool pipe2_kernel_runs(const Lattice &L) {
-  return L.kernel == PFLB_KERNEL_PIPE2 && L.p.storage == PFLB_STORAGE_FP32 && pipe_layout_ok(L);
-}
 inline bool pipe_kernel_runs(const Lattice &L) {
-  return (L.kernel == PFLB_KERNEL_PIPE ||
-          (L.kernel == PFLB_KERNEL_PIPE2 && L.p.storage != PFLB_STORAGE_FP32)) &&
-         pipe_layout_ok(L);
+  return L.kernel == PFLB_KERNEL_PIPE && pipe_layout_ok(L);
 }
 
 // Sets the thread-local message returned by pflb_last_error().
@@ -155,7 +149,8 @@ template <class S, class R> cudaError_t mark_xbc(Lattice &L, bool on);
 // and the occupancy-limited blocks per SM of the batch kernel.
 template <class S, class R> size_t batch_desc_bytes();
 template <class S, class R> void batch_build_descs(Lattice *const *lats, int n, char *host);
-template <class S, class R> cudaError_t batch_launch_step(const BatchDev &b, bool diag);
+template <class S, class R> cudaError_t batch_launch_step(const BatchDev &b, bool diag,
+                                                         int tpar);
 template <class S, class R> int batch_max_blocks_per_sm(int bx, int by);
 template <class S, class R> int batch_pipe_blocks_per_sm();
 

@@ -9,7 +9,6 @@
 #include "pflb_internal.h"
 #include "pflb_kernels.cuh"
 #include "pflb_pipe.cuh"
-#include "pflb_pipe2.cuh"
 
 namespace pflb {
 
@@ -185,42 +184,8 @@ static cudaError_t launch_pipe_t(Lattice &L, Args<S, R> &a) {
   return cudaGetLastError();
 }
 
-template <bool ODD, bool DIAG>
-static cudaError_t pipe2_attrs() {
-  static unsigned long long done = 0;  // bit d: set on device d
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
-  if (bit && (done & bit)) return cudaSuccess;
-  e = cudaFuncSetAttribute(k_pipe2<ODD, DIAG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sizeof(Pipe2Smem));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_pipe2<ODD, DIAG>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           100);
-  if (e != cudaSuccess) return e;
-  done |= bit;
-  return cudaSuccess;
-}
-
-template <bool ODD, bool DIAG>
-static cudaError_t launch_pipe2_t(Lattice &L, Args<float, float> &a) {
-  cudaError_t e = pipe2_attrs<ODD, DIAG>();
-  if (e != cudaSuccess) return e;
-  const dim3 grid((L.nx + PP_BX - 1) / PP_BX, (L.ny + PP_BY - 1) / PP_BY,
-                  (L.nz + L.lz - 1) / L.lz);
-  k_pipe2<ODD, DIAG><<<grid, P2_NT, sizeof(Pipe2Smem), L.stream>>>(a);
-  e = cudaGetLastError();
-  if (e != cudaSuccess || L.nw == 0) return e;
-  k_wall<float, float, ODD, DIAG><<<(L.nw + 127) / 128, 128, 0, L.stream>>>(a);
-  return cudaGetLastError();
-}
-
 template <class S, class R, bool ODD, bool DIAG>
 static cudaError_t launch_fused_t(Lattice &L, Args<S, R> &a) {
-  if constexpr (std::is_same<S, float>::value && std::is_same<R, float>::value) {
-    if (pipe2_kernel_runs(L)) return launch_pipe2_t<ODD, DIAG>(L, a);
-  }
   if constexpr (pipe_storage<S>()) {
     if (pipe_eligible(L)) return launch_pipe_t<S, R, ODD, DIAG>(L, a);
   }
@@ -263,22 +228,15 @@ static cudaError_t launch_cell_t(Lattice &L, Args<S, R> &a) {
 template <class S, class R>
 int auto_lz(const Lattice &L) {
   int dev = 0, nsm = 0, per = 0;
-  bool tma = false, pipe = false, pipe2 = false;
-  if constexpr (std::is_same<S, float>::value && std::is_same<R, float>::value) {
+  bool tma = false, pipe = false;
+  if constexpr (std::is_same<S, float>::value && std::is_same<R, float>::value)
     tma = async_eligible(L);
-    pipe2 = pipe2_kernel_runs(L);
-  }
-  if constexpr (pipe_storage<S>()) pipe = pipe2 || pipe_eligible(L);
+  if constexpr (pipe_storage<S>()) pipe = pipe_eligible(L);
   const int bx = pipe ? PP_BX : (tma ? AB_X : L.bx), by = pipe ? PP_BY : (tma ? AB_Y : L.by);
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) {
-    if (pipe2) {
-      e = pipe2_attrs<false, true>();
-      if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pipe2<false, true>, P2_NT,
-                                                          sizeof(Pipe2Smem));
-    } else if (pipe) {
+    if (pipe) {
       if constexpr (pipe_storage<S>()) {
         e = pipe_attrs<S, R, false, true>();
         if (e == cudaSuccess)
@@ -384,7 +342,7 @@ void batch_build_descs(Lattice *const *lats, int n, char *host) {
   }
 }
 
-template <class S, class R, bool DIAG>
+template <class S, class R, bool ODD, bool DIAG>
 static cudaError_t batch_pipe_attrs() {
   static unsigned long long done = 0;  // bit d: set on device d
   int dev = 0;
@@ -392,10 +350,11 @@ static cudaError_t batch_pipe_attrs() {
   if (e != cudaSuccess) return e;
   const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
   if (bit && (done & bit)) return cudaSuccess;
-  e = cudaFuncSetAttribute(k_batch_pipe<S, R, DIAG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(k_batch_pipe<S, R, ODD, DIAG>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(sizeof(PipeSmem<S, R>) + sizeof(Args<S, R>)));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_batch_pipe<S, R, DIAG>,
+  e = cudaFuncSetAttribute(k_batch_pipe<S, R, ODD, DIAG>,
                            cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
   done |= bit;
@@ -405,37 +364,44 @@ static cudaError_t batch_pipe_attrs() {
 template <class S, class R>
 int batch_pipe_blocks_per_sm() {
   int nb = 0;
-  if (batch_pipe_attrs<S, R, true>() != cudaSuccess ||
+  if (batch_pipe_attrs<S, R, false, true>() != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &nb, k_batch_pipe<S, R, true>, PP_NT, sizeof(PipeSmem<S, R>) + sizeof(Args<S, R>)) !=
-          cudaSuccess) {
+          &nb, k_batch_pipe<S, R, false, true>, PP_NT,
+          sizeof(PipeSmem<S, R>) + sizeof(Args<S, R>)) != cudaSuccess) {
     cudaGetLastError();
     return 1;
   }
   return nb > 0 ? nb : 1;
 }
 
-// The pipelined lattices of a batch: their march, then their wall nodes.
-template <class S, class R>
-static cudaError_t batch_launch_pipe(const BatchDev &b, bool diag) {
-  if (b.npitems == 0) return cudaSuccess;
-  const Args<S, R> *d = (const Args<S, R> *)b.descs;
-  cudaError_t e = cudaMemsetAsync(b.pcounter, 0, sizeof(int), b.stream);
+template <class S, class R, bool ODD, bool DIAG>
+static cudaError_t batch_pipe_one(const BatchDev &b) {
+  cudaError_t e = batch_pipe_attrs<S, R, ODD, DIAG>();
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(b.pcounter, 0, sizeof(int), b.stream);
   if (e != cudaSuccess) return e;
   const size_t smem = sizeof(PipeSmem<S, R>) + sizeof(Args<S, R>);
-  const int4 *it = (const int4 *)b.pitems;
-  if (diag) {
-    e = batch_pipe_attrs<S, R, true>();
-    if (e != cudaSuccess) return e;
-    k_batch_pipe<S, R, true><<<b.pgrid, PP_NT, smem, b.stream>>>(d, b.par0, it, b.npitems,
-                                                                b.pcounter, b.bstep, b.plz);
-  } else {
-    e = batch_pipe_attrs<S, R, false>();
-    if (e != cudaSuccess) return e;
-    k_batch_pipe<S, R, false><<<b.pgrid, PP_NT, smem, b.stream>>>(d, b.par0, it, b.npitems,
-                                                                 b.pcounter, b.bstep, b.plz);
+  k_batch_pipe<S, R, ODD, DIAG><<<b.pgrid, PP_NT, smem, b.stream>>>(
+      (const Args<S, R> *)b.descs, b.par0, (const int4 *)b.pitems, b.npitems, b.pcounter,
+      b.bstep, b.plz);
+  return cudaGetLastError();
+}
+
+// The pipelined lattices of a batch: their march (one launch per A-A parity
+// present at this step; tpar = parity of the batch step), then their wall
+// nodes.
+template <class S, class R>
+static cudaError_t batch_launch_pipe(const BatchDev &b, bool diag, int tpar) {
+  if (b.npitems == 0) return cudaSuccess;
+  const Args<S, R> *d = (const Args<S, R> *)b.descs;
+  cudaError_t e = cudaSuccess;
+  for (int par = 0; par < 2 && e == cudaSuccess; ++par) {
+    if (!((b.pmask >> (par ^ tpar)) & 1)) continue;  // no lattice at this parity now
+    if (par)
+      e = diag ? batch_pipe_one<S, R, true, true>(b) : batch_pipe_one<S, R, true, false>(b);
+    else
+      e = diag ? batch_pipe_one<S, R, false, true>(b) : batch_pipe_one<S, R, false, false>(b);
   }
-  e = cudaGetLastError();
   if (e != cudaSuccess || b.nwitems == 0) return e;
   const int2 *wit = (const int2 *)b.witems;
   if (diag)
@@ -446,7 +412,7 @@ static cudaError_t batch_launch_pipe(const BatchDev &b, bool diag) {
 }
 
 template <class S, class R>
-cudaError_t batch_launch_step(const BatchDev &b, bool diag) {
+cudaError_t batch_launch_step(const BatchDev &b, bool diag, int tpar) {
   cudaError_t e = cudaMemsetAsync(b.counter, 0, sizeof(int), b.stream);
   if (e != cudaSuccess) return e;
   const size_t smem = batch_smem<S, R>(b.bx, b.by, diag);
@@ -458,7 +424,7 @@ cudaError_t batch_launch_step(const BatchDev &b, bool diag) {
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  e = batch_launch_pipe<S, R>(b, diag);
+  e = batch_launch_pipe<S, R>(b, diag, tpar);
   if (e != cudaSuccess) return e;
   if (b.nitems == 0) {  // every lattice ran the pipelined march
     k_batch_tick<<<1, 1, 0, b.stream>>>(b.bstep);
@@ -501,7 +467,7 @@ int batch_max_blocks_per_sm(int bx, int by) {
   template int batch_pipe_blocks_per_sm<S, R>();                                 \
   template size_t batch_desc_bytes<S, R>();                                      \
   template void batch_build_descs<S, R>(Lattice *const *, int, char *);         \
-  template cudaError_t batch_launch_step<S, R>(const BatchDev &, bool);          \
+  template cudaError_t batch_launch_step<S, R>(const BatchDev &, bool, int);          \
   template int batch_max_blocks_per_sm<S, R>(int, int);                          \
   template cudaError_t launch_init<S, R>(Lattice &, const double *, double);     \
   template cudaError_t launch_step<S, R>(Lattice &, bool);                       \

@@ -365,13 +365,15 @@ __global__ void __launch_bounds__(PP_NT, PFLB_PIPE_MIN_BLOCKS)
 // parity at this batch step ((par0[l] + t) & 1) into shared memory and
 // marches the item's tile column over LZ planes.  The first item of each
 // lattice zeroes its next diagnostic accumulator.
-// The step descriptor lives in shared memory here, so its fields cost
-// registers that k_pipe's constant-bank parameters do not: three blocks per
-// SM (168 registers) instead of four keep the march from spilling (at four,
-// 60-80 bytes of spill stores without diagnostics and several hundred with
-// them; measured 5 % slower on eight serving lattices at FP32).
-template <class S, class R, bool DIAG>
-__global__ void __launch_bounds__(PP_NT, 3)
+// One launch marches one parity (ODD): the items of lattices at the other
+// parity are skipped, and the host launches the second parity only when a
+// lattice of the batch is at it.  With both marches in one kernel the step
+// descriptor's fields in shared memory cost registers that k_pipe's
+// constant-bank parameters do not (168 per thread, three blocks per SM);
+// with one, the march fits k_pipe's 128 registers and four blocks per SM
+// without spilling.
+template <class S, class R, bool ODD, bool DIAG>
+__global__ void __launch_bounds__(PP_NT, 4)
     k_batch_pipe(const Args<S, R> *__restrict__ descs, const int *__restrict__ par0,
                  const int4 *__restrict__ items, int nitems, int *counter, const int *bstep,
                  int LZ) {
@@ -389,6 +391,10 @@ __global__ void __launch_bounds__(PP_NT, 3)
     if (idx >= nitems) break;
     const int4 it = items[idx];
     const int p = (par0[it.x] + t) & 1;
+    if (p != (ODD ? 1 : 0)) {  // the other parity's launch marches this item
+      __syncthreads();         // s_item is read before it is replaced
+      continue;
+    }
     const int *src = reinterpret_cast<const int *>(descs + 2 * it.x + p);
     int *dst = reinterpret_cast<int *>(sa);
     for (int k = tid; k < (int)(sizeof(Args<S, R>) / 4); k += blockDim.x) dst[k] = src[k];
@@ -397,10 +403,7 @@ __global__ void __launch_bounds__(PP_NT, 3)
     if (DIAG && it.y == 0 && it.z == 0 && it.w == 0 && tid < 32 && a.diag_zero)
       a.diag_zero[tid] = 0.0;
     const int ze = min(it.w + LZ, a.nz);
-    if (p)
-      pipe_march<S, R, true, DIAG>(a, it.y, it.z, it.w, ze, sm, wacc);
-    else
-      pipe_march<S, R, false, DIAG>(a, it.y, it.z, it.w, ze, sm, wacc);
+    pipe_march<S, R, ODD, DIAG>(a, it.y, it.z, it.w, ze, sm, wacc);
     __syncthreads();  // shared descriptor and staging buffers are reused by the next item
   }
 }

@@ -21,7 +21,7 @@ OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NAN, ERR_TIMEOUT, ERR_BUDGET, ERR_STATE = ra
 STORAGE_FP64, STORAGE_FP32, STORAGE_FP16, STORAGE_BF16 = 0, 1, 2, 3
 FIELD_PHI, FIELD_RHO, FIELD_P, FIELD_UX, FIELD_UY, FIELD_UZ = range(6)
 FIELDS = {"phi": 0, "rho": 1, "P": 2, "ux": 3, "uy": 4, "uz": 5}
-KERNEL_FUSED, KERNEL_TWOPASS, KERNEL_FUSED_TMA, KERNEL_PIPE, KERNEL_PIPE2 = 0, 1, 2, 3, 4
+KERNEL_FUSED, KERNEL_TWOPASS, KERNEL_FUSED_TMA, KERNEL_PIPE = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NAN",
                 5: "ERR_TIMEOUT", 6: "ERR_BUDGET", 7: "ERR_STATE"}

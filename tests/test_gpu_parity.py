@@ -35,7 +35,7 @@ def _compare(G, Orc, steps_list, storage, p_scale, label=""):
 
 
 @pytest.mark.parametrize("storage", ["fp64", "fp32"])
-@pytest.mark.parametrize("kernel", [0, 1, 3, 4])
+@pytest.mark.parametrize("kernel", [0, 1, 3])
 def test_static_droplet_400_steps(storage, kernel):
     """Periodic 32^3 droplet (R=8, W=4, ratio 1000, sigma=0.01, tau=0.8,
     M=0.02): phi, P, u after 0, 1, 2, 7 and 400 steps."""
@@ -45,7 +45,7 @@ def test_static_droplet_400_steps(storage, kernel):
 
 
 @pytest.mark.parametrize("storage", ["fp64", "fp32"])
-@pytest.mark.parametrize("kernel", [0, 1, 3, 4])
+@pytest.mark.parametrize("kernel", [0, 1, 3])
 def test_sessile_sphere_walls_wetting_free_slip(storage, kernel):
     """Droplet on a voxelised sphere between two planes (32^3 scaling of the
     128^3 workload), theta=60, optimised model: tanh F, free-slip band,
@@ -57,7 +57,7 @@ def test_sessile_sphere_walls_wetting_free_slip(storage, kernel):
 
 @pytest.mark.parametrize("storage", ["fp64", "fp32"])
 @pytest.mark.parametrize("F_mode", [0, 1])
-@pytest.mark.parametrize("kernel", [0, 3, 4])
+@pytest.mark.parametrize("kernel", [0, 3])
 def test_slit_with_force_and_viscosity_ratio(storage, F_mode, kernel):
     """Capillary slit (scaled): walls with theta=45 only in the channel,
     viscosity ratio 50, a small body force, free-slip band and blend.
@@ -113,7 +113,7 @@ def test_ragged_and_tiny_lattices(dims):
     init = dict(shape=0, center=(nx / 2.0 + 0.37, ny / 2.0 - 0.21, nz / 2.0 + 0.13),
                 R=max(1.5, min(dims) / 3.0))
     for storage in ("fp64", "fp32"):
-        for kernel in (0, 3, 4):
+        for kernel in (0, 3):
             G, Orc = CS.make_pair(g, p, init, storage=storage, kernel=kernel)
             _compare(G, Orc, [1, 9], storage, 2 * p["sigma"] / init["R"],
                      f"ragged{dims} kernel {kernel}")
@@ -178,19 +178,19 @@ def test_mask_normals_fallback_parity():
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("kernel", [3, 4])
+@pytest.mark.parametrize("kernel", [3])
 def test_sessile_sphere_64_parity_fp32(kernel):
     """The curved-wall workload at 64^3 (all lengths halved), FP32 storage,
-    the pipelined kernels (one and two cells per thread), 100 steps."""
+    the bench launch configuration, 100 steps."""
     g, p, init = CS.sessile_case(64, 90.0)
     G, Orc = CS.make_pair(g, p, init, storage="fp32", kernel=kernel)
     _compare(G, Orc, [100], "fp32", 2 * p["sigma"] / init["R"], "sessile64")
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("kernel", [3, 4])
+@pytest.mark.parametrize("kernel", [3])
 def test_full_size_128_first_steps_fp32(kernel):
-    """Full 128^3 curved-wall workload in the bench launch configurations:
+    """Full 128^3 curved-wall workload in the bench launch configuration:
     every cell against the oracle after 2 steps."""
     g, p, init = CS.sessile_case(128, 30.0)
     G, Orc = CS.make_pair(g, p, init, storage="fp32", kernel=kernel)
@@ -244,7 +244,7 @@ def test_staged_kernel_matches_plain_bitwise(dims):
 
 
 @pytest.mark.parametrize("storage", ["fp64", "fp32"])
-@pytest.mark.parametrize("kernel", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3])
 def test_diagnostics_match_oracle_fields(storage, kernel):
     """The FP64 diagnostics reduced inside the step kernel (and by the
     macro pass) equal the same sums taken over the oracle's fields: mass,

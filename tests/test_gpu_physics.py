@@ -41,6 +41,16 @@ def test_laplace_pressure_jump():
     assert abs(dp - want) / want < 0.01, (dp, want)
 
 
+def _off_axis(center, dx=1e-3):
+    """The drop's centre moved 1e-3 of a spacing in x.  Started exactly on
+    the box's mirror planes, the 30 and 150 deg drops can go non-finite at
+    FP32 after 4-9 k steps depending on the compiled variant (roundoff
+    asymmetry amplified by n = grad phi / (|grad phi| + 1e-10) where the
+    symmetric start makes grad phi vanish); shifted by 1e-5 to 5e-5 they and
+    the FP64 runs all settle at the same max |u|."""
+    return (center[0] + dx, center[1], center[2])
+
+
 def _axis_top(phi3, c):
     """Highest z where phi on the vertical axis x = y = c is 0.5 (linear
     interpolation; the axis lies between four lattice columns)."""
@@ -60,7 +70,7 @@ def test_drop_height_on_sphere(theta):
     n = 64
     g, p, drop = synth.sessile_sphere(n, theta)
     L = _lattice(g, p)
-    L.init_tanh(0, drop["center"], drop["R"])
+    L.init_tanh(0, _off_axis(drop["center"]), drop["R"])
     V = L.diag()["mass"]
     L.step(15000)
     d = L.diag()
@@ -90,7 +100,7 @@ def test_sessile_drop_on_sphere_128_full_run(theta):
     n = 128
     g, p, drop = synth.sessile_sphere(n, theta)
     L = _lattice(g, p)
-    L.init_tanh(0, drop["center"], drop["R"])
+    L.init_tanh(0, _off_axis(drop["center"]), drop["R"])
     V = L.diag()["mass"]
     L.step(60000 if theta == 30.0 else 20000)
     d = L.diag()
@@ -260,3 +270,49 @@ def test_dynamic_slug_in_a_slit():
     # Poiseuille flow at its speed, above it (1.6x measured: in a slug two
     # gaps long the flow recirculates near the menisci and dissipates more)
     assert dP_wall > 0 and 1.0 < -slope / pois < 2.5
+
+
+def _slug_angle(phi2, ylo, yhi, nx):
+    """Contact angle of the right meniscus of a static slug between walls at
+    ylo and yhi (circle fit to the phi = 0.5 contour, rows W/2 off the
+    walls, inside the liquid)."""
+    ny = phi2.shape[0]
+    sub = phi2[1:ny - 1, nx // 2:]
+    pts = synth.contour_points(sub, 0.5)
+    pts[:, 0] += nx // 2
+    pts[:, 1] += 1.0
+    core = pts[(pts[:, 1] > ylo + 3.0) & (pts[:, 1] < yhi - 3.0)]
+    cx, cy, r = synth.fit_circle(core)
+    c = min(1.0, ((yhi - ylo) / 2.0) / r)
+    wetting = cx > core[:, 0].mean()  # centre of curvature on the gas side
+    return math.degrees(math.acos(c)) if wetting else 180.0 - math.degrees(math.acos(c))
+
+
+@pytest.mark.parametrize("delta", [0.2, 0.5, 0.8])
+@pytest.mark.parametrize("theta", [20.0, 60.0, 120.0, 160.0])
+def test_offset_slug_angle(theta, delta):
+    """The static slug between plates moved into the channel by delta (Sec.
+    IV A, walls at 0.5 + delta and H + 0.5 - delta, sub-voxel reading R23),
+    20000 steps at FP32: the run stays finite with bounded spurious
+    currents, the meniscus keeps the wetting side of its input angle, and at
+    60 and 120 deg its angle (circle fit, gap H - 2 delta) is within 8 deg
+    of the input.  This light weighting does not give the paper's
+    offset-independent angles (Fig. 10): measured 63.6 / 65.1 / 65.5 deg
+    for 60 and 116.5 / 114.9 / 114.4 for 120 at delta 0.2 / 0.4 / 0.8, and
+    32 / 37 / 41 for 20 and 149 / 143 / 141 for 160 (the cut cells evolve as
+    whole fluid cells, so the wetting weakens as the wall moves into them)."""
+    g, p, init = synth.offset_slug(theta, delta)
+    from paper_2512_01032_gb300 import pflb
+    L = pflb.Lattice(g.nx, g.ny, g.nz, solid=g.solid, wall_normal=g.normals(),
+                     theta_cells=g.theta(), storage="fp32", solid_frac=g.solid_frac(), **p)
+    L.init_tanh(init["shape"], init["center"], init["R"], init["normal"])
+    L.step(20000)
+    d = L.diag()
+    assert d["nonfinite"] == 0 and d["u_max"] < 5e-3
+    H = g.ny - 2
+    got = _slug_angle(L.read("phi").reshape(g.nz, g.ny, g.nx)[0], 0.5 + delta,
+                      H + 0.5 - delta, g.nx)
+    print("OFFSET", theta, delta, "angle", got, "u_max", d["u_max"])
+    assert (got - 90.0) * (theta - 90.0) > 0
+    if theta in (60.0, 120.0):
+        assert abs(got - theta) < 8.0, got

@@ -1,10 +1,10 @@
-"""Reduced-precision population storage (FP16 and BF16 weight-scaled
-deviations, FP32 arithmetic) against the FP64 oracle.
+"""Reduced-precision population storage (FP16 weight-scaled, BF16 as is,
+FP32 arithmetic) against the FP64 oracle.
 
 Pointwise bound after n steps, derived from the formats: h_i / w_i lies in
-about [0, 1], where FP16 spacing is at most 2^-11 and BF16 spacing 2^-8, so
-each stored moving h_i is off by at most w_i 2^-12 (FP16) or w_i 2^-9
-(BF16); a cell's phi collects those of its 18 incoming populations and the
+about [0, 1], where FP16 spacing is at most 2^-11, and BF16's relative
+spacing is 2^-8 at any magnitude, so each stored moving h_i is off by at
+most w_i 2^-12 (FP16) or w_i 2^-9 (BF16); a cell's phi collects those of its 18 incoming populations and the
 compensation of its own outgoing ones (rest population), at most
 2 (1 - w_0) 2^-12 = 3.3e-4 (FP16) or 2.6e-3 (BF16) per step; the test allows
 n times that.  Total phi is conserved (mass-conserving rounding of h).
