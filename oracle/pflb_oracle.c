@@ -25,7 +25,11 @@
  *       (g_eq of Eq. 6); Pi = sum_l c_l c_l (g_l - g_eq_l), full tensor.
  *   R3  Per-step order: phi -> wall ghosts -> stencils -> macros -> collide
  *       -> stream; u in h_eq is the same step's hydrodynamic velocity.
- *   R4  "Delta phi" in delta-theta is the CD Laplacian; s = lap/|lap+eps|.
+ *   R4  "Delta phi" in delta-theta is the CD Laplacian; s = lap/(|lap|+eps),
+ *       a sign of the Laplacian regularised by eps.  Printed literally,
+ *       lap/|lap+eps| divides by zero at lap = -eps (the pole that eps is
+ *       said to avoid) and leaves [-1, 1] near it; the two agree to eps/|lap|
+ *       wherever |lap| >> eps.
  *   R5  n (interface normal) and n_w (wall normal, into the fluid) differ.
  *   R6  phi_smpl = phi of the wall node itself; one ghost per solid link.
  *   R8  If the tangential part of grad(phi) at the wall has norm < 1e-10,
@@ -221,7 +225,7 @@ double orc_delta_theta(const orc_params *p, double phi, const double grad[3], do
     double F2b = clamp01(-(phi - p->phi_m) / p->D);
     double Y1 = F1a < F1b ? F1a : F1b;
     double Y2 = F2a < F2b ? F2a : F2b;
-    double s = lap / fabs(lap + p->eps);
+    double s = lap / (fabs(lap) + p->eps);
     double gnorm = sqrt(grad[0] * grad[0] + grad[1] * grad[1] + grad[2] * grad[2]);
     return p->gamma * p->M / (TT * p->W) * gnorm * ((1.0 + s) * Y1 + (1.0 - s) * Y2);
 }

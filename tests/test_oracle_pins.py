@@ -131,6 +131,40 @@ def test_delta_theta_hand_values():
         assert abs(got - case["expect"]) < 1e-9, case
 
 
+def test_delta_theta_sign_switch_is_bounded():
+    """Reading R4 of Eq. 4: the switch Delta phi / (|Delta phi| + eps) is a
+    sign of the Laplacian regularised by eps, bounded by 1 in magnitude and
+    odd in Delta phi, so delta-theta never exceeds the correction's full
+    strength |gamma| M / (T W) |grad phi| * 2 max(Y1, Y2).  The printed
+    Delta phi / |Delta phi + eps| has a pole at Delta phi = -eps, right where
+    the text says eps avoids a division by zero; on either side of it the
+    two forms agree once |Delta phi| >> eps."""
+    p = _params()
+    grad = np.array([0.06, 0.0, 0.08])  # |grad phi| = 0.1
+    full = abs(p.gamma) * p.M / ((1.0 / 3.0) * p.W) * 0.1 * 2.0
+    eps = p.eps
+    for phi in (0.00005, 0.1, 0.19999, 0.9, 0.99995):
+        for lap in (-eps, -eps * (1 + 1e-12), -eps * (1 - 1e-12), -2 * eps, -0.5 * eps, 0.0,
+                    eps, 1e-3, -1e-3):
+            d = O.delta_theta(p, phi, grad, lap)
+            assert np.isfinite(d) and abs(d) <= full * (1 + 1e-12), (phi, lap, d)
+        # at Delta phi = 0 the switch is 0: Y1 and Y2 weigh equally
+        F = lambda x: max(0.0, min(1.0, x))  # noqa: E731
+        y1 = min(F((phi - p.phi_M) / p.D), F(-(phi - 1.0) / p.D))
+        y2 = min(F(phi / p.D), F(-(phi - p.phi_m) / p.D))
+        want0 = p.gamma * p.M / ((1.0 / 3.0) * p.W) * 0.1 * (y1 + y2)
+        assert abs(O.delta_theta(p, phi, grad, 0.0) - want0) < 1e-15
+        # odd switch: d(+L) + d(-L) = 2 x the value at 0 for any L
+        for lap in (0.3 * eps, eps, 7 * eps, 1e-4):
+            dp, dm = O.delta_theta(p, phi, grad, lap), O.delta_theta(p, phi, grad, -lap)
+            assert abs(dp + dm - 2 * want0) < 1e-15, (phi, lap)
+        # far from zero the switch is +-1 to eps / |Delta phi|
+        for lap in (1e-3, -1e-3):
+            sgn = 1.0 if lap > 0 else -1.0
+            want = p.gamma * p.M / ((1.0 / 3.0) * p.W) * 0.1 * ((1 + sgn) * y1 + (1 - sgn) * y2)
+            assert abs(O.delta_theta(p, phi, grad, lap) - want) <= full * eps / abs(lap)
+
+
 def test_recovery_makes_nonequilibrium_moment_free():
     """Reading R2 pinned by an exact invariant: with P and rho u recovered
     as the text after Eq. 11 states, sum (g - g_eq) = 0 and
