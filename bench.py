@@ -52,7 +52,8 @@ KERNEL_SOURCES = ("pflb_kernels.cuh", "pflb_model.cuh", "pflb_launch.cuh", "pflb
 KERNEL_NAMES = {0: "k_fused", 1: "k_phi + k_cell", 2: "k_fused_async", 3: "k_pipe"}
 KERNEL_TEXT = {0: "fused z-marching, direct loads", 1: "phi pass + per-cell pass",
                2: "fused z-marching, h staged by TMA",
-               3: "fused z-marching, populations staged one plane ahead by cp.async"}
+               3: "fused z-marching, populations staged one plane ahead by cp.async, "
+                  "each block's wall nodes after its march"}
 ORACLE_KEYS = ("sigma", "W", "M", "rho_H", "rho_L", "nu_H", "nu_L", "theta_deg", "Fex", "blend",
                "F_mode", "mobility_corr", "free_slip")
 
@@ -648,8 +649,9 @@ def main(argv=None):
     value = world * fluid * args.steps / (ms * 1e-3) / 1e6
 
     launch = L.get_kernel()
-    # the pipelined kernel leaves wall nodes to a second launch (k_wall)
-    launches_per_step = 2 if launch["kind"] == 3 and g.wall_nodes3().any() else 1
+    # one launch per step: the pipelined kernel updates each block's wall
+    # nodes after its march (per-block lists built for the launch shape)
+    launches_per_step = 1
     peak, peak_kind = hbm_peak()
     achieved = fluid * ALGO_BYTES_FP32 / (ms_step * 1e-3) / 1e9
     traffic = recorded_traffic(KERNEL_NAMES.get(launch["kind"], ""))

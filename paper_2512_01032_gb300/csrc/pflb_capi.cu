@@ -134,6 +134,45 @@ int resolve_lz(Lattice *L) {
   });
 }
 
+// Per-block wall lists of the pipelined kernel for the lz in effect: wall
+// records grouped by the block (32 x 4 tile, chunk of lz planes) whose march
+// covers their cell, in the kernel's block numbering (x, then y, then the z
+// chunks alternating from both ends: chunk c < ceil(n/2) is block row 2c,
+// the others 2 (n - 1 - c) + 1).  Copied on stream st (the lattice's
+// stream once created, so that steps queued before use the previous lists);
+// copies from pageable memory have read the host vectors on return.
+cudaError_t ensure_wall_lists(Lattice *L, cudaStream_t st) {
+  if (!L->wl || L->nw == 0 || L->wl_lz == L->lz || !pflb::pipe_layout_ok(*L)) return cudaSuccess;
+  const int lz = L->lz, gx = (L->nx + 31) / 32, gy = (L->ny + 3) / 4;
+  const int nch = (L->nz + lz - 1) / lz;
+  const size_t nb = (size_t)gx * gy * nch;
+  std::vector<int> start(nb + 1, 0), list((size_t)L->nw), blk((size_t)L->nw);
+  const long long sxy = (long long)L->nx * L->ny;
+  for (int r = 0; r < L->nw; ++r) {
+    const long long c = L->wcell_h[(size_t)r];
+    const int x = (int)(c % L->nx), y = (int)((c / L->nx) % L->ny), z = (int)(c / sxy);
+    const int ch = z / lz;
+    const int bz = ch < (nch + 1) / 2 ? 2 * ch : 2 * (nch - 1 - ch) + 1;
+    blk[(size_t)r] = x / 32 + gx * (y / 4 + gy * bz);
+    ++start[(size_t)blk[(size_t)r] + 1];
+  }
+  for (size_t b = 0; b < nb; ++b) start[b + 1] += start[b];
+  std::vector<int> fill(start.begin(), start.end() - 1);
+  for (int r = 0; r < L->nw; ++r) list[(size_t)fill[(size_t)blk[(size_t)r]]++] = r;
+  cudaError_t e = cudaMemcpyAsync(L->wl, list.data(), list.size() * sizeof(int),
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(L->wl_start, start.data(), start.size() * sizeof(int),
+                        cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) L->wl_lz = lz;
+  return e;
+}
+
+// Blocks of the pipelined grid at one plane per block (the size of wl_start).
+size_t wall_list_blocks(long long nx, long long ny, long long nz) {
+  return (size_t)(((nx + 31) / 32) * ((ny + 3) / 4) * nz);
+}
+
 pflb_status check_lattice(const pflb_lattice *L) {
   if (!L) return fail(PFLB_ERR_ARG, "null lattice");
   if (L->poisoned) return fail(PFLB_ERR_STATE, "lattice poisoned by an earlier CUDA error");
@@ -366,7 +405,7 @@ cudaError_t dev_alloc(Lattice *L, T **ptr, size_t count) {
 void free_all(Lattice *L) {
   void *ptrs[] = {L->h[0], L->h[1], L->g, L->wp[0], L->wp[1], L->flags, L->widx, L->wmask,
                   L->wgeo, L->ghost, L->phi, L->diag, L->out, L->phi0, L->err, L->bcm,
-                  L->wcell, L->wcut, L->sfrac};
+                  L->wcell, L->wcut, L->sfrac, L->wl, L->wl_start};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (L->aux) cudaStreamDestroy(L->aux);
@@ -377,12 +416,15 @@ void free_all(Lattice *L) {
   L->ev_init = nullptr;
 }
 
-int64_t bytes_for(long long N, long long nw, int storage, bool has_cut = false) {
+int64_t bytes_for(long long nx, long long ny, long long nz, long long nw, int storage,
+                  bool has_cut = false) {
+  const long long N = nx * ny * nz;
   const int64_t e = (int64_t)storage_bytes(storage);
   const int64_t r = (int64_t)compute_bytes(storage);
   const int64_t flag_bytes = (N + 3) & ~(int64_t)3;  // whole 4-byte words
+  const int64_t lists = nw ? nw * 4 + ((int64_t)wall_list_blocks(nx, ny, nz) + 1) * 4 : 0;
   return (2 * (int64_t)h_slots_of(storage) + 19) * N * e + 2 * 18 * nw * e + flag_bytes +
-         N * 4 + nw * 8 + 5 * nw * r + 18 * nw * r + N * r + 96 * 8 + 4 +
+         N * 4 + nw * 8 + 5 * nw * r + 18 * nw * r + N * r + 96 * 8 + 4 + lists +
          (has_cut ? nw * 4 + N * r : 0);
 }
 
@@ -518,6 +560,10 @@ pflb_status pflb_create(const pflb_geometry *geom, const pflb_params *params, vo
   }
   A(&L->ghost, 18 * nw * Rb);
   A(&L->phi, N * Rb);
+  if (nw) {
+    A((void **)&L->wl, nw * sizeof(int));
+    A((void **)&L->wl_start, (wall_list_blocks(L->nx, L->ny, L->nz) + 1) * sizeof(int));
+  }
   A((void **)&L->diag, 96 * sizeof(double));
   A((void **)&L->err, sizeof(int));
   if (e != cudaSuccess) {
@@ -577,6 +623,14 @@ pflb_status pflb_create(const pflb_geometry *geom, const pflb_params *params, vo
   }
   make_tmaps(L);
   L->lz = resolve_lz(L);
+  L->wcell_h.swap(hg.wcell);
+  e = ensure_wall_lists(L, L->aux);  // nothing on the lattice's stream reads them yet
+  if (e == cudaSuccess) e = cudaStreamSynchronize(L->aux);
+  if (e != cudaSuccess) {
+    free_all(L);
+    delete L;
+    return fail(PFLB_ERR_CUDA, std::string("upload failed: ") + cudaGetErrorString(e));
+  }
   *out = L;
   return PFLB_OK;
 }
@@ -689,6 +743,7 @@ pflb_status pflb_set_kernel(pflb_lattice *L, int kind, int bx, int by, int lz) {
   if (lz > 0) L->lz_req = lz;
   if (lz == -1) L->lz_req = 0;
   L->lz = resolve_lz(L);
+  CK(L, ensure_wall_lists(L, L->stream));
   return PFLB_OK;
 }
 
@@ -742,6 +797,7 @@ pflb_status pflb_set_x_boundaries(pflb_lattice *L, const pflb_xbc *lo, const pfl
   }
   L->bc_on = on;
   L->lz = resolve_lz(L);  // the TMA kernel is not used with open boundaries
+  CK(L, ensure_wall_lists(L, L->stream));
   return PFLB_OK;
 }
 
@@ -931,7 +987,7 @@ int64_t pflb_estimate_bytes(const pflb_geometry *geom, int storage) {
     nw += (all[(size_t)c] | cut[(size_t)c]) != 0;
     has_cut = has_cut || (geom->solid_frac && !geom->solid[c] && geom->solid_frac[c] > 0.0);
   }
-  return bytes_for(N, nw, storage, has_cut);
+  return bytes_for(geom->nx, geom->ny, geom->nz, nw, storage, has_cut);
 }
 
 static const char kMagic[8] = {'P', 'F', 'L', 'B', 'C', 'K', 'P', '1'};

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "../../include/pflb.h"
 
@@ -57,6 +58,12 @@ struct Lattice {
   int64_t bc_t0 = 0, bc_ramp = 0;  // ramp start step and length
   void *bcm = nullptr;             // [5][2 ny nz] boundary states, compute type
   int reg[6] = {0, 0, 0, 0, 0, 0};
+  // per-block wall lists of the pipelined kernel (wall records grouped by
+  // the 32 x 4 x lz block whose march covers them), built for lz = wl_lz
+  int *wl = nullptr;               // [nw]
+  int *wl_start = nullptr;         // [blocks + 1], sized for lz = 1
+  int wl_lz = 0;
+  std::vector<int> wcell_h;        // host copy of wcell
   bool poisoned = false;
   int64_t dev_bytes = 0;
 };

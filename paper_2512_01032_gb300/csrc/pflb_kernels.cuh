@@ -25,6 +25,10 @@
 namespace pflb {
 
 enum { MODE_STEP = 0, MODE_MACRO = 1 };
+// Collision forms: per direction (collide), per opposite pair
+// (collide_pairs), pairs in packed FP32 lanes with and without the body
+// force terms (collide_pairs_x2; FP32 arithmetic only, else collide_pairs).
+enum { COLL_PLAIN = 0, COLL_PAIRS = 1, COLL_X2 = 2, COLL_X2_NOF = 3 };
 
 // Blocks of 256 threads per SM the batch kernel is compiled for (sets its
 // register cap: 128).
@@ -67,6 +71,10 @@ struct Args {
   double *out;       // macro outputs [6][N] (phi, rho, P, ux, uy, uz) or null
   R *bcm;            // open x boundaries: states [5][nbc] (phi, P, ux, uy, uz), or null
   int nbc;           // 2 ny nz: plane x = 0, then plane x = nx-1
+  // pipelined kernel: wall records grouped by the block whose march covers
+  // them (block b owns wl[wl_start[b] .. wl_start[b + 1])), or null
+  const int *wl;
+  const int *wl_start;
 };
 
 // Index of the boundary state of a cell in plane x = 0 or x = nx-1.
@@ -187,7 +195,7 @@ __device__ __forceinline__ void boundary_cell(const Args<S, R> &a, int x, int y,
 // once its populations are gathered: h[] and g[] hold the streamed
 // populations, phi = sum h, val[1..18] the phi of the 18 neighbours
 // (anything for solid ones), lm/rec the wall data (0 for bulk cells).
-template <class S, class R, bool ODD, int MODE, bool DIAG, bool XBC = false, bool PAIRS = false>
+template <class S, class R, bool ODD, int MODE, bool DIAG, bool XBC = false, int PAIRS = COLL_PLAIN>
 __device__ __forceinline__ void finish_cell(const Args<S, R> &a, int x, int y, int z, int c,
                                             uint8_t f, uint32_t lm, int rec, const Nbr &nb,
                                             R h[Q], R g[Q], R phi, R val[Q], DiagAcc<R> &acc) {
@@ -263,14 +271,21 @@ __device__ __forceinline__ void finish_cell(const Args<S, R> &a, int x, int y, i
         }
     }
   }
-  cd_stencil(val, gx, gy, gz, lap);
+  if constexpr (PAIRS >= COLL_X2 && std::is_same<R, float>::value)
+    cd_stencil_x2(val, gx, gy, gz, lap);
+  else
+    cd_stencil(val, gx, gy, gz, lap);
   if (wall) {
     gx += cgx;
     gy += cgy;
     gz += cgz;
     lap += clap;
   }
-  const Macro<R> mc = macros(m, g, phi, gx, gy, gz, lap);
+  Macro<R> mc;
+  if constexpr (PAIRS >= COLL_X2 && std::is_same<R, float>::value)
+    mc = macros_x2(m, g, phi, gx, gy, gz, lap);
+  else
+    mc = macros(m, g, phi, gx, gy, gz, lap);
 
   if (DIAG) {
     acc.v[D_MASS] += phi;
@@ -317,7 +332,9 @@ __device__ __forceinline__ void finish_cell(const Args<S, R> &a, int x, int y, i
     return;
   }
 
-  if constexpr (PAIRS)
+  if constexpr (PAIRS >= COLL_X2 && std::is_same<R, float>::value)
+    collide_pairs_x2<PAIRS == COLL_X2>(m, h, g, mc, phi, gx, gy, gz, lap);
+  else if constexpr (PAIRS >= COLL_PAIRS)
     collide_pairs(m, h, g, mc, phi, gx, gy, gz, lap);
   else
     collide(m, h, g, mc, phi, gx, gy, gz, lap);
@@ -390,7 +407,7 @@ __device__ __forceinline__ void store_cell(const Args<S, R> &a, int c, uint32_t 
 
 // Full update (or macro evaluation) of one fluid cell: wall data, g
 // gather, then finish_cell.
-template <class S, class R, bool ODD, int MODE, bool DIAG, bool XBC = false, bool PAIRS = false>
+template <class S, class R, bool ODD, int MODE, bool DIAG, bool XBC = false, int PAIRS = COLL_PLAIN>
 __device__ __forceinline__ void update_cell(const Args<S, R> &a, int x, int y, int z, int c,
                                             uint8_t f, R h[Q], R phi, R val[Q],
                                             DiagAcc<R> &acc) {

@@ -79,6 +79,8 @@ static Args<S, R> make_args(Lattice &L) {
   a.out = nullptr;
   a.bcm = L.bc_on ? (R *)L.bcm : nullptr;
   a.nbc = 2 * L.ny * L.nz;
+  a.wl = nullptr;  // set by the pipelined launch when its lists are current
+  a.wl_start = nullptr;
   return a;
 }
 
@@ -153,7 +155,7 @@ constexpr bool pipe_storage() {
 inline bool pipe_eligible(const Lattice &L) { return pipe_kernel_runs(L); }
 
 // Dynamic shared memory above 48 KB is opted into once per device.
-template <class S, class R, bool ODD, bool DIAG>
+template <class S, class R, bool ODD, bool DIAG, bool FORCE>
 static cudaError_t pipe_attrs() {
   static unsigned long long done = 0;  // bit d: set on device d
   int dev = 0;
@@ -161,27 +163,40 @@ static cudaError_t pipe_attrs() {
   if (e != cudaSuccess) return e;
   const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
   if (bit && (done & bit)) return cudaSuccess;
-  e = cudaFuncSetAttribute(k_pipe<S, R, ODD, DIAG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sizeof(PipeSmem<S, R>));
+  e = cudaFuncSetAttribute(k_pipe<S, R, ODD, DIAG, FORCE>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PipeSmem<S, R>));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_pipe<S, R, ODD, DIAG>,
+  e = cudaFuncSetAttribute(k_pipe<S, R, ODD, DIAG, FORCE>,
                            cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
   done |= bit;
   return cudaSuccess;
 }
 
-template <class S, class R, bool ODD, bool DIAG>
-static cudaError_t launch_pipe_t(Lattice &L, Args<S, R> &a) {
-  cudaError_t e = pipe_attrs<S, R, ODD, DIAG>();
+template <class S, class R, bool ODD, bool DIAG, bool FORCE>
+static cudaError_t launch_pipe_f(Lattice &L, Args<S, R> &a) {
+  cudaError_t e = pipe_attrs<S, R, ODD, DIAG, FORCE>();
   if (e != cudaSuccess) return e;
   const dim3 grid((L.nx + PP_BX - 1) / PP_BX, (L.ny + PP_BY - 1) / PP_BY,
                   (L.nz + L.lz - 1) / L.lz);
-  k_pipe<S, R, ODD, DIAG><<<grid, PP_NT, sizeof(PipeSmem<S, R>), L.stream>>>(a);
+  // wall nodes inside the march when the per-block lists match the launch
+  // shape, else by k_wall after it
+  const bool inblock = L.nw > 0 && L.wl && L.wl_lz == L.lz;
+  a.wl = inblock ? L.wl : nullptr;
+  a.wl_start = inblock ? L.wl_start : nullptr;
+  k_pipe<S, R, ODD, DIAG, FORCE><<<grid, PP_NT, sizeof(PipeSmem<S, R>), L.stream>>>(a);
   e = cudaGetLastError();
-  if (e != cudaSuccess || L.nw == 0) return e;
+  if (e != cudaSuccess || L.nw == 0 || inblock) return e;
   k_wall<S, R, ODD, DIAG><<<(L.nw + 127) / 128, 128, 0, L.stream>>>(a);
   return cudaGetLastError();
+}
+
+// The variant without body-force terms when F_ex = 0 (they vanish there).
+template <class S, class R, bool ODD, bool DIAG>
+static cudaError_t launch_pipe_t(Lattice &L, Args<S, R> &a) {
+  if (a.m.Fx == R(0) && a.m.Fy == R(0) && a.m.Fz == R(0))
+    return launch_pipe_f<S, R, ODD, DIAG, false>(L, a);
+  return launch_pipe_f<S, R, ODD, DIAG, true>(L, a);
 }
 
 template <class S, class R, bool ODD, bool DIAG>
@@ -238,10 +253,10 @@ int auto_lz(const Lattice &L) {
   if (e == cudaSuccess) {
     if (pipe) {
       if constexpr (pipe_storage<S>()) {
-        e = pipe_attrs<S, R, false, true>();
+        e = pipe_attrs<S, R, false, true, true>();
         if (e == cudaSuccess)
-          e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pipe<S, R, false, true>, PP_NT,
-                                                            sizeof(PipeSmem<S, R>));
+          e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+              &per, k_pipe<S, R, false, true, true>, PP_NT, sizeof(PipeSmem<S, R>));
       }
     } else if (tma) {
       if constexpr (std::is_same<S, float>::value && std::is_same<R, float>::value) {

@@ -16,6 +16,8 @@
 // Populations: h = phase field, g = hydrodynamic (the paper's g-bar).
 #pragma once
 #include <cstdint>
+#include <cstring>
+#include <type_traits>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -352,7 +354,7 @@ template <class R>
 __device__ __forceinline__ R delta_theta(const Model<R> &m, R phi, R gnorm, R lap) {
   R Y1 = fminf_(clamp01_((phi - m.phi_M) * m.inv_D), clamp01_((R(1) - phi) * m.inv_D));
   R Y2 = fminf_(clamp01_(phi * m.inv_D), clamp01_((m.phi_m - phi) * m.inv_D));
-  R s = div_(lap, abs_(lap + m.eps));
+  R s = div_(lap, abs_(lap) + m.eps);  // reading R4: the sign of lap, regularised
   return m.gamma * m.theta_coef * gnorm * ((R(1) + s) * Y1 + (R(1) - s) * Y2);
 }
 
@@ -532,6 +534,224 @@ __device__ __forceinline__ void collide_pairs(const Model<R> &m, R h[Q], R g[Q],
     g[i] += d;
     g[i + 1] += d;
   }
+}
+
+// ------------------------------------------------------------ packed FP32
+// Blackwell issues two FP32 operations on a float2 register pair as one
+// instruction (add / sub / mul / fma .f32x2, each lane rounded exactly as
+// its scalar form).  collide_pairs_x2 is collide_pairs with two opposite
+// pairs in the two lanes: (+x, +y), (+x+y, +x-y), (+x+z, +x-z),
+// (+y+z, +y-z); the +z pair stays scalar.  Within a lane the operations
+// are collide_pairs' with the weight w_i factored out of K_i, E_i and the
+// blends until the populations are formed, so the results agree with
+// collide_pairs to rounding.  The step is issue-bound (instruction issue,
+// not DRAM, limits it), so halving the issued arithmetic instructions is
+// what pays.  FORCE = false drops the terms of the body force; the host
+// chooses it only when F_ex = 0, where those terms vanish identically.
+__device__ __forceinline__ float2 f2_(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ float2 bc_(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 add2_(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2_(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2_(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2_(float2 a, float2 b) {
+  unsigned long long A, B, D;
+  memcpy(&A, &a, 8);
+  memcpy(&B, &b, 8);
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(D) : "l"(A), "l"(B));
+  float2 d;
+  memcpy(&d, &D, 8);
+  return d;
+}
+
+// Dot product of c_i with (x, y, z) for a compile-time direction i.
+template <int I>
+__device__ __forceinline__ float cdot_(float x, float y, float z) {
+  float r = 0.0f;
+  bool any = false;
+  if (cx_of(I) != 0) { r = cx_of(I) > 0 ? x : -x; any = true; }
+  if (cy_of(I) != 0) { r = any ? (cy_of(I) > 0 ? r + y : r - y) : (cy_of(I) > 0 ? y : -y); any = true; }
+  if (cz_of(I) != 0) { r = any ? (cz_of(I) > 0 ? r + z : r - z) : (cz_of(I) > 0 ? z : -z); }
+  return r;
+}
+
+// Shared per-cell terms of the packed collision, as lane pairs.
+struct X2Cell {
+  float2 M0, AL, AL3, MUT, NUG, P3, RHO, RHO3, OM, HALF;
+  float2 NUF3, NUF9;  // -3 u.F, -9 u.F (FORCE)
+};
+
+// Eq. 13 (cd_stencil) with the opposite pairs' differences and sums of the
+// (+x, +y), (+x+y, +x-y), (+x+z, +x-z), (+y+z, +y-z) pairs in packed lanes.
+__device__ __forceinline__ void cd_stencil_x2(const float v[Q], float &gx, float &gy, float &gz,
+                                              float &lap) {
+  const float a = 1.0f / 6.0f, b = 1.0f / 12.0f;
+  const float2 iA = f2_(v[1], v[3]), jA = f2_(v[2], v[4]), iB = f2_(v[7], v[9]),
+               jB = f2_(v[8], v[10]), iC = f2_(v[11], v[13]), jC = f2_(v[12], v[14]),
+               iD = f2_(v[15], v[17]), jD = f2_(v[16], v[18]);
+  const float2 dA = sub2_(iA, jA), dB = sub2_(iB, jB), dC = sub2_(iC, jC), dD = sub2_(iD, jD);
+  gx = a * dA.x + b * ((dB.x + dB.y) + (dC.x + dC.y));
+  gy = a * dA.y + b * ((dB.x - dB.y) + (dD.x + dD.y));
+  gz = a * (v[5] - v[6]) + b * ((dC.x - dC.y) + (dD.x - dD.y));
+  const float2 sA = add2_(iA, jA);
+  const float2 sE = add2_(add2_(add2_(iB, jB), add2_(iC, jC)), add2_(iD, jD));
+  const float sf = (sA.x + sA.y) + (v[5] + v[6]), se = sE.x + sE.y;
+  lap = 6.0f * ((1.0f / 18.0f) * sf + (1.0f / 36.0f) * se - (2.0f / 3.0f) * v[0]);
+}
+
+// macros() with the moment sums of g taken over packed opposite pairs.
+__device__ __forceinline__ Macro<float> macros_x2(const Model<float> &m, const float g[Q],
+                                                  float phi, float gx, float gy, float gz,
+                                                  float lap) {
+  Macro<float> r;
+  r.rho = m.rho_L + phi * m.rho_dif;
+  r.mu = m.mu_a * phi * (phi - 1.0f) * (phi - 0.5f) - m.mu_b * lap;
+  const float2 iA = f2_(g[1], g[3]), jA = f2_(g[2], g[4]), iB = f2_(g[7], g[9]),
+               jB = f2_(g[8], g[10]), iC = f2_(g[11], g[13]), jC = f2_(g[12], g[14]),
+               iD = f2_(g[15], g[17]), jD = f2_(g[16], g[18]);
+  const float2 dA = sub2_(iA, jA), dB = sub2_(iB, jB), dC = sub2_(iC, jC), dD = sub2_(iD, jD);
+  const float2 s2 = add2_(add2_(add2_(iA, jA), add2_(iB, jB)), add2_(add2_(iC, jC), add2_(iD, jD)));
+  const float s = (s2.x + s2.y) + (g[0] + (g[5] + g[6]));
+  const float jx = dA.x + ((dB.x + dB.y) + (dC.x + dC.y));
+  const float jy = dA.y + ((dB.x - dB.y) + (dD.x + dD.y));
+  const float jz = (g[5] - g[6]) + ((dC.x - dC.y) + (dD.x - dD.y));
+  const float irho = div_(1.0f, r.rho);
+  r.ux = (jx + 0.5f * (r.mu * gx + m.Fx)) * irho;
+  r.uy = (jy + 0.5f * (r.mu * gy + m.Fy)) * irho;
+  r.uz = (jz + 0.5f * (r.mu * gz + m.Fz)) * irho;
+  const float ug = r.ux * gx + r.uy * gy + r.uz * gz;
+  r.P = (1.0f / 3.0f) * s + (0.5f / 3.0f) * m.rho_dif * ug;
+  return r;
+}
+
+// One packed group: lanes I and K (odd directions), opposites I + 1, K + 1,
+// weight w (the same for both lanes).  Returns the pair's non-equilibrium
+// sums (lane I, lane K) for Pi; h[] and g[] are updated in place and the
+// moved h are subtracted from rest.
+template <int I, int K, bool FORCE>
+__device__ __forceinline__ float2 x2_group(const X2Cell &c, const Model<float> &m, float h[Q],
+                                           float g[Q], float ux, float uy, float uz, float gx,
+                                           float gy, float gz, float2 WPHI, float2 W3PHI,
+                                           float2 WTHN, float2 W, float2 NW, float2 &rest) {
+  const float2 a = f2_(cdot_<I>(ux, uy, uz), cdot_<K>(ux, uy, uz));
+  const float2 cg = f2_(cdot_<I>(gx, gy, gz), cdot_<K>(gx, gy, gz));
+  const float2 mm = fma2_(mul2_(a, bc_(4.5f)), a, c.M0);  // s - 1
+  // h (Eqs. 1-2): h_eq = w phi s +- w (3 phi a + theta n . c)
+  const float2 HS = fma2_(mm, WPHI, WPHI);
+  const float2 HA = fma2_(a, W3PHI, mul2_(cg, WTHN));
+  float2 hi = f2_(h[I], h[K]), hj = f2_(h[I + 1], h[K + 1]);
+  hi = fma2_(c.OM, sub2_(add2_(HS, HA), hi), hi);
+  hj = fma2_(c.OM, sub2_(sub2_(HS, HA), hj), hj);
+  rest = sub2_(rest, add2_(hi, hj));
+  h[I] = hi.x; h[K] = hi.y; h[I + 1] = hj.x; h[K + 1] = hj.y;
+  // g (Eqs. 5-6, reading R2 of Eqs. 9-11), all divided by w
+  const float2 B = fma2_(mm, c.AL, c.MUT);
+  const float2 C = mul2_(a, c.AL3);
+  float2 KS = fma2_(C, cg, mul2_(B, c.NUG));
+  float2 KA = fma2_(B, cg, mul2_(C, c.NUG));
+  if constexpr (FORCE) {
+    const float2 cF = f2_(cdot_<I>(m.Fx, m.Fy, m.Fz), cdot_<K>(m.Fx, m.Fy, m.Fz));
+    const float2 s = add2_(mm, bc_(1.0f));
+    KS = fma2_(s, c.NUF3, fma2_(mul2_(a, bc_(9.0f)), cF, KS));
+    KA = fma2_(a, c.NUF9, fma2_(mul2_(s, bc_(3.0f)), cF, KA));
+  }
+  const float2 ES = fma2_(c.RHO, mm, c.P3), EA = mul2_(c.RHO3, a);
+  const float2 BS = fma2_(c.HALF, KS, ES), BA = fma2_(c.HALF, KA, EA);
+  const float2 gi = f2_(g[I], g[K]), gj = f2_(g[I + 1], g[K + 1]);
+  // non-equilibrium sum: (g_i + g_opp) - w (2 E_S - K_S)
+  const float2 nsum = fma2_(NW, sub2_(add2_(ES, ES), KS), add2_(gi, gj));
+  const float2 gni = mul2_(W, add2_(BS, BA)), gnj = mul2_(W, sub2_(BS, BA));
+  g[I] = gni.x; g[K] = gni.y; g[I + 1] = gnj.x; g[K + 1] = gnj.y;
+  return nsum;
+}
+
+// Filtered correction of a packed group: g_i and g_opp += f w_i cc_i.
+template <int I, int K>
+__device__ __forceinline__ void x2_filter(float g[Q], float2 cc, float2 FW) {
+  const float2 d = mul2_(FW, cc);
+  const float2 gi = add2_(f2_(g[I], g[K]), d), gj = add2_(f2_(g[I + 1], g[K + 1]), d);
+  g[I] = gi.x; g[K] = gi.y; g[I + 1] = gj.x; g[K + 1] = gj.y;
+}
+
+template <bool FORCE>
+__device__ __forceinline__ void collide_pairs_x2(const Model<float> &m, float h[Q], float g[Q],
+                                                 const Macro<float> &mc, float phi, float gx,
+                                                 float gy, float gz, float lap) {
+  const float ux = mc.ux, uy = mc.uy, uz = mc.uz;
+  const float gnorm = sqrt_(gx * gx + gy * gy + gz * gz);
+  const float inv = div_(1.0f, gnorm + m.eps);
+  float th = m.theta_coef * (1.0f - 4.0f * (phi - 0.5f) * (phi - 0.5f));
+  if (m.mobility_corr) th += delta_theta(m, phi, gnorm, lap);
+  const float thn = th * inv;  // theta n = thn grad phi
+  const float m0 = -1.5f * (ux * ux + uy * uy + uz * uz);
+  const float ug = ux * gx + uy * gy + uz * gz;
+  const float uF = FORCE ? ux * m.Fx + uy * m.Fy + uz * m.Fz : 0.0f;
+  const float muT = 3.0f * mc.mu, al = m.rho_dif + muT, P3 = 3.0f * mc.P, rho = mc.rho;
+  X2Cell c;
+  c.M0 = bc_(m0); c.AL = bc_(al); c.AL3 = bc_(3.0f * al); c.MUT = bc_(muT); c.NUG = bc_(-ug);
+  c.P3 = bc_(P3); c.RHO = bc_(rho); c.RHO3 = bc_(3.0f * rho); c.OM = bc_(m.inv_tau_phi);
+  c.HALF = bc_(0.5f);
+  if (FORCE) { c.NUF3 = bc_(-3.0f * uF); c.NUF9 = bc_(-9.0f * uF); }
+  constexpr float wf = 1.0f / 18.0f, we = 1.0f / 36.0f;
+  float2 rest = f2_(phi, 0.0f);
+  // faces (+x, +y)
+  const float2 nA = x2_group<1, 3, FORCE>(c, m, h, g, ux, uy, uz, gx, gy, gz, bc_(wf * phi),
+                                          bc_(3.0f * wf * phi), bc_(wf * thn), bc_(wf),
+                                          bc_(-wf), rest);
+  // edges
+  const float2 WPHI = bc_(we * phi), W3PHI = bc_(3.0f * we * phi), WTHN = bc_(we * thn);
+  const float2 W = bc_(we), NW = bc_(-we);
+  const float2 nB = x2_group<7, 9, FORCE>(c, m, h, g, ux, uy, uz, gx, gy, gz, WPHI, W3PHI, WTHN,
+                                          W, NW, rest);
+  const float2 nC = x2_group<11, 13, FORCE>(c, m, h, g, ux, uy, uz, gx, gy, gz, WPHI, W3PHI,
+                                            WTHN, W, NW, rest);
+  const float2 nD = x2_group<15, 17, FORCE>(c, m, h, g, ux, uy, uz, gx, gy, gz, WPHI, W3PHI,
+                                            WTHN, W, NW, rest);
+  // +z pair, scalar (collide_pairs' arithmetic)
+  float n5;
+  float rs = rest.x + rest.y;
+  {
+    const float a = uz, cgr = gz, mm = m0 + 4.5f * a * a;
+    const float HS = wf * (phi + phi * mm), HA = wf * (3.0f * phi * a + thn * cgr);
+    h[5] = h[5] + m.inv_tau_phi * ((HS + HA) - h[5]);
+    h[6] = h[6] + m.inv_tau_phi * ((HS - HA) - h[6]);
+    rs -= h[5] + h[6];
+    const float B = mm * al + muT, C = 3.0f * a * al;
+    float KS = C * cgr - B * ug, KA = B * cgr - C * ug;
+    if (FORCE) {
+      const float s = 1.0f + mm, cF = m.Fz;
+      KS += -s * 3.0f * uF + 9.0f * a * cF;
+      KA += 3.0f * s * cF - 9.0f * a * uF;
+    }
+    const float ES = P3 + rho * mm, EA = 3.0f * rho * a;
+    const float BS = ES + 0.5f * KS, BA = EA + 0.5f * KA;
+    n5 = (g[5] + g[6]) - wf * (2.0f * ES - KS);
+    g[5] = wf * (BS + BA);
+    g[6] = wf * (BS - BA);
+  }
+  h[0] = rs;
+  {  // rest direction: a = c . grad = c . F = 0
+    constexpr float w0 = 1.0f / 3.0f;
+    const float B = m0 * al + muT;
+    const float K0 = w0 * (-B * ug - (1.0f + m0) * 3.0f * uF);
+    g[0] = w0 * (P3 + rho * m0) + 0.5f * K0;
+  }
+  // Pi from the pairs' sums: (+x,+y) | (+x+y,+x-y) | (+x+z,+x-z) | (+y+z,+y-z) | +z
+  const float tB = nB.x + nB.y, tC = nC.x + nC.y, tD = nD.x + nD.y;
+  const float pxx = nA.x + tB + tC, pyy = nA.y + tB + tD, pzz = n5 + tC + tD;
+  const float pxy = nB.x - nB.y, pxz = nC.x - nC.y, pyz = nD.x - nD.y;
+  const float tau = tau_mix(m, phi);
+  const float f = (1.0f - div_(1.0f, tau)) * 4.5f;
+  const float tr3 = (pxx + pyy + pzz) * (1.0f / 3.0f);
+  g[0] = g[0] - (f * (1.0f / 3.0f)) * tr3;
+  const float2 FWf = bc_(f * wf), FWe = bc_(f * we);
+  x2_filter<1, 3>(g, f2_(pxx - tr3, pyy - tr3), FWf);
+  const float bxy = pxx + pyy - tr3, bxz = pxx + pzz - tr3, byz = pyy + pzz - tr3;
+  x2_filter<7, 9>(g, f2_(bxy + 2.0f * pxy, bxy - 2.0f * pxy), FWe);
+  x2_filter<11, 13>(g, f2_(bxz + 2.0f * pxz, bxz - 2.0f * pxz), FWe);
+  x2_filter<15, 17>(g, f2_(byz + 2.0f * pyz, byz - 2.0f * pyz), FWe);
+  const float d5 = (f * wf) * (pzz - tr3);
+  g[5] += d5;
+  g[6] += d5;
 }
 
 // h_eq (Eqs. 2-4) for initialisation.

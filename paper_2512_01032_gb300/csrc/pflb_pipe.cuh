@@ -26,10 +26,12 @@
 // wraps as a whole.  Rows and planes wrap individually.  Chunks whose cells
 // are all solid are not copied, using flag words staged one iteration
 // earlier still.  Wall nodes (a few percent of the cells; their update
-// reads wall records, ghosts and wall populations) are left to k_wall,
-// launched after this kernel: k_pipe writes the phi of the cells those
-// nodes read to the phi field.  16-bit storage stages the stored
-// values and decodes them when they are read.
+// reads wall records, ghosts and wall populations) are taken out of the
+// march: each block updates the wall nodes among its cells after its last
+// plane, from a per-block list, while the SM's other blocks keep marching
+// (the wall nodes' chains of dependent loads held whole blocks at the
+// plane barriers when they were updated in the march).  16-bit storage
+// stages the stored values and decodes them when they are read.
 //
 // Shared memory per block (FP32): h 2 planes x 19 x 6 rows x 40, g 19 x 4
 // rows x 40, flags 4 planes x 6 x 10 words, phi 4 planes x 34 x 6: 54 KB,
@@ -100,14 +102,81 @@ __device__ __forceinline__ bool chunk_solid(const uint32_t *flrow, int ch) {
   return solid;
 }
 
+// Update of wall node rec of lattice a (k_cell's per-cell step: populations,
+// wall records and wall populations loaded directly; the neighbours' phi from
+// the field the pipelined march wrote for exactly these reads; solid
+// neighbours replaced by the lagged ghosts).
+__device__ __forceinline__ void prefetch_l1(const void *p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+// A wall node's update is a chain of dependent loads (record -> cell ->
+// link mask -> sources).  With only a few warps per SM nothing hides it, so
+// every line the update will read is prefetched into L1 first, in two
+// rounds: what the record indexes, then what the cell indexes.
+template <class S, class R, bool ODD>
+__device__ __forceinline__ void wall_prefetch(const Args<S, R> &a, int rec) {
+  const int nw = a.nw;
+  prefetch_l1(a.wcell + rec);
+  prefetch_l1(a.wmask + rec);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) prefetch_l1(a.wgeo + (k * nw + rec));
+#pragma unroll
+  for (int i = 0; i < Q - 1; ++i) {
+    prefetch_l1(a.ghost + (i * nw + rec));
+    prefetch_l1(a.wp_rd + (i * nw + rec));
+  }
+  const int c = a.wcell[rec];
+  const int x = c % a.nx, y = (c / a.nx) % a.ny, z = c / (a.nx * a.ny);
+  Nbr nb;
+  nb.init(x, y, z, a.nx, a.ny, a.nz);
+  prefetch_l1(a.flags + c);
+  prefetch_l1(a.widx + c);
+#pragma unroll
+  for (int i = 0; i < h_slots<S>(); ++i) prefetch_l1(a.hin[i] + c);
+#pragma unroll
+  for (int i = 1; i < Q; ++i) prefetch_l1(a.phi_w + (c + nb.off(i)));
+#pragma unroll
+  for (int k = 0; k < Q; ++k)
+    prefetch_l1(ODD ? a.g[opp_of(k)] + (c + nb.off(opp_of(k))) : a.g[k] + c);
+}
+
+template <class S, class R, bool ODD, bool DIAG>
+__device__ __forceinline__ void wall_node(const Args<S, R> &a, int rec, DiagAcc<R> &acc) {
+  wall_prefetch<S, R, ODD>(a, rec);
+  const int c = a.wcell[rec];
+  const uint8_t f = a.flags[c];
+  const int x = c % a.nx, y = (c / a.nx) % a.ny, z = c / (a.nx * a.ny);
+  Nbr nb;
+  nb.init(x, y, z, a.nx, a.ny, a.nz);
+  R h[Q], val[Q];
+  ld_h_cell<S, R>(a.hin, c, h);
+  R phi = R(0);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) phi += h[i];
+  // the neighbours' phi from the field the march wrote in this launch
+  // (plain loads through the written pointer: never the read-only path)
+#pragma unroll
+  for (int i = 1; i < Q; ++i) val[i] = a.phi_w[c + nb.off(i)];
+  update_cell<S, R, ODD, MODE_STEP, DIAG, false, COLL_X2>(a, x, y, z, c, f, h, phi, val, acc);
+}
+
 // One tile column (x0, y0) over planes [zb, ze) of lattice a, by the whole
 // block (PP_NT threads), with shared memory sm and the warp slots wacc of
-// the diagnostics (flushed into a.diag at the end).  Every thread returns
-// with no copy in flight; the caller separates two marches that reuse sm
-// by a barrier.
-template <class S, class R, bool ODD, bool DIAG>
+// the diagnostics (flushed into a.diag at the end).  Wall records
+// a.wl[w0 .. w1) are the wall nodes among the march's cells: the block
+// updates them after the march (wall_node), from the phi of the cells
+// around them, which it writes to the phi field as it sums them (own and
+// ring cells of every plane it sums; only this block reads them before the
+// step ends, and a cell summed by two blocks gets the same bits from
+// both).  Without per-block lists (a.wl_start null) the march writes the
+// phi of its own cells in [zb, ze) that wall nodes read, for k_wall after
+// the launch.  Every thread returns with no copy in flight; the caller
+// separates two marches that reuse sm by a barrier.
+template <class S, class R, bool ODD, bool DIAG, bool FORCE>
 __device__ __forceinline__ void pipe_march(const Args<S, R> &a, int x0, int y0, int zb, int ze,
-                                           PipeSmem<S, R> &sm, R (*wacc)[32]) {
+                                           PipeSmem<S, R> &sm, R (*wacc)[32], int w0 = 0,
+                                           int w1 = 0) {
   using SM = PipeSmem<S, R>;
   constexpr int V = SM::V, NCH = SM::NCH, HS = SM::HS;
   static_assert(F_SOLID == 1, "all_solid tests bit 0");
@@ -139,6 +208,10 @@ __device__ __forceinline__ void pipe_march(const Args<S, R> &a, int x0, int y0, 
       ry = 1 + (k >> 1);
     }
   }
+  // phi field writes: 2 = own and ring cells of every summed plane (this
+  // block's wall nodes read them), 1 = own cells of [zb, ze) (k_wall reads
+  // them), 0 = none (block-uniform)
+  const int phimode = w1 > w0 ? 2 : (a.wl_start ? 0 : 1);
   // Plane wrap by additions: the planes touched lie within a few of [0, nz).
   auto wrapz = [nz](int zu) {
     while (zu < 0) zu += nz;
@@ -262,6 +335,7 @@ __device__ __forceinline__ void pipe_march(const Args<S, R> &a, int x0, int y0, 
     for (int i = 0; i < Q; ++i) v += h[i];
     return v;
   };
+  const int rcol = wrap(x0 - 1 + rx, nx) + nx * wrap(y0 - 1 + ry, ny);
   auto phi_plane = [&](int zu) {
     const S(*st)[PP_ROWS][SM::W] = sm.h[zu & 1];
     const uint32_t (*fl)[PP_FW] = sm.fl[zu & 3];
@@ -269,11 +343,16 @@ __device__ __forceinline__ void pipe_march(const Args<S, R> &a, int x0, int y0, 
     const uint8_t f = flag_byte(fl, ty + 1, tx);
     const R v = (f & F_SOLID) ? R(0) : staged_phi(st, ty + 1, V + tx);
     dst[(ty + 1) * PP_PW + tx + 1] = v;
-    // the cells whose phi a wall node reads go to the field for k_wall
-    if ((f & F_NEAR) && valid && zu >= zb && zu < ze) a.phi_w[col + sz * zu] = v;
-    if (ring)
-      dst[ry * PP_PW + rx] = (flag_byte(fl, ry, rx - 1) & F_SOLID) ? R(0)
-                                                                   : staged_phi(st, ry, V - 1 + rx);
+    // (a column beyond a ragged edge sums the cell it wraps to, which a
+    // wall node of the last valid column reads)
+    if ((f & F_NEAR) && (phimode == 2 || (phimode == 1 && valid && zu >= zb && zu < ze)))
+      a.phi_w[col + sz * wrapz(zu)] = v;
+    if (ring) {
+      const uint8_t fr = flag_byte(fl, ry, rx - 1);
+      const R vr = (fr & F_SOLID) ? R(0) : staged_phi(st, ry, V - 1 + rx);
+      dst[ry * PP_PW + rx] = vr;
+      if (phimode == 2 && (fr & F_NEAR)) a.phi_w[rcol + sz * wrapz(zu)] = vr;
+    }
   };
 
   DiagAcc<R> tot;
@@ -330,8 +409,8 @@ __device__ __forceinline__ void pipe_march(const Args<S, R> &a, int x0, int y0, 
       DiagAcc<R> acc;
       acc.zero();
       // a bulk cell: no wall flag, no solid link
-      finish_cell<S, R, ODD, MODE_STEP, DIAG, false, true>(a, cx0, cy0, z, c, 0, 0u, 0, nb, h, g,
-                                                           phi, val, acc);
+      finish_cell<S, R, ODD, MODE_STEP, DIAG, false, FORCE ? COLL_X2 : COLL_X2_NOF>(
+          a, cx0, cy0, z, c, 0, 0u, 0, nb, h, g, phi, val, acc);
       if (DIAG) {
 #pragma unroll
         for (int k = 0; k < D_UMAX; ++k) tot.v[k] += acc.v[k];
@@ -342,22 +421,50 @@ __device__ __forceinline__ void pipe_march(const Args<S, R> &a, int x0, int y0, 
     }
   }
   cp_async_wait_all();  // nothing is in flight at exit
+  if (w1 > w0) {  // this block's wall nodes
+    __syncthreads();  // the block's phi field writes are visible to all its threads
+    for (int k = w0 + tid; k < w1; k += PP_NT) {
+      DiagAcc<R> acc;
+      acc.zero();
+      wall_node<S, R, ODD, DIAG>(a, a.wl[k], acc);
+      if (DIAG) {
+#pragma unroll
+        for (int q = 0; q < D_UMAX; ++q) tot.v[q] += acc.v[q];
+        tot.umax = tot.umax > acc.umax ? tot.umax : acc.umax;
+        tot.front = tot.front > acc.front ? tot.front : acc.front;
+        tot.rear = tot.rear > acc.rear ? tot.rear : acc.rear;
+      }
+    }
+  }
   if (DIAG) {
     diag_warp_add(wacc[tid >> 5], tot);
     diag_block_flush(a.diag, wacc);
   }
 }
 
-// One lattice: a grid of (tile column, chunk of lz planes) blocks.
-template <class S, class R, bool ODD, bool DIAG>
+// One lattice: a grid of (tile column, chunk of lz planes) blocks.  FORCE
+// = false is the variant for a lattice without body force.
+template <class S, class R, bool ODD, bool DIAG, bool FORCE>
 __global__ void __launch_bounds__(PP_NT, PFLB_PIPE_MIN_BLOCKS)
     k_pipe(const __grid_constant__ Args<S, R> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ R wacc[DIAG_MAX_WARPS][32];
   zero_next_diag(a);
-  const int zb = blockIdx.z * a.lz;
-  pipe_march<S, R, ODD, DIAG>(a, blockIdx.x * PP_BX, blockIdx.y * PP_BY, zb, min(zb + a.lz, a.nz),
-                              *reinterpret_cast<PipeSmem<S, R> *>(smem_raw), wacc);
+  // z chunks alternate from both ends of the lattice (0, n-1, 1, n-2, ...)
+  // so that the chunks next to the bounding walls, whose blocks carry the
+  // most wall nodes, are dispatched early instead of last
+  const int nch = gridDim.z, bz = blockIdx.z;
+  const int zb = ((bz & 1) ? nch - 1 - (bz >> 1) : (bz >> 1)) * a.lz;
+  int w0 = 0, w1 = 0;
+  if (a.wl_start) {
+    const int b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * bz);
+    w0 = a.wl_start[b];
+    w1 = a.wl_start[b + 1];
+  }
+  pipe_march<S, R, ODD, DIAG, FORCE>(a, blockIdx.x * PP_BX, blockIdx.y * PP_BY, zb,
+                                     min(zb + a.lz, a.nz),
+                                     *reinterpret_cast<PipeSmem<S, R> *>(smem_raw), wacc, w0,
+                                     w1);
 }
 
 // Many lattices: a persistent grid pulls work items (lattice, x0, y0, z0)
@@ -403,75 +510,19 @@ __global__ void __launch_bounds__(PP_NT, 4)
     if (DIAG && it.y == 0 && it.z == 0 && it.w == 0 && tid < 32 && a.diag_zero)
       a.diag_zero[tid] = 0.0;
     const int ze = min(it.w + LZ, a.nz);
-    pipe_march<S, R, ODD, DIAG>(a, it.y, it.z, it.w, ze, sm, wacc);
+    pipe_march<S, R, ODD, DIAG, true>(a, it.y, it.z, it.w, ze, sm, wacc);
     __syncthreads();  // shared descriptor and staging buffers are reused by the next item
   }
 }
 
-// Update of wall node rec of lattice a (k_cell's per-cell step: populations,
-// wall records and wall populations loaded directly; the neighbours' phi from
-// the field the pipelined march wrote for exactly these reads; solid
-// neighbours replaced by the lagged ghosts).
-__device__ __forceinline__ void prefetch_l1(const void *p) {
-  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-}
-
-// A wall node's update is a chain of dependent loads (record -> cell ->
-// link mask -> sources).  With only a few warps per SM nothing hides it, so
-// every line the update will read is prefetched into L1 first, in two
-// rounds: what the record indexes, then what the cell indexes.
-template <class S, class R, bool ODD>
-__device__ __forceinline__ void wall_prefetch(const Args<S, R> &a, int rec) {
-  const int nw = a.nw;
-  prefetch_l1(a.wcell + rec);
-  prefetch_l1(a.wmask + rec);
-#pragma unroll
-  for (int k = 0; k < 5; ++k) prefetch_l1(a.wgeo + (k * nw + rec));
-#pragma unroll
-  for (int i = 0; i < Q - 1; ++i) {
-    prefetch_l1(a.ghost + (i * nw + rec));
-    prefetch_l1(a.wp_rd + (i * nw + rec));
-  }
-  const int c = a.wcell[rec];
-  const int x = c % a.nx, y = (c / a.nx) % a.ny, z = c / (a.nx * a.ny);
-  Nbr nb;
-  nb.init(x, y, z, a.nx, a.ny, a.nz);
-  prefetch_l1(a.flags + c);
-  prefetch_l1(a.widx + c);
-#pragma unroll
-  for (int i = 0; i < h_slots<S>(); ++i) prefetch_l1(a.hin[i] + c);
-#pragma unroll
-  for (int i = 1; i < Q; ++i) prefetch_l1(a.phi + (c + nb.off(i)));
-#pragma unroll
-  for (int k = 0; k < Q; ++k)
-    prefetch_l1(ODD ? a.g[opp_of(k)] + (c + nb.off(opp_of(k))) : a.g[k] + c);
-}
-
-template <class S, class R, bool ODD, bool DIAG>
-__device__ __forceinline__ void wall_node(const Args<S, R> &a, int rec, DiagAcc<R> &acc) {
-  wall_prefetch<S, R, ODD>(a, rec);
-  const int c = a.wcell[rec];
-  const uint8_t f = a.flags[c];
-  const int x = c % a.nx, y = (c / a.nx) % a.ny, z = c / (a.nx * a.ny);
-  Nbr nb;
-  nb.init(x, y, z, a.nx, a.ny, a.nz);
-  R h[Q], val[Q];
-  ld_h_cell<S, R>(a.hin, c, h);
-  R phi = R(0);
-#pragma unroll
-  for (int i = 0; i < Q; ++i) phi += h[i];
-#pragma unroll
-  for (int i = 1; i < Q; ++i) val[i] = a.phi[c + nb.off(i)];
-  update_cell<S, R, ODD, MODE_STEP, DIAG, false, true>(a, x, y, z, c, f, h, phi, val, acc);
-}
-
 // Wall nodes of a step whose bulk cells k_pipe updates, one thread per wall
-// node; it runs after k_pipe on the same stream.  The two kernels touch
-// disjoint data: under A-A every g slot is read and written by one cell,
-// h is pushed from each cell into slots no other cell writes, and only wall
-// nodes use the ghosts and wall populations.
+// node, launched after k_pipe on the same stream (used when the per-block
+// wall lists are not built for the launch shape in effect).  The two
+// kernels touch disjoint data: under A-A every g slot is read and written
+// by one cell, h is pushed from each cell into slots no other cell writes,
+// and only wall nodes use the ghosts and wall populations.
 template <class S, class R, bool ODD, bool DIAG>
-__global__ void __launch_bounds__(128) k_wall(const __grid_constant__ Args<S, R> a) {
+__global__ void __launch_bounds__(128, 4) k_wall(const __grid_constant__ Args<S, R> a) {
   __shared__ R wacc[DIAG_MAX_WARPS][32];
   if (DIAG) {
     diag_block_zero(wacc);

@@ -171,8 +171,11 @@ def test_estimate_bytes_counts_wall_nodes():
     assert empty == 3 * 19 * N * 4 + N * 5 + N * 4 + 96 * 8 + 4
     nw = 2 * n * n  # planes z = 1 and z = n-1 (periodic) touch the solid layer
     # per wall node: two wall-population buffers, link mask, cell index,
-    # geometry (5) and ghosts (18)
-    assert walled - empty == nw * (2 * 18 * 4 + 4 + 4 + 5 * 4 + 18 * 4)
+    # geometry (5), ghosts (18) and its slot in the pipelined kernel's
+    # per-block wall lists; plus the lists' block offsets (32 x 4 tiles,
+    # one plane per block: 1 x 4 x 16 blocks, and one more offset)
+    blocks = 1 * (n // 4) * n
+    assert walled - empty == nw * (2 * 18 * 4 + 4 + 4 + 5 * 4 + 18 * 4 + 4) + (blocks + 1) * 4
 
 
 def test_estimate_bytes_with_cut_cells():
@@ -188,7 +191,7 @@ def test_estimate_bytes_with_cut_cells():
     frac = np.zeros((n, n, n))
     frac[1] = 0.3  # the plane z = 1 is cut
     cut = pflb.estimate_bytes(n, n, n, solid, solid_frac=frac)
-    per_node = 2 * 18 * 4 + 4 + 4 + 5 * 4 + 18 * 4
+    per_node = 2 * 18 * 4 + 4 + 4 + 5 * 4 + 18 * 4 + 4
     # z = 2 joins the wall nodes (z = 1 and z = n - 1 already are)
     assert cut - walled == n * n * per_node + 3 * n * n * 4 + N * 4
     frac[1, 0, 0] = 1.0
