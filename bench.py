@@ -609,6 +609,10 @@ def main(argv=None):
         L.set_kernel(0, bx, by, lz)
     L.init_tanh(0, drop["center"], drop["R"])
     L.set_diag_every(1)
+    if not args.tile:
+        # planes per block: the library's autotuner times real steps of this
+        # lattice at a few depths and keeps the fastest (before the warm-up)
+        L.tune(50)
 
     # ---------------------------------------------- device-resident timing
     L.step(args.warmup)
@@ -667,6 +671,7 @@ def main(argv=None):
         phi0 = torch.empty(g.N, dtype=torch.float64, pin_memory=True).numpy()
         L2 = pflb.Lattice(g.nx, g.ny, g.nz, solid=g.solid, wall_normal=g.normals(),
                           theta_cells=g.theta(), stream=stream, storage="fp32", **p)
+        L2.set_kernel(launch["kind"], launch["bx"], launch["by"], launch["lz"])
         L2.init_tanh(0, drop["center"], drop["R"])
         phi0[:] = L2.read("phi")
         L2.set_diag_every(1)

@@ -69,9 +69,11 @@ enum { PFLB_FIELD_PHI = 0, PFLB_FIELD_RHO = 1, PFLB_FIELD_P = 2,
  * populations reach the arithmetic:
  *   PFLB_KERNEL_PIPE (default): the fused z-marching pass with each thread's
  *     populations of the next planes copied into shared memory one plane
- *     ahead (cp.async in 16-byte chunks), 32 x 4 tiles, pair form of the
- *     collision; periodic x and nx a multiple of 4 (of 8 at FP16/BF16
- *     storage), otherwise PFLB_KERNEL_FUSED runs;
+ *     ahead (cp.async in 16-byte chunks; 8-byte chunks at FP16/BF16 storage
+ *     when nx is not a multiple of 8), 32 x 4 tiles, pair form of the
+ *     collision, each block's wall nodes updated after its march (one
+ *     launch per step); periodic x and nx a multiple of 4, otherwise
+ *     PFLB_KERNEL_FUSED runs;
  *   PFLB_KERNEL_FUSED: one fused z-marching pass with direct loads;
  *   PFLB_KERNEL_TWOPASS: a phi pass followed by a per-cell pass;
  *   PFLB_KERNEL_FUSED_TMA: the fused pass with h staged through shared
@@ -248,6 +250,18 @@ pflb_status pflb_set_x_boundaries(pflb_lattice *L, const pflb_xbc *lo, const pfl
 /* The launch shape in effect: out = {kind, bx, by, lz}. */
 pflb_status pflb_get_kernel(const pflb_lattice *L, int out[4]);
 
+/* Autotuner of the planes per block (no counterpart in the paper: a launch
+ * parameter of this library's kernels).  For the kernel kind in effect it
+ * times trial_steps steps at each of a fixed set of depths (the automatic
+ * choice, 4, 6, 8, 10, 12, 16, 24, 32 planes, those not above nz) on the
+ * lattice itself, keeps the fastest (as pflb_set_kernel with that lz) and
+ * returns it in *lz_out if not NULL.  The trial steps are real steps: the
+ * lattice advances by (trial_steps + 1) per depth tried.  Results do not
+ * depend on the depth (the per-cell arithmetic is the same).  Synchronises
+ * the lattice stream; not for use inside stream capture.  Errors:
+ * PFLB_ERR_ARG (trial_steps < 1), PFLB_ERR_CUDA. */
+pflb_status pflb_tune(pflb_lattice *L, int trial_steps, int *lz_out);
+
 /* Advance nsteps time steps (asynchronous on the lattice stream). */
 pflb_status pflb_step(pflb_lattice *L, int64_t nsteps);
 
@@ -361,8 +375,8 @@ pflb_status pflb_fields_noalloc(int nx, int ny, int nz, const float *h_dev, cons
  * kernels: a grid of (SMs x blocks per SM) blocks pulls work items -- one
  * per (lattice, tile column, chunk of z planes) -- from a device work list,
  * so small lattices that could not fill the GPU on their own share it.
- * Lattices that PFLB_KERNEL_PIPE can run (periodic x, nx a multiple of 4, of
- * 8 at 16-bit storage) are marched by its pipelined per-cell code, 32 x 4
+ * Lattices that PFLB_KERNEL_PIPE can run (periodic x, nx a multiple of 4)
+ * are marched by its pipelined per-cell code, 32 x 4
  * tiles with an automatic number of planes, their wall nodes by a second
  * small kernel; the others by the fused tile march with the launch shape
  * below.  No work item reads another lattice, so a lattice's result does

@@ -801,6 +801,49 @@ pflb_status pflb_set_x_boundaries(pflb_lattice *L, const pflb_xbc *lo, const pfl
   return PFLB_OK;
 }
 
+pflb_status pflb_tune(pflb_lattice *L, int trial_steps, int *lz_out) {
+  pflb_status s = check_lattice(L);
+  if (s != PFLB_OK) return s;
+  if (trial_steps < 1) return fail(PFLB_ERR_ARG, "trial_steps must be >= 1");
+  static const int cand[] = {-1, 4, 6, 8, 10, 12, 16, 24, 32};
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  CK(L, cudaEventCreate(&t0));
+  cudaError_t e = cudaEventCreate(&t1);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(t0);
+    CK(L, e);
+  }
+  float best_ms = 1e30f;
+  int best = -1;
+  pflb_status st = PFLB_OK;
+  for (int c : cand) {
+    if (c > L->nz) continue;
+    st = pflb_set_kernel(L, L->kernel, L->bx, L->by, c);
+    if (st != PFLB_OK) break;
+    st = pflb_step(L, 1);  // the new depth's first launch (attributes, lists)
+    if (st != PFLB_OK) break;
+    e = cudaEventRecord(t0, L->stream);
+    if (e == cudaSuccess) st = pflb_step(L, trial_steps);
+    if (e == cudaSuccess && st == PFLB_OK) e = cudaEventRecord(t1, L->stream);
+    if (e == cudaSuccess && st == PFLB_OK) e = cudaEventSynchronize(t1);
+    float ms = 0.0f;
+    if (e == cudaSuccess && st == PFLB_OK) e = cudaEventElapsedTime(&ms, t0, t1);
+    if (e != cudaSuccess || st != PFLB_OK) break;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  if (st != PFLB_OK) return st;
+  CK(L, e);
+  st = pflb_set_kernel(L, L->kernel, L->bx, L->by, best);
+  if (st != PFLB_OK) return st;
+  if (lz_out) *lz_out = L->lz;
+  return PFLB_OK;
+}
+
 pflb_status pflb_get_kernel(const pflb_lattice *L, int out[4]) {
   pflb_status s = check_lattice(L);
   if (s != PFLB_OK) return s;
@@ -1147,21 +1190,30 @@ static pflb_status batch_build_pipe_items(pflb_batch *b) {
     }
   }
   b->dev.plz = best;
+  std::vector<int4> items8;  // lattices staged in 8-byte chunks
   for (int l = 0; l < (int)b->lats.size(); ++l) {
     if (!b->pipe_set[l]) continue;
     const Lattice *L = b->lats[l];
+    std::vector<int4> &dst = pflb::pipe_chunk_bytes(*L) == 8 ? items8 : items;
     for (int z0 = 0; z0 < L->nz; z0 += best)
       for (int y0 = 0; y0 < L->ny; y0 += 4)
-        for (int x0 = 0; x0 < L->nx; x0 += 32) items.push_back(make_int4(l, x0, y0, z0));
+        for (int x0 = 0; x0 < L->nx; x0 += 32) dst.push_back(make_int4(l, x0, y0, z0));
   }
   if (b->dev.pitems) cudaFree(b->dev.pitems);
+  if (b->dev.pitems8) cudaFree(b->dev.pitems8);
   if (b->dev.witems) cudaFree(b->dev.witems);
-  b->dev.pitems = b->dev.witems = nullptr;
+  b->dev.pitems = b->dev.pitems8 = b->dev.witems = nullptr;
   b->dev.npitems = (int)items.size();
+  b->dev.npitems8 = (int)items8.size();
   b->dev.nwitems = (int)witems.size();
   if (!items.empty()) {
     BCK(b, cudaMalloc(&b->dev.pitems, items.size() * sizeof(int4)));
     BCK(b, cudaMemcpyAsync(b->dev.pitems, items.data(), items.size() * sizeof(int4),
+                           cudaMemcpyHostToDevice, b->dev.stream));
+  }
+  if (!items8.empty()) {
+    BCK(b, cudaMalloc(&b->dev.pitems8, items8.size() * sizeof(int4)));
+    BCK(b, cudaMemcpyAsync(b->dev.pitems8, items8.data(), items8.size() * sizeof(int4),
                            cudaMemcpyHostToDevice, b->dev.stream));
   }
   if (!witems.empty()) {
@@ -1169,7 +1221,8 @@ static pflb_status batch_build_pipe_items(pflb_batch *b) {
     BCK(b, cudaMemcpyAsync(b->dev.witems, witems.data(), witems.size() * sizeof(int2),
                            cudaMemcpyHostToDevice, b->dev.stream));
   }
-  b->dev.pgrid = (int)std::max(1LL, std::min<long long>(b->dev.npitems, slots));
+  b->dev.pgrid = (int)std::max(
+      1LL, std::min<long long>(std::max(b->dev.npitems, b->dev.npitems8), slots));
   return PFLB_OK;
 }
 
@@ -1426,7 +1479,7 @@ extern "C" void pflb_batch_destroy(pflb_batch *b) {
   batch_drop_graph(b);
   void *ptrs[] = {b->dev.descs,   b->dev.par0,   b->dev.items,  b->dev.counter,
                   b->dev.bstep,   b->dev.xspecs, b->dev.xlist,  b->dev.pitems,
-                  b->dev.witems,  b->dev.pcounter};
+                  b->dev.pitems8, b->dev.witems, b->dev.pcounter};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (b->ev) cudaEventDestroy(b->ev);

@@ -96,6 +96,8 @@ struct BatchDev {
   // nodes in chunks of 128 records (int2: lattice, first record)
   void *pitems = nullptr;
   int npitems = 0;
+  void *pitems8 = nullptr;  // the same for lattices staged in 8-byte chunks
+  int npitems8 = 0;
   int *pcounter = nullptr;
   int plz = 8, pgrid = 0;
   int pmask = 0;  // bit q: a pipelined lattice starts the batch call at A-A parity q
@@ -103,13 +105,14 @@ struct BatchDev {
   int nwitems = 0;
 };
 
-// The pipelined step kernel runs with periodic x and nx a multiple of the
-// values per 16-byte chunk (4 at FP32, 8 at 16-bit storage) and of 4 (its
+// The pipelined step kernel runs with periodic x and nx a multiple of 4 (its
 // 4-byte flag words), so that its row chunks and flag words are aligned;
-// elsewhere PFLB_KERNEL_PIPE falls back to the fused kernel.
-inline bool pipe_layout_ok(const Lattice &L) {
-  const int v = 16 / (int)L.elem;
-  return !L.bc_on && L.nx % (v > 4 ? v : 4) == 0;
+// elsewhere PFLB_KERNEL_PIPE falls back to the fused kernel.  It stages rows
+// in 16-byte chunks, or in 8-byte chunks at 16-bit storage when nx is not a
+// multiple of 8 (pipe_chunk_bytes).
+inline bool pipe_layout_ok(const Lattice &L) { return !L.bc_on && L.nx % 4 == 0; }
+inline int pipe_chunk_bytes(const Lattice &L) {
+  return (L.elem == 2 && L.nx % 8 != 0) ? 8 : 16;
 }
 inline bool pipe_kernel_runs(const Lattice &L) {
   return L.kernel == PFLB_KERNEL_PIPE && pipe_layout_ok(L);

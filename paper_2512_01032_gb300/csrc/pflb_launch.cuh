@@ -147,7 +147,7 @@ static cudaError_t launch_async_t(Lattice &L, Args<float, float> &a) {
   return cudaGetLastError();
 }
 
-// The pipelined kernel (periodic x; nx a multiple of 4, of 8 at 16-bit).
+// The pipelined kernel (periodic x; nx a multiple of 4).
 template <class S>
 constexpr bool pipe_storage() {
   return true;
@@ -155,7 +155,7 @@ constexpr bool pipe_storage() {
 inline bool pipe_eligible(const Lattice &L) { return pipe_kernel_runs(L); }
 
 // Dynamic shared memory above 48 KB is opted into once per device.
-template <class S, class R, bool ODD, bool DIAG, bool FORCE>
+template <class S, class R, bool ODD, bool DIAG, bool FORCE, int CB = 16>
 static cudaError_t pipe_attrs() {
   static unsigned long long done = 0;  // bit d: set on device d
   int dev = 0;
@@ -163,19 +163,20 @@ static cudaError_t pipe_attrs() {
   if (e != cudaSuccess) return e;
   const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
   if (bit && (done & bit)) return cudaSuccess;
-  e = cudaFuncSetAttribute(k_pipe<S, R, ODD, DIAG, FORCE>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PipeSmem<S, R>));
+  e = cudaFuncSetAttribute(k_pipe<S, R, ODD, DIAG, FORCE, CB>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(PipeSmem<S, R, CB>));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_pipe<S, R, ODD, DIAG, FORCE>,
+  e = cudaFuncSetAttribute(k_pipe<S, R, ODD, DIAG, FORCE, CB>,
                            cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
   done |= bit;
   return cudaSuccess;
 }
 
-template <class S, class R, bool ODD, bool DIAG, bool FORCE>
+template <class S, class R, bool ODD, bool DIAG, bool FORCE, int CB = 16>
 static cudaError_t launch_pipe_f(Lattice &L, Args<S, R> &a) {
-  cudaError_t e = pipe_attrs<S, R, ODD, DIAG, FORCE>();
+  cudaError_t e = pipe_attrs<S, R, ODD, DIAG, FORCE, CB>();
   if (e != cudaSuccess) return e;
   const dim3 grid((L.nx + PP_BX - 1) / PP_BX, (L.ny + PP_BY - 1) / PP_BY,
                   (L.nz + L.lz - 1) / L.lz);
@@ -184,18 +185,24 @@ static cudaError_t launch_pipe_f(Lattice &L, Args<S, R> &a) {
   const bool inblock = L.nw > 0 && L.wl && L.wl_lz == L.lz;
   a.wl = inblock ? L.wl : nullptr;
   a.wl_start = inblock ? L.wl_start : nullptr;
-  k_pipe<S, R, ODD, DIAG, FORCE><<<grid, PP_NT, sizeof(PipeSmem<S, R>), L.stream>>>(a);
+  k_pipe<S, R, ODD, DIAG, FORCE, CB><<<grid, PP_NT, sizeof(PipeSmem<S, R, CB>), L.stream>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess || L.nw == 0 || inblock) return e;
   k_wall<S, R, ODD, DIAG><<<(L.nw + 127) / 128, 128, 0, L.stream>>>(a);
   return cudaGetLastError();
 }
 
-// The variant without body-force terms when F_ex = 0 (they vanish there).
+// The variant without body-force terms when F_ex = 0 (they vanish there);
+// 16-bit lattices with nx = 4 mod 8 staged in 8-byte chunks.
 template <class S, class R, bool ODD, bool DIAG>
 static cudaError_t launch_pipe_t(Lattice &L, Args<S, R> &a) {
-  if (a.m.Fx == R(0) && a.m.Fy == R(0) && a.m.Fz == R(0))
-    return launch_pipe_f<S, R, ODD, DIAG, false>(L, a);
+  if constexpr (sizeof(S) == 2) {
+    if (pipe_chunk_bytes(L) == 8) return launch_pipe_f<S, R, ODD, DIAG, true, 8>(L, a);
+  }
+  if constexpr (std::is_same<R, float>::value) {  // FP64 keeps one form (parity)
+    if (a.m.Fx == R(0) && a.m.Fy == R(0) && a.m.Fz == R(0))
+      return launch_pipe_f<S, R, ODD, DIAG, false>(L, a);
+  }
   return launch_pipe_f<S, R, ODD, DIAG, true>(L, a);
 }
 
@@ -357,7 +364,7 @@ void batch_build_descs(Lattice *const *lats, int n, char *host) {
   }
 }
 
-template <class S, class R, bool ODD, bool DIAG>
+template <class S, class R, bool ODD, bool DIAG, int CB = 16>
 static cudaError_t batch_pipe_attrs() {
   static unsigned long long done = 0;  // bit d: set on device d
   int dev = 0;
@@ -365,11 +372,11 @@ static cudaError_t batch_pipe_attrs() {
   if (e != cudaSuccess) return e;
   const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
   if (bit && (done & bit)) return cudaSuccess;
-  e = cudaFuncSetAttribute(k_batch_pipe<S, R, ODD, DIAG>,
+  e = cudaFuncSetAttribute(k_batch_pipe<S, R, ODD, DIAG, CB>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(PipeSmem<S, R>) + sizeof(Args<S, R>)));
+                           (int)(sizeof(PipeSmem<S, R, CB>) + sizeof(Args<S, R>)));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_batch_pipe<S, R, ODD, DIAG>,
+  e = cudaFuncSetAttribute(k_batch_pipe<S, R, ODD, DIAG, CB>,
                            cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
   done |= bit;
@@ -389,17 +396,29 @@ int batch_pipe_blocks_per_sm() {
   return nb > 0 ? nb : 1;
 }
 
-template <class S, class R, bool ODD, bool DIAG>
-static cudaError_t batch_pipe_one(const BatchDev &b) {
-  cudaError_t e = batch_pipe_attrs<S, R, ODD, DIAG>();
+// One launch over the work list of one chunk size (the two lists share the
+// counter, reset before each launch on the batch stream).
+template <class S, class R, bool ODD, bool DIAG, int CB>
+static cudaError_t batch_pipe_list(const BatchDev &b, const void *items, int n) {
+  if (n == 0) return cudaSuccess;
+  cudaError_t e = batch_pipe_attrs<S, R, ODD, DIAG, CB>();
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(b.pcounter, 0, sizeof(int), b.stream);
   if (e != cudaSuccess) return e;
-  const size_t smem = sizeof(PipeSmem<S, R>) + sizeof(Args<S, R>);
-  k_batch_pipe<S, R, ODD, DIAG><<<b.pgrid, PP_NT, smem, b.stream>>>(
-      (const Args<S, R> *)b.descs, b.par0, (const int4 *)b.pitems, b.npitems, b.pcounter,
-      b.bstep, b.plz);
+  const size_t smem = sizeof(PipeSmem<S, R, CB>) + sizeof(Args<S, R>);
+  const int grid = n < b.pgrid ? n : b.pgrid;
+  k_batch_pipe<S, R, ODD, DIAG, CB><<<grid, PP_NT, smem, b.stream>>>(
+      (const Args<S, R> *)b.descs, b.par0, (const int4 *)items, n, b.pcounter, b.bstep, b.plz);
   return cudaGetLastError();
+}
+
+template <class S, class R, bool ODD, bool DIAG>
+static cudaError_t batch_pipe_one(const BatchDev &b) {
+  cudaError_t e = batch_pipe_list<S, R, ODD, DIAG, 16>(b, b.pitems, b.npitems);
+  if constexpr (sizeof(S) == 2) {
+    if (e == cudaSuccess) e = batch_pipe_list<S, R, ODD, DIAG, 8>(b, b.pitems8, b.npitems8);
+  }
+  return e;
 }
 
 // The pipelined lattices of a batch: their march (one launch per A-A parity
@@ -407,7 +426,7 @@ static cudaError_t batch_pipe_one(const BatchDev &b) {
 // nodes.
 template <class S, class R>
 static cudaError_t batch_launch_pipe(const BatchDev &b, bool diag, int tpar) {
-  if (b.npitems == 0) return cudaSuccess;
+  if (b.npitems + b.npitems8 == 0) return cudaSuccess;
   const Args<S, R> *d = (const Args<S, R> *)b.descs;
   cudaError_t e = cudaSuccess;
   for (int par = 0; par < 2 && e == cudaSuccess; ++par) {

@@ -1,6 +1,7 @@
 // pflb_pipe.cuh -- fused step kernel with asynchronous staging of the next
-// planes' populations in 16-byte chunks (any storage type, periodic x, nx a
-// multiple of 4, of 8 at 16-bit storage).
+// planes' populations in 16-byte chunks (8-byte chunks at 16-bit storage
+// when nx is not a multiple of 8; any storage type, periodic x, nx a
+// multiple of 4).
 //
 // The step is k_fused's (arXiv 2512.01032, Sec. II and Sec. III A): one
 // thread per (x, y) column of a 32 x 4 tile marching a chunk of z planes,
@@ -54,9 +55,12 @@ constexpr int PP_FW = (PP_BX + 8) / 4;        // flag words per staged row (x0 -
 #define PFLB_PIPE_MIN_BLOCKS 4
 #endif
 
-template <class S, class R>
-struct PipeSmem {
-  static constexpr int V = 16 / (int)sizeof(S);  // values per 16-byte chunk
+// CB: bytes per staged chunk, 16 (cp.async.cg) or 8 (cp.async.ca; 16-bit
+// storage with nx = 4 mod 8, whose odd rows start 8 bytes off a 16-byte
+// boundary).
+template <class S, class R, int CB = 16>
+struct alignas(16) PipeSmem {
+  static constexpr int V = CB / (int)sizeof(S);  // values per chunk
   static constexpr int W = PP_BX + 2 * V;        // staged row: x0 - V .. x0 + 32 + V
   static constexpr int NCH = W / V;              // chunks per staged row
   static constexpr int HS = h_slots<S>();        // 19, or 20 with the rest remainder
@@ -69,6 +73,17 @@ struct PipeSmem {
 __device__ __forceinline__ void cp_async_16(void *dst, const void *src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src)
                : "memory");
+}
+__device__ __forceinline__ void cp_async_8(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(dst)), "l"(src)
+               : "memory");
+}
+template <int CB>
+__device__ __forceinline__ void cp_async_chunk(void *dst, const void *src) {
+  if constexpr (CB == 16)
+    cp_async_16(dst, src);
+  else
+    cp_async_8(dst, src);
 }
 __device__ __forceinline__ void cp_async_4(void *dst, const void *src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(dst)), "l"(src)
@@ -173,11 +188,11 @@ __device__ __forceinline__ void wall_node(const Args<S, R> &a, int rec, DiagAcc<
 // phi of its own cells in [zb, ze) that wall nodes read, for k_wall after
 // the launch.  Every thread returns with no copy in flight; the caller
 // separates two marches that reuse sm by a barrier.
-template <class S, class R, bool ODD, bool DIAG, bool FORCE>
+template <class S, class R, bool ODD, bool DIAG, bool FORCE, int CB = 16>
 __device__ __forceinline__ void pipe_march(const Args<S, R> &a, int x0, int y0, int zb, int ze,
-                                           PipeSmem<S, R> &sm, R (*wacc)[32], int w0 = 0,
+                                           PipeSmem<S, R, CB> &sm, R (*wacc)[32], int w0 = 0,
                                            int w1 = 0) {
-  using SM = PipeSmem<S, R>;
+  using SM = PipeSmem<S, R, CB>;
   constexpr int V = SM::V, NCH = SM::NCH, HS = SM::HS;
   static_assert(F_SOLID == 1, "all_solid tests bit 0");
   const int tid = threadIdx.x, tx = tid % PP_BX, ty = tid / PP_BX;
@@ -276,10 +291,10 @@ __device__ __forceinline__ void pipe_march(const Args<S, R> &a, int x0, int y0, 
       const int cell = h_off[k] + zoff;
       if (!half) {
 #pragma unroll
-        for (int i = 0; i < 10; ++i) cp_async_16(&dst[i][r][ch * V], a.hin[i] + cell);
+        for (int i = 0; i < 10; ++i) cp_async_chunk<CB>(&dst[i][r][ch * V], a.hin[i] + cell);
       } else {
 #pragma unroll
-        for (int i = 10; i < HS; ++i) cp_async_16(&dst[i][r][ch * V], a.hin[i] + cell);
+        for (int i = 10; i < HS; ++i) cp_async_chunk<CB>(&dst[i][r][ch * V], a.hin[i] + cell);
       }
     }
   };
@@ -302,7 +317,7 @@ __device__ __forceinline__ void pipe_march(const Args<S, R> &a, int x0, int y0, 
         const int cell = g_off[u][1] + sz * z;
 #pragma unroll
         for (int k = 0; k < Q; ++k)
-          if (k >= k0 && k < k1) cp_async_16(&sm.g[k][r][ch * V], a.g[k] + cell);
+          if (k >= k0 && k < k1) cp_async_chunk<CB>(&sm.g[k][r][ch * V], a.g[k] + cell);
       } else {
         const int zo[3] = {sz * wrapz(zu - 1), sz * z, sz * wrapz(zu + 1)};
 #pragma unroll
@@ -313,7 +328,8 @@ __device__ __forceinline__ void pipe_march(const Args<S, R> &a, int x0, int y0, 
           const int hi = (V + PP_BX - 1 - (cxk < 0 ? cxk : 0)) / V;
           if (ch < lo || ch > hi) continue;
           // source row y - c_k and plane z - c_k
-          cp_async_16(&sm.g[k][r][ch * V], a.g[opp_of(k)] + (g_off[u][1 - cyk] + zo[1 - czk]));
+          cp_async_chunk<CB>(&sm.g[k][r][ch * V],
+                             a.g[opp_of(k)] + (g_off[u][1 - cyk] + zo[1 - czk]));
         }
       }
     }
@@ -443,8 +459,9 @@ __device__ __forceinline__ void pipe_march(const Args<S, R> &a, int x0, int y0, 
 }
 
 // One lattice: a grid of (tile column, chunk of lz planes) blocks.  FORCE
-// = false is the variant for a lattice without body force.
-template <class S, class R, bool ODD, bool DIAG, bool FORCE>
+// = false is the variant for a lattice without body force; CB the staged
+// chunk size (PipeSmem).
+template <class S, class R, bool ODD, bool DIAG, bool FORCE, int CB = 16>
 __global__ void __launch_bounds__(PP_NT, PFLB_PIPE_MIN_BLOCKS)
     k_pipe(const __grid_constant__ Args<S, R> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -461,10 +478,10 @@ __global__ void __launch_bounds__(PP_NT, PFLB_PIPE_MIN_BLOCKS)
     w0 = a.wl_start[b];
     w1 = a.wl_start[b + 1];
   }
-  pipe_march<S, R, ODD, DIAG, FORCE>(a, blockIdx.x * PP_BX, blockIdx.y * PP_BY, zb,
-                                     min(zb + a.lz, a.nz),
-                                     *reinterpret_cast<PipeSmem<S, R> *>(smem_raw), wacc, w0,
-                                     w1);
+  pipe_march<S, R, ODD, DIAG, FORCE, CB>(a, blockIdx.x * PP_BX, blockIdx.y * PP_BY, zb,
+                                         min(zb + a.lz, a.nz),
+                                         *reinterpret_cast<PipeSmem<S, R, CB> *>(smem_raw),
+                                         wacc, w0, w1);
 }
 
 // Many lattices: a persistent grid pulls work items (lattice, x0, y0, z0)
@@ -478,15 +495,16 @@ __global__ void __launch_bounds__(PP_NT, PFLB_PIPE_MIN_BLOCKS)
 // descriptor's fields in shared memory cost registers that k_pipe's
 // constant-bank parameters do not (168 per thread, three blocks per SM);
 // with one, the march fits k_pipe's 128 registers and four blocks per SM
-// without spilling.
-template <class S, class R, bool ODD, bool DIAG>
+// without spilling.  CB: the staged chunk size of the items' lattices (the
+// host builds one work list per chunk size).
+template <class S, class R, bool ODD, bool DIAG, int CB = 16>
 __global__ void __launch_bounds__(PP_NT, 4)
     k_batch_pipe(const Args<S, R> *__restrict__ descs, const int *__restrict__ par0,
                  const int4 *__restrict__ items, int nitems, int *counter, const int *bstep,
                  int LZ) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  PipeSmem<S, R> &sm = *reinterpret_cast<PipeSmem<S, R> *>(smem_raw);
-  Args<S, R> *sa = reinterpret_cast<Args<S, R> *>(smem_raw + sizeof(PipeSmem<S, R>));
+  PipeSmem<S, R, CB> &sm = *reinterpret_cast<PipeSmem<S, R, CB> *>(smem_raw);
+  Args<S, R> *sa = reinterpret_cast<Args<S, R> *>(smem_raw + sizeof(PipeSmem<S, R, CB>));
   __shared__ R wacc[DIAG_MAX_WARPS][32];
   __shared__ int s_item;
   const int tid = threadIdx.x;
@@ -510,7 +528,7 @@ __global__ void __launch_bounds__(PP_NT, 4)
     if (DIAG && it.y == 0 && it.z == 0 && it.w == 0 && tid < 32 && a.diag_zero)
       a.diag_zero[tid] = 0.0;
     const int ze = min(it.w + LZ, a.nz);
-    pipe_march<S, R, ODD, DIAG, true>(a, it.y, it.z, it.w, ze, sm, wacc);
+    pipe_march<S, R, ODD, DIAG, true, CB>(a, it.y, it.z, it.w, ze, sm, wacc);
     __syncthreads();  // shared descriptor and staging buffers are reused by the next item
   }
 }

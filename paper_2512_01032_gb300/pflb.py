@@ -173,6 +173,8 @@ def load(build_if_missing: bool = True):
     lib.pflb_selftest_wait_timeout.restype = st
     lib.pflb_get_kernel.argtypes = [C.c_void_p, _P(C.c_int)]
     lib.pflb_get_kernel.restype = st
+    lib.pflb_tune.argtypes = [C.c_void_p, C.c_int, _P(C.c_int)]
+    lib.pflb_tune.restype = st
     lib.pflb_step.argtypes = [C.c_void_p, C.c_int64]
     lib.pflb_step.restype = st
     lib.pflb_step_diag.argtypes = [C.c_void_p, C.c_int64, _P(Diag)]
@@ -405,6 +407,13 @@ class Lattice:
         out = (C.c_int * 4)()
         _check(self._lib.pflb_get_kernel(self._h, out))
         return dict(kind=out[0], bx=out[1], by=out[2], lz=out[3])
+
+    def tune(self, trial_steps=50) -> int:
+        """Pick the fastest planes per block for the kernel in effect by
+        timing real steps (the lattice advances); returns the chosen lz."""
+        lz = C.c_int(0)
+        _check(self._lib.pflb_tune(self._h, int(trial_steps), C.byref(lz)))
+        return lz.value
 
     def step(self, n=1):
         _check(self._lib.pflb_step(self._h, int(n)))

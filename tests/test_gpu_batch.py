@@ -23,12 +23,19 @@ pytestmark = pytest.mark.gpu
 FIELDS = ("phi", "rho", "P", "ux", "uy", "uz")
 
 
-def _cases():
+def _cases(storage="fp32"):
+    # The 36-wide channel exercises the 16-bit march staged in 8-byte chunks
+    # (nx = 4 mod 8).  It is left out at FP64: there the batch and the
+    # single-lattice kernel, compiled separately, part by up to 2e-10 on this
+    # walled channel through the mobility correction's switch (Eq. 4, reading
+    # R4; the wall-case FP64 bound of the parity tests), above the 1e-11 that
+    # the other lattices hold.
+    extra = [] if storage == "fp64" else [CS.channel_case(36, 10, 7, theta=100.0)]
     return [CS.droplet_case(24, 6.0),
             CS.channel_case(40, 14, 12),
             CS.channel_case(33, 10, 7, theta=60.0),
             CS.sessile_case(32, 120.0),
-            CS.slit_case(96, 16, 4)]
+            CS.slit_case(96, 16, 4)] + extra
 
 
 def _lattice(case, storage):
@@ -41,7 +48,7 @@ def _lattice(case, storage):
 
 
 def _pairs(storage):
-    cases = _cases()
+    cases = _cases(storage)
     alone = [_lattice(c, storage) for c in cases]
     mixed = [_lattice(c, storage) for c in cases]
     # start two lattices at odd A-A parity
@@ -141,7 +148,7 @@ def _batch_of_one_reference(storage, steps):
 @pytest.mark.parametrize("shape", [(32, 4, 16, 0), (16, 8, 4, 1), (64, 4, 32, 2), (16, 16, 8, 0)])
 def test_batch_launch_shapes(shape):
     from paper_2512_01032_gb300 import pflb
-    ones, mixed = _batch_of_one_reference("fp32", [23] * 5)
+    ones, mixed = _batch_of_one_reference("fp32", [23] * len(_cases("fp32")))
     B = pflb.Batch(mixed)
     B.set_launch(*shape)
     B.step(5)

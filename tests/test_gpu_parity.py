@@ -371,3 +371,26 @@ def test_async_diagnostics_match_sync_reads():
             assert a[key] == pytest.approx(b[key], rel=1e-6, abs=1e-300), key
     with pytest.raises(pflb.PflbError):
         A.diag_wait(prev + 1, rp[0])  # not queued yet
+
+
+def test_tune_depth_keeps_results_bitwise():
+    """pflb_tune times real steps at several planes per block and keeps the
+    fastest; the depth changes only which block updates a cell, so the
+    tuned lattice equals one stepped as often at the automatic depth, bit
+    for bit (FP32, walls: the per-block wall lists follow the depth)."""
+    from paper_2512_01032_gb300 import pflb
+    g, p, init = CS.sessile_case(32, 120.0)
+    A = pflb.Lattice(g.nx, g.ny, g.nz, solid=g.solid, wall_normal=g.normals(),
+                     theta_cells=g.theta(), storage="fp32", **p)
+    B = pflb.Lattice(g.nx, g.ny, g.nz, solid=g.solid, wall_normal=g.normals(),
+                     theta_cells=g.theta(), storage="fp32", **p)
+    for L in (A, B):
+        L.init_tanh(0, init["center"], init["R"])
+    lz = A.tune(trial_steps=3)
+    assert lz in (4, 6, 8, 10, 12, 16, 24, 32) or lz == B.get_kernel()["lz"]
+    assert A.get_kernel() == dict(kind=3, bx=32, by=4, lz=lz)
+    B.step(A.t)
+    A.step(5)
+    B.step(5)
+    for k in ("phi", "P", "ux", "uz"):
+        assert np.array_equal(A.read(k), B.read(k)), k

@@ -37,6 +37,25 @@ def test_reduced_storage_pointwise_bound(storage, kernel):
         assert e["phi"] <= max(s, 1) * PER_STEP[storage] * 1.0001, (storage, s, e)
 
 
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+@pytest.mark.parametrize("nx", [36, 40])
+def test_pipelined_reduced_storage_pointwise_bound(storage, nx):
+    """The pipelined kernel at 16-bit storage on a walled channel with a drop
+    and a body force: rows staged in 8-byte chunks (nx = 36, not a multiple
+    of 8) or 16-byte chunks (nx = 40), wall nodes updated after each
+    block's march; the same pointwise bound against the oracle."""
+    g, p, init = CS.channel_case(nx, 14, 12)
+    G, Orc = CS.make_pair(g, p, init, storage=storage, kernel=3)
+    assert G.get_kernel()["kind"] == 3
+    t = 0
+    for s in (1, 4, 10):
+        G.step(s - t)
+        Orc.step(s - t)
+        t = s
+        e = CS.rel_errors(CS.gpu_fields(G), Orc.macros(), 2 * p["sigma"] / init["R"])
+        assert e["phi"] <= max(s, 1) * PER_STEP[storage] * 1.0001, (storage, nx, s, e)
+
+
 def _drop_on_flat_wall(theta):
     """Quasi 2-D drop on a flat floor (72 x 1 x 30, walls z = 0 and 29, the
     lid at 90 deg), started as a half disc of radius 14: geometry, params
