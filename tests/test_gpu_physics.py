@@ -43,11 +43,14 @@ def test_laplace_pressure_jump():
 
 def _off_axis(center, dx=1e-3):
     """The drop's centre moved 1e-3 of a spacing in x.  Started exactly on
-    the box's mirror planes, the 30 and 150 deg drops can go non-finite at
-    FP32 after 4-9 k steps depending on the compiled variant (roundoff
-    asymmetry amplified by n = grad phi / (|grad phi| + 1e-10) where the
-    symmetric start makes grad phi vanish); shifted by 1e-5 to 5e-5 they and
-    the FP64 runs all settle at the same max |u|."""
+    the box's mirror planes, the 30 deg drop at FP32 went non-finite after
+    about 820 steps in one build: spreading fast over the sphere (max |u|
+    1e-2) it drove phi down to -3.5e-4 next to the wall, where
+    rho = rho_L + phi (rho_H - rho_L) falls to 6.5e-4 and u = j / rho
+    runs away; started off the planes it has stayed finite in every run.  (The
+    FP64 blow-ups at 120 and 150 deg after 2-17 k steps had another cause,
+    the pole of the printed mobility-correction switch, reading R4 of
+    Eq. 4.)"""
     return (center[0] + dx, center[1], center[2])
 
 
