@@ -549,6 +549,48 @@ def batch_compare(dev, steps=100, warmup=5):
     return out
 
 
+def serve_compare(count=8, ramp_every=500, budget_gb=16.0, max_cells=8 << 20):
+    """Compact serving figure for the default line: the first `count`
+    requests of the seeded Poisson trace (critical-pressure solves in
+    constriction ducts, body-force ramp of `ramp_every` steps per beta level,
+    at most 13 levels) replayed in real time through the batching server at
+    BF16 and through the plain server at FP32 (one request at a time), on
+    the host clock as the full serving workload measures them.  Tens of
+    seconds in all; the full trace with the stated ramp is
+    --workload serve."""
+    from paper_2512_01032_gb300 import pflb, shard
+    trace = synth.serving_trace(count)
+    prepared = []
+    for req in trace:
+        r = synth.constriction_request(req, ramp_every=ramp_every, max_steps=13 * ramp_every)
+        g = r["geometry"]
+        geo = dict(nx=g.nx, ny=g.ny, nz=g.nz, solid=g.solid, normals=g.normals(),
+                   theta=g.theta())
+        prepared.append((geo, r["params"], synth.constriction_spec(r)))
+    out = {"workload": f"first {count} requests of the seeded serving trace, beta ramp every "
+                       f"{ramp_every} steps, at most {13 * ramp_every} steps",
+           "budget_gb": budget_gb}
+    for name, cfg in (("batched_bf16", dict(storage="bf16", batched=True,
+                                            max_active_cells=max_cells)),
+                      ("plain_fp32", dict(storage="fp32", batched=False, max_active=1))):
+        S = pflb.Server(hbm_budget_bytes=int(budget_gb * (1 << 30)),
+                        steps_per_tick=ramp_every // 2, **cfg)
+        tickets, wall = serve_trace(S, prepared, trace)
+        st = S.stats()
+        res = [S.poll(t) for t in tickets]
+        S.close()
+        lat = sorted(q["latency_s"] for q in res if q["state"] == pflb.REQ_DONE)
+        out[name] = {"solves_per_s": st["completed"] / max(st["makespan_s"], 1e-9),
+                     "p50_s": shard.nearest_rank(lat, 0.5),
+                     "p99_s": shard.nearest_rank(lat, 0.99),
+                     "completed": st["completed"], "failed": st["failed"],
+                     "mlups": st["cell_updates"] / max(st["makespan_s"], 1e-9) / 1e6,
+                     "broke_through": sum(q["broke_through"] for q in res)}
+    out["ratio_solves_per_s"] = out["batched_bf16"]["solves_per_s"] / max(
+        out["plain_fp32"]["solves_per_s"], 1e-12)
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -559,7 +601,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true",
-                    help="skip the compact batched-vs-per-lattice figure of the default line")
+                    help="skip the compact batching and serving figures of the default line")
     ap.add_argument("--workload", choices=["sessile", "channels", "serve"], default="sessile",
                     help="sessile: the 128^3 sessile droplet (default); channels: many "
                          "uneven channel lattices advanced as one batch; serve: a request "
@@ -712,9 +754,10 @@ def main(argv=None):
                "final_mass": float(phi_out.sum()), "final_diag_mass": last["mass"]}
         L2.close()
 
-    batch = None
+    batch = serve = None
     if rank == 0 and world == 1 and not args.no_batch:
         batch = batch_compare(dev)
+        serve = serve_compare()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -733,7 +776,7 @@ def main(argv=None):
                                "region, and the timed region"),
                 "diag_last": {"mass": d["mass"], "dp": d["dp"], "u_max": d["u_max"],
                               "nonfinite": d["nonfinite"]},
-                "batch": batch}
+                "batch": batch, "serve": serve}
         print(json.dumps(line), flush=True)
     L.close()
     if world > 1:

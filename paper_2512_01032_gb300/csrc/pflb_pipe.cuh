@@ -224,8 +224,8 @@ __device__ __forceinline__ void pipe_march(const Args<S, R> &a, int x0, int y0, 
     }
   }
   // phi field writes: 2 = own and ring cells of every summed plane (this
-  // block's wall nodes read them), 1 = own cells of [zb, ze) (k_wall reads
-  // them), 0 = none (block-uniform)
+  // block's wall nodes read them), 1 = own cells of [zb, ze) (k_wall or
+  // k_batch_wall reads them), 0 = none (block-uniform)
   const int phimode = w1 > w0 ? 2 : (a.wl_start ? 0 : 1);
   // Plane wrap by additions: the planes touched lie within a few of [0, nz).
   auto wrapz = [nz](int zu) {
@@ -398,7 +398,7 @@ __device__ __forceinline__ void pipe_march(const Args<S, R> &a, int x0, int y0, 
     phi_plane(z + 1);
     const int c = col + sz * z;
     const uint8_t f = flag_byte(sm.fl[z & 3], ty + 1, tx);
-    const bool fluid = valid && !(f & (F_SOLID | F_WALL));  // wall nodes: k_wall
+    const bool fluid = valid && !(f & (F_SOLID | F_WALL));  // wall nodes: after the march
     R h[Q], g[Q];
     if (fluid) {
       cell_h(sm.h[z & 1], ty + 1, V + tx, h);
