@@ -151,3 +151,52 @@ def test_precision_error_table():
         assert abs(r["angle60"]) <= BAR_ANGLE[st] and abs(r["angle120"]) <= BAR_ANGLE[st], (st, r)
         for k in ("drift_drop", "drift_wall60", "drift_wall120"):
             assert abs(r[k]) <= BAR_DRIFT[st], (st, k, r)
+
+
+@pytest.mark.slow
+def test_config3_slit_filling_precision():
+    """The capillary-filling slit as configured for the precision study:
+    1024 x 64 x 4, walls y = 0 and 63 over 128 <= x < 896 (theta = 45),
+    liquid filling the left reservoir, density ratio 1000, viscosity ratio
+    50 (nu_H = 1/60), sigma = 0.01, W = 4, 100 000 steps.  The penetration
+    length l(t) (the device front probe, phi = 0.5 crossing along x in the
+    channel's centre rows) every 5000 steps at each storage against FP64
+    storage on the GPU, which stands in for the oracle here (parity with it
+    per step is 1e-11, 1e-10 in wall cases; the oracle itself would need
+    about 45 minutes on 16 host cores for this run).  The slit fills until
+    the reservoir's 128 cells of liquid are used up (l ~ 190 after 35 000
+    steps) and then rests.
+    Measured: l(t) within 2.5e-4 (FP32), 2.2e-3 (FP16) and 2.6e-2 (BF16) of
+    FP64; relative mass drift 5.8e-5 (FP32, no compensation), -4.2e-4 (FP16:
+    the gas phase's populations sit below FP16's normal range and the
+    rounding compensation cannot hold them), 1.4e-7 (BF16).  BF16 misses
+    the 1 % target on this case: it lags during the fast filling (107.8
+    against 110.6 at 15 000 steps) and rests 1.5 % further in with spurious
+    currents four times FP64's.  The bars below hold FP32 and FP16 to their
+    formats and record BF16's shortfall without calling it a pass of the
+    1 % target."""
+    import synth
+    from paper_2512_01032_gb300 import pflb
+    g, p, init = synth.slit(1024, 64, 4, 128)
+    runs = {}
+    for st in ("fp64", "fp32", "fp16", "bf16"):
+        L = pflb.Lattice(g.nx, g.ny, g.nz, solid=g.solid, wall_normal=g.normals(),
+                         theta_cells=g.theta(), storage=st, **p)
+        L.init_tanh(init["shape"], init["center"], init["R"], init["normal"])
+        L.set_region((128, 896, 31, 33, 0, g.nz))
+        m0 = L.diag()["mass"]
+        ls = []
+        for _ in range(20):
+            L.step(5000)
+            d = L.diag()
+            ls.append(d["front_x"] - 127.0)
+        runs[st] = (np.array(ls), (d["mass"] - m0) / m0)
+        L.close()
+    ref, drift64 = runs["fp64"]
+    assert abs(drift64) < 1e-12
+    assert ref[0] > 5 and 150 < ref[-1] < 230
+    err = {st: np.max(np.abs(runs[st][0] - ref) / ref) for st in ("fp32", "fp16", "bf16")}
+    drift = {st: abs(runs[st][1]) for st in ("fp32", "fp16", "bf16")}
+    assert err["fp32"] < 1e-3 and drift["fp32"] < 2e-4, (err, drift)
+    assert err["fp16"] < 1e-2 and drift["fp16"] < 1e-3, (err, drift)
+    assert err["bf16"] < 5e-2 and drift["bf16"] < 1e-6, (err, drift)
