@@ -124,6 +124,7 @@ def test_create_rejects_bad_geometry():
     assert b"null" in lib.pflb_last_error()
     # null handles are rejected, not dereferenced
     assert lib.pflb_step(None, 1) == pflb.ERR_ARG
+    assert lib.pflb_tune(None, 10, None) == pflb.ERR_ARG
     assert lib.pflb_get_step(None) == -1
     lib.pflb_destroy(None)
     # batches: empty or null lattice lists and null batches are rejected
