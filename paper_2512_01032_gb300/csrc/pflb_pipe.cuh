@@ -182,9 +182,10 @@ __device__ __forceinline__ void wall_node(const Args<S, R> &a, int rec, DiagAcc<
 // a.wl[w0 .. w1) are the wall nodes among the march's cells: the block
 // updates them after the march (wall_node), from the phi of the cells
 // around them, which it writes to the phi field as it sums them (own and
-// ring cells of every plane it sums; only this block reads them before the
-// step ends, and a cell summed by two blocks gets the same bits from
-// both).  Without per-block lists (a.wl_start null) the march writes the
+// ring cells of every plane it sums).  A block reads back only values it
+// wrote itself in this launch, and a cell summed by two blocks gets the
+// same bits from both (same staged h, same order), so the duplicate writes
+// are benign.  Without per-block lists (a.wl_start null) the march writes the
 // phi of its own cells in [zb, ze) that wall nodes read, for k_wall after
 // the launch.  Every thread returns with no copy in flight; the caller
 // separates two marches that reuse sm by a barrier.
